@@ -1,0 +1,523 @@
+// C ABI of libgwcp (include/gwcp.h): context, trace loading, the analysis pipeline,
+// race reporting, test hooks.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+
+#include "gwcp_internal.cuh"
+
+namespace gwcp {
+unsigned long long launch_count();
+size_t check_chunks(uint32_t n_acc);
+size_t check_group_count(uint32_t n_acc);
+void phaseE_scan(const Bufs& b, const Sizes& z, cudaStream_t s, Prof& p);
+void phaseF_deps(const Bufs& b, const Sizes& z, cudaStream_t s, Prof& p);
+
+cudaEvent_t Prof::ev() {
+  if (used == pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    pool.push_back(e);
+  }
+  return pool[used++];
+}
+void Prof::begin(const char* name, double bytes) {
+  if (!on) return;
+  Rec r{name, ev(), ev(), bytes};
+  cudaEventRecord(r.a, s);
+  recs.push_back(r);
+}
+void Prof::end() {
+  if (!on || recs.empty()) return;
+  cudaEventRecord(recs.back().b, s);
+}
+}  // namespace gwcp
+
+using namespace gwcp;
+
+struct gwcp_ctx {
+  int device = 0;
+  gwcp_options opt{};
+  const Event* ev_dev = nullptr;
+  Event* ev_own = nullptr;
+  size_t ev_own_cap = 0;
+  uint64_t n = 0;
+  Geo g{};
+  bool has_trace = false, computed = false;
+  int compute_rc = GWCP_ERR_STATE;
+  std::map<std::string, std::pair<void*, size_t>> allocs;
+  Bufs b{};
+  Sizes z{};
+  DevStatus* st_host = nullptr;
+  uint32_t* cnt_host = nullptr;  // pinned readback of sizes
+  Prof prof;
+  bool races_second = false;
+  uint64_t n_races = 0;
+  unsigned long long bad_index = ~0ull;
+  uint64_t counters[8] = {};
+  std::vector<float> prof_ms;
+  std::vector<double> prof_bytes;
+  std::vector<const char*> prof_names;
+};
+
+namespace {
+
+const uint32_t kNoneHost = 0xFFFFFFFFu;
+
+template <typename T>
+T* get(gwcp_ctx* c, const char* name, size_t count, bool* oom) {
+  const size_t bytes = (count ? count : 1) * sizeof(T);
+  auto& a = c->allocs[name];
+  if (a.second < bytes) {
+    if (a.first) cudaFree(a.first);
+    a.first = nullptr;
+    a.second = 0;
+    const size_t want = bytes + bytes / 8;
+    if (cudaMalloc(&a.first, want) != cudaSuccess) {
+      cudaGetLastError();
+      *oom = true;
+      return nullptr;
+    }
+    a.second = want;
+  }
+  return static_cast<T*>(a.first);
+}
+
+int cuda_rc() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GWCP_OK : GWCP_ERR_CUDA;
+}
+
+int read_status(gwcp_ctx* c, cudaStream_t s, const uint32_t* const* extra, int n_extra) {
+  cudaMemcpyAsync(c->st_host, c->b.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+  for (int i = 0; i < n_extra; ++i)
+    cudaMemcpyAsync(c->cnt_host + i, extra[i], sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return GWCP_ERR_CUDA;
+  return cuda_rc();
+}
+
+int run(gwcp_ctx* c, cudaStream_t s) {
+  Bufs& b = c->b;
+  Sizes& z = c->z;
+  const Geo& g = c->g;
+  bool oom = false;
+  z = Sizes{};
+  z.N = c->n;
+  z.TA = g.Wp <= 256 ? 2048 : 8192;
+  z.ntA = uint32_t((z.N + z.TA - 1) / z.TA);
+  b.ev = c->ev_dev;
+  b.st = get<DevStatus>(c, "st", 1, &oom);
+  b.hist_a = get<uint32_t>(c, "hist_a", size_t(g.W) * z.ntA + 1, &oom);
+  b.tile_cnt = get<uint32_t>(c, "tile_cnt", 3 * (size_t(z.ntA) + 1), &oom);
+  const size_t scan_need = std::max({scan_tmp_need(size_t(g.W) * z.ntA + 1), radix_tmp_need(z.N + 1),
+                                     scan_tmp_need(z.N + 1)}) + 64;
+  b.scan_tmp = get<uint32_t>(c, "scan_tmp", scan_need, &oom);
+  if (oom) return GWCP_ERR_OOM;
+  DevStatus init{};
+  init.bad_index = ~0ull;
+  init.key_and = ~0ull;
+  init.lock_and = ~0ull;
+  cudaMemcpyAsync(b.st, &init, sizeof(init), cudaMemcpyHostToDevice, s);
+  c->prof.on = c->opt.profile != 0;
+  c->prof.s = s;
+  c->prof.recs.clear();
+  c->prof.used = 0;
+
+  // ---- A: counts, then sync 1 -------------------------------------------------------
+  phaseA_count(b, g, z, s, c->prof);
+  {
+    const uint32_t* ex[4] = {b.hist_a + size_t(g.W) * z.ntA, b.tile_cnt + z.ntA, b.tile_cnt + 2 * z.ntA + 1,
+                             b.tile_cnt + 3 * z.ntA + 2};
+    int rc = read_status(c, s, ex, 4);
+    if (rc) return rc;
+  }
+  int code = c->st_host->code;
+  if (code && code != GWCP_ERR_INVALID_TRACE) return code;
+  z.nS = c->cnt_host[0];
+  z.n_acc = c->cnt_host[1];
+  z.n_acqrel = c->cnt_host[2];
+  z.n_bar = c->cnt_host[3];
+  z.n_sync = z.nS - z.n_acc;
+  const uint64_t key_mask = c->st_host->key_or ^ c->st_host->key_and;
+  const uint64_t lock_mask = c->st_host->lock_or ^ c->st_host->lock_and;
+
+  b.S = get<uint32_t>(c, "S", z.nS, &oom);
+  b.seg = get<uint32_t>(c, "seg", g.W + 1, &oom);
+  b.acqrel = get<uint32_t>(c, "acqrel", z.n_acqrel, &oom);
+  b.bar = get<uint32_t>(c, "bar", z.n_bar, &oom);
+  b.acc_key = get<uint64_t>(c, "acc_key", z.n_acc, &oom);
+  b.acc_idx = get<uint32_t>(c, "acc_idx", z.n_acc, &oom);
+  b.acc_key2 = get<uint64_t>(c, "acc_key2", z.n_acc, &oom);
+  b.acc_idx2 = get<uint32_t>(c, "acc_idx2", z.n_acc, &oom);
+  const size_t ns1 = size_t(z.n_sync) + 1;
+  b.sy_cnt = get<uint32_t>(c, "sy_cnt", z.nS / 4096 + 2, &oom);
+  b.sy_spos = get<uint32_t>(c, "sy_spos", ns1, &oom);
+  b.sy_idx = get<uint32_t>(c, "sy_idx", ns1, &oom);
+  b.sy_kind = get<uint32_t>(c, "sy_kind", ns1, &oom);
+  b.sy_start = get<uint32_t>(c, "sy_start", g.W + 1, &oom);
+  b.sy_aux = get<uint32_t>(c, "sy_aux", ns1, &oom);
+  b.sy_N = get<uint32_t>(c, "sy_N", ns1, &oom);
+  b.sy_depth = get<uint32_t>(c, "sy_depth", ns1, &oom);
+  b.sy_inner = get<uint32_t>(c, "sy_inner", ns1, &oom);
+  b.sy_ver = get<uint32_t>(c, "sy_ver", ns1, &oom);
+  b.sy_match = get<uint32_t>(c, "sy_match", ns1, &oom);
+  b.sy_relk = get<uint32_t>(c, "sy_relk", ns1, &oom);
+  b.incs_cnt = get<uint32_t>(c, "incs_cnt", ns1, &oom);
+  b.vcount = get<uint32_t>(c, "vcount", g.W + 1, &oom);
+  const size_t na1 = size_t(z.n_acqrel) + 1;
+  b.lk_key = get<uint64_t>(c, "lk_key", na1, &oom);
+  b.lk_k = get<uint32_t>(c, "lk_k", na1, &oom);
+  b.lk_key2 = get<uint64_t>(c, "lk_key2", na1, &oom);
+  b.lk_k2 = get<uint32_t>(c, "lk_k2", na1, &oom);
+  b.lk_flags = get<uint32_t>(c, "lk_flags", na1, &oom);
+  b.lk_csid = get<uint32_t>(c, "lk_csid", na1, &oom);
+  b.lk_rank = get<uint32_t>(c, "lk_rank", na1, &oom);
+  b.lock_first = get<uint32_t>(c, "lock_first", na1 + 1, &oom);
+  b.lock_cs_lo = get<uint32_t>(c, "lock_cs_lo", na1 + 1, &oom);
+  b.cs_of_sync = get<uint32_t>(c, "cs_of_sync", ns1, &oom);
+  b.cs_agent = get<uint32_t>(c, "cs_agent", na1, &oom);
+  b.cs_sid = get<uint32_t>(c, "cs_sid", na1, &oom);
+  b.cs_epoch = get<uint32_t>(c, "cs_epoch", na1, &oom);
+  b.cs_rel_idx = get<uint32_t>(c, "cs_rel_idx", na1, &oom);
+  b.cs_lock = get<uint32_t>(c, "cs_lock", na1, &oom);
+  b.cs_parent = get<uint32_t>(c, "cs_parent", na1, &oom);
+  b.acq_dep_off = get<uint32_t>(c, "acq_dep_off", na1, &oom);
+  b.acq_dep_cnt = get<uint32_t>(c, "acq_dep_cnt", na1, &oom);
+  if (oom) return GWCP_ERR_OOM;
+
+  phaseA_scatter(b, g, z, s, c->prof);
+  phaseB_sync(b, g, z, s, c->prof);
+  cudaMemsetAsync(b.vcount, 0, size_t(g.W + 1) * 4, s);
+  cudaMemsetAsync(b.cs_of_sync, 0xFF, ns1 * 4, s);
+  phaseC_walk(b, g, z, s, c->prof);
+  phaseE_locks(b, g, z, lock_mask, s, c->prof);
+  phaseE_scan(b, z, s, c->prof);
+  {
+    const uint32_t* ex[5] = {b.incs_cnt + z.n_sync, b.vcount + g.W, b.lk_csid + z.n_acqrel,
+                             b.lk_flags + z.n_acqrel, reinterpret_cast<const uint32_t*>(&b.st->spare[1])};
+    int rc = read_status(c, s, ex, 5);
+    if (rc) return rc;
+  }
+  code = c->st_host->code;
+  if (code && code != GWCP_ERR_INVALID_TRACE) return code;
+  z.n_incs = c->cnt_host[0];
+  z.n_rows = c->cnt_host[1];
+  z.n_cs = z.n_acqrel ? c->cnt_host[2] : 0;
+  z.n_locks = z.n_acqrel ? c->cnt_host[3] : 0;
+  z.n_exp = c->cnt_host[4];
+  const uint32_t slots = std::min<uint32_t>(g.B + 1, kMaxLockScopes);
+  z.pool_cap = z.n_cs * slots + z.n_exp * 2 * slots + 64;
+  b.dep_pool = get<uint32_t>(c, "dep_pool", z.pool_cap, &oom);
+  z.race_cap = c->opt.race_capacity ? c->opt.race_capacity : std::max<uint64_t>(1u << 20, z.N);
+  // scratch for every later scan and sort (the stream is idle here, so it may move)
+  const size_t ex_bound = size_t(z.n_incs) * kMaxNest + 1;
+  const size_t need2 = std::max({scan_need, radix_tmp_need(ex_bound), radix_tmp_need(z.race_cap + 1),
+                                 scan_tmp_need(ex_bound)}) + 64;
+  b.scan_tmp = get<uint32_t>(c, "scan_tmp", need2, &oom);
+  if (oom) return GWCP_ERR_OOM;
+  phaseE_walk(b, g, z, s, c->prof);  // W3; runs on invalid traces too, for the first bad index
+  if (code == GWCP_ERR_INVALID_TRACE) {
+    int rc = read_status(c, s, nullptr, 0);
+    if (rc) return rc;
+    c->bad_index = c->st_host->bad_index;
+    return GWCP_ERR_INVALID_TRACE;
+  }
+
+  // ---- remaining buffers ------------------------------------------------------------
+  const size_t ni1 = size_t(z.n_incs) + 1;
+  b.acc_info = get<AccInfo>(c, "acc_info", z.N, &oom);
+  b.incs_idx = get<uint32_t>(c, "incs_idx", ni1, &oom);
+  b.incs_ver = get<uint32_t>(c, "incs_ver", ni1, &oom);
+  b.incs_k = get<uint32_t>(c, "incs_k", ni1, &oom);
+  b.incs_key = get<uint64_t>(c, "incs_key", ni1, &oom);
+  b.incs_wr = get<uint32_t>(c, "incs_wr", ni1, &oom);
+  b.exp_off = get<uint32_t>(c, "exp_off", ni1, &oom);
+  // expanded records: sized by the bound (depth <= kMaxNest), sorted by the exact count
+  const size_t ne1 = std::max<size_t>(size_t(z.n_exp), size_t(z.n_incs) * kMaxNest) + 1;
+  b.ex_key = get<uint64_t>(c, "ex_key", ne1, &oom);
+  b.ex_val = get<uint32_t>(c, "ex_val", ne1, &oom);
+  b.ex_key2 = get<uint64_t>(c, "ex_key2", ne1, &oom);
+  b.ex_val2 = get<uint32_t>(c, "ex_val2", ne1, &oom);
+  b.ex_rec = get<uint32_t>(c, "ex_rec", ne1, &oom);
+  b.ex_cs = get<uint32_t>(c, "ex_cs", ne1, &oom);
+  b.ex_flags = get<uint32_t>(c, "ex_flags", ne1, &oom);
+  b.ex_group = get<uint32_t>(c, "ex_group", ne1 + 1, &oom);
+  b.ex_dep_off = get<uint32_t>(c, "ex_dep_off", ne1, &oom);
+  b.ex_dep_cnt = get<uint32_t>(c, "ex_dep_cnt", ne1, &oom);
+  b.rows = get<uint32_t>(c, "rows", size_t(z.n_rows) * g.Wp, &oom);
+  b.psnap = get<uint32_t>(c, "psnap", (size_t(z.n_cs) + 1) * g.Wp, &oom);
+  b.hsnap = get<uint32_t>(c, "hsnap", (size_t(z.n_cs) + 1) * g.Wp, &oom);
+  b.done = get<uint32_t>(c, "done", size_t(z.n_cs) + 1, &oom);
+  b.cursor = get<uint32_t>(c, "cursor", size_t(g.W) * (z.n_locks + 1), &oom);
+  const size_t smem = size_t(2) * g.apb * 2 * g.Wp * 4;
+  z.cta_barriers = g.apb <= 32 && smem <= 96 * 1024;
+  const bool global_bars = !z.cta_barriers || g.gran == GWCP_GRAN_THREAD;
+  b.bar_j = get<uint32_t>(c, "bar_j", global_bars ? size_t(z.n_bar) * 2 * g.Wp : 1, &oom);
+  b.bar_cnt = get<uint32_t>(c, "bar_cnt", global_bars ? z.n_bar : 1, &oom);
+  z.n_chunks = uint32_t(check_chunks(z.n_acc));
+  const size_t ng = check_group_count(z.n_acc);
+  b.tails = get<uint32_t>(c, "tails", (size_t(z.n_chunks) + ng) * 4 * g.Wp * 2 + ng + 8, &oom);
+  b.races = get<uint64_t>(c, "races", z.race_cap, &oom);
+  b.races2 = get<uint64_t>(c, "races2", z.race_cap, &oom);
+  if (oom) return GWCP_ERR_OOM;
+  cudaMemsetAsync(b.done, 0, (size_t(z.n_cs) + 1) * 4, s);
+  cudaMemsetAsync(b.cursor, 0, size_t(g.W) * (z.n_locks + 1) * 4, s);
+  if (global_bars && z.n_bar) {
+    cudaMemsetAsync(b.bar_j, 0, size_t(z.n_bar) * 2 * g.Wp * 4, s);
+    cudaMemsetAsync(b.bar_cnt, 0, size_t(z.n_bar) * 4, s);
+  }
+
+  phaseD_gaps(b, g, z, s, c->prof);
+  phaseF_incs(b, g, z, key_mask, s, c->prof);
+  phaseF_walk(b, g, z, key_mask, s, c->prof);
+  z.n_groups = z.n_exp;  // upper bound; the kernel reads the exact count on the device
+  phaseF_deps(b, z, s, c->prof);
+  phaseH_sort(b, g, z, key_mask, s, c->prof);
+  int prc = phaseG_propagate(b, g, z, s, c->prof);
+  if (prc) return prc;
+  phaseI_check(b, g, z, s, c->prof);
+  {
+    int rc = read_status(c, s, nullptr, 0);
+    if (rc) return rc;
+  }
+  code = c->st_host->code;
+  c->bad_index = c->st_host->bad_index;
+  if (code) return code;
+  c->n_races = c->st_host->n_races;
+  c->races_second = phaseI_sort_races(b, z, c->n_races, s, c->prof);
+  c->counters[0] = z.n_acc;
+  c->counters[1] = z.n_sync;
+  c->counters[2] = z.n_cs;
+  c->counters[3] = z.n_incs;
+  c->counters[4] = z.n_rows;
+  c->counters[5] = c->st_host->partner_tests;
+  c->counters[6] = c->st_host->loop_visits;
+  c->counters[7] = c->st_host->joins;
+  return cuda_rc();
+}
+
+}  // namespace
+
+extern "C" {
+
+int gwcp_create(gwcp_ctx** out, int device, const gwcp_options* opt) {
+  if (!out) return GWCP_ERR_ARGS;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return GWCP_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return GWCP_ERR_CUDA;
+  auto* c = new gwcp_ctx();
+  c->device = device;
+  if (opt) c->opt = *opt;
+  if (cudaMallocHost(&c->st_host, sizeof(DevStatus)) != cudaSuccess ||
+      cudaMallocHost(&c->cnt_host, 16 * sizeof(uint32_t)) != cudaSuccess) {
+    gwcp_destroy(c);
+    return GWCP_ERR_OOM;
+  }
+  *out = c;
+  return GWCP_OK;
+}
+
+int gwcp_load_trace(gwcp_ctx* c, const gwcp_event* ev, uint64_t n, const gwcp_geometry* geo, int ev_is_device,
+                    void* stream) {
+  if (!c || !geo || (!ev && n)) return GWCP_ERR_ARGS;
+  if (n > kMaxEvents || geo->num_agents == 0 || geo->agents_per_block == 0 || geo->reserved != 0 ||
+      geo->num_agents % geo->agents_per_block != 0 || geo->granularity > 1)
+    return GWCP_ERR_ARGS;
+  if (geo->num_agents > kMaxAgents) return GWCP_ERR_UNSUPPORTED;
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Geo g{};
+  g.W = geo->num_agents;
+  g.apb = geo->agents_per_block;
+  g.B = g.W / g.apb;
+  g.gran = geo->granularity;
+  uint32_t k = 1;
+  while (k * 32 < g.W) k <<= 1;
+  g.K = k;
+  g.Wp = 32 * k;
+  c->g = g;
+  c->n = n;
+  c->computed = false;
+  c->compute_rc = GWCP_ERR_STATE;
+  if (ev_is_device) {
+    c->ev_dev = reinterpret_cast<const Event*>(ev);
+  } else {
+    const size_t bytes = (n ? n : 1) * sizeof(Event);
+    if (c->ev_own_cap < bytes) {
+      if (c->ev_own) cudaFree(c->ev_own);
+      c->ev_own = nullptr;
+      c->ev_own_cap = 0;
+      if (cudaMalloc(&c->ev_own, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return GWCP_ERR_OOM;
+      }
+      c->ev_own_cap = bytes;
+    }
+    if (n && cudaMemcpyAsync(c->ev_own, ev, n * sizeof(Event), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return GWCP_ERR_CUDA;
+    c->ev_dev = c->ev_own;
+  }
+  c->has_trace = true;
+  return GWCP_OK;
+}
+
+int gwcp_compute_order(gwcp_ctx* c, void* stream) {
+  if (!c) return GWCP_ERR_ARGS;
+  if (!c->has_trace) return GWCP_ERR_STATE;
+  cudaSetDevice(c->device);
+  c->bad_index = ~0ull;
+  c->n_races = 0;
+  if (c->n == 0) {
+    c->computed = true;
+    c->compute_rc = GWCP_OK;
+    std::memset(c->counters, 0, sizeof(c->counters));
+    return GWCP_OK;
+  }
+  int rc = run(c, static_cast<cudaStream_t>(stream));
+  c->computed = true;
+  c->compute_rc = rc;
+  return rc;
+}
+
+int gwcp_report_races(gwcp_ctx* c, gwcp_race* out, uint64_t cap, uint64_t* n_races, void* stream) {
+  if (!c || !n_races || (cap && !out)) return GWCP_ERR_ARGS;
+  if (!c->computed) return GWCP_ERR_STATE;
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return GWCP_ERR_CUDA;
+  *n_races = 0;
+  if (c->compute_rc) return c->compute_rc;
+  *n_races = c->n_races;
+  if (c->n_races > c->z.race_cap) return GWCP_ERR_CAPACITY;
+  const uint64_t m = std::min<uint64_t>(cap, c->n_races);
+  if (m) {
+    std::vector<uint64_t> tmp(m);
+    const uint64_t* src = c->races_second ? c->b.races2 : c->b.races;
+    if (cudaMemcpyAsync(tmp.data(), src, m * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return GWCP_ERR_CUDA;
+    for (uint64_t i = 0; i < m; ++i) {
+      out[i].later = tmp[i] >> 32;
+      out[i].earlier = tmp[i] & 0xFFFFFFFFu;
+    }
+  }
+  // profile of this compute
+  c->prof_ms.clear();
+  c->prof_bytes.clear();
+  c->prof_names.clear();
+  if (c->prof.on) {
+    for (auto& r : c->prof.recs) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      c->prof_ms.push_back(ms);
+      c->prof_bytes.push_back(r.bytes);
+      c->prof_names.push_back(r.name);
+    }
+  }
+  return cap < c->n_races ? GWCP_ERR_CAPACITY : GWCP_OK;
+}
+
+int gwcp_debug_clock(gwcp_ctx* c, uint64_t idx, int which, uint32_t* out) {
+  if (!c || !out) return GWCP_ERR_ARGS;
+  if (!c->computed || c->compute_rc) return GWCP_ERR_STATE;
+  if (idx >= c->n) return GWCP_ERR_ARGS;
+  cudaSetDevice(c->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) return GWCP_ERR_CUDA;
+  const Geo& g = c->g;
+  const Bufs& b = c->b;
+  Event e;
+  cudaMemcpy(&e, c->ev_dev + idx, sizeof(e), cudaMemcpyDeviceToHost);
+  std::vector<uint32_t> row(g.Wp);
+  uint32_t own = 0;
+  const uint32_t* src = nullptr;
+  if (e.op <= GWCP_ATOMIC) {
+    if (which != 0) return GWCP_ERR_UNSUPPORTED;
+    AccInfo inf;
+    cudaMemcpy(&inf, b.acc_info + idx, sizeof(inf), cudaMemcpyDeviceToHost);
+    src = b.rows + size_t(inf.row) * g.Wp;
+    own = inf.epoch;
+  } else if (e.op == GWCP_ACQ || e.op == GWCP_REL) {
+    uint32_t k0, k1;
+    cudaMemcpy(&k0, b.sy_start + e.agent, 4, cudaMemcpyDeviceToHost);
+    cudaMemcpy(&k1, b.sy_start + e.agent + 1, 4, cudaMemcpyDeviceToHost);
+    std::vector<uint32_t> ids(k1 - k0);
+    if (k1 > k0) cudaMemcpy(ids.data(), b.sy_idx + k0, size_t(k1 - k0) * 4, cudaMemcpyDeviceToHost);
+    auto it = std::lower_bound(ids.begin(), ids.end(), uint32_t(idx));
+    if (it == ids.end() || *it != idx) return GWCP_ERR_STATE;
+    const uint32_t k = k0 + uint32_t(it - ids.begin());
+    uint32_t N, ver, rb, cs;
+    cudaMemcpy(&N, b.sy_N + k, 4, cudaMemcpyDeviceToHost);
+    cudaMemcpy(&ver, b.sy_ver + k, 4, cudaMemcpyDeviceToHost);
+    cudaMemcpy(&rb, b.vcount + e.agent, 4, cudaMemcpyDeviceToHost);
+    cudaMemcpy(&cs, b.cs_of_sync + k, 4, cudaMemcpyDeviceToHost);
+    own = e.op == GWCP_REL ? N - 1 : N;
+    if (which == 0) {
+      src = b.rows + size_t(rb + ver) * g.Wp;
+    } else {
+      if (e.op != GWCP_REL || cs == kNoneHost) return GWCP_ERR_UNSUPPORTED;
+      src = b.hsnap + size_t(cs) * g.Wp;
+      cudaMemcpy(row.data(), src, g.Wp * 4, cudaMemcpyDeviceToHost);
+      std::memcpy(out, row.data(), g.W * 4);
+      return cuda_rc();
+    }
+  } else {
+    return GWCP_ERR_UNSUPPORTED;
+  }
+  cudaMemcpy(row.data(), src, g.Wp * 4, cudaMemcpyDeviceToHost);
+  row[e.agent] = own;
+  std::memcpy(out, row.data(), g.W * 4);
+  return cuda_rc();
+}
+
+uint64_t gwcp_first_bad_index(const gwcp_ctx* c) { return c ? c->bad_index : ~0ull; }
+
+uint64_t gwcp_launch_count(void) { return gwcp::launch_count(); }
+
+int gwcp_profile_get(const gwcp_ctx* c, int i, const char** name, float* ms, double* bytes) {
+  if (!c || i < 0 || size_t(i) >= c->prof_ms.size()) return GWCP_ERR_ARGS;
+  if (name) *name = c->prof_names[i];
+  if (ms) *ms = c->prof_ms[i];
+  if (bytes) *bytes = c->prof_bytes[i];
+  return GWCP_OK;
+}
+
+int gwcp_counters(const gwcp_ctx* c, uint64_t* out8) {
+  if (!c || !out8) return GWCP_ERR_ARGS;
+  std::memcpy(out8, c->counters, sizeof(c->counters));
+  return GWCP_OK;
+}
+
+void gwcp_destroy(gwcp_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  for (auto& kv : c->allocs)
+    if (kv.second.first) cudaFree(kv.second.first);
+  if (c->ev_own) cudaFree(c->ev_own);
+  if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->cnt_host) cudaFreeHost(c->cnt_host);
+  for (auto e : c->prof.pool) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* gwcp_strerror(int code) {
+  switch (code) {
+    case GWCP_OK: return "ok";
+    case GWCP_ERR_INVALID_TRACE: return "invalid trace (see gwcp_first_bad_index)";
+    case GWCP_ERR_OOM: return "out of device memory";
+    case GWCP_ERR_CUDA: return "CUDA error";
+    case GWCP_ERR_CAPACITY: return "race buffer too small";
+    case GWCP_ERR_TIMEOUT: return "a bounded device wait gave up";
+    case GWCP_ERR_STATE: return "calls out of order";
+    case GWCP_ERR_ARGS: return "invalid arguments";
+    case GWCP_ERR_UNSUPPORTED: return "unsupported size or configuration";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,338 @@
+// Access grouping and the per-location race check of libgwcp.
+//
+// Accesses are sorted by (location key, trace index) with the library's radix sort,
+// then cut into fixed chunks of CH entries; one warp checks one chunk in order. The
+// warp keeps, for every agent v (lane l owns agents [l*K, l*K+K)) and access class
+// (read, write, block-scoped atomic, device-scoped atomic), the latest access by v to
+// the current location as (index << 32 | epoch) - the R_x / W_x state of the paper's
+// metadata, kept per agent. For an access b by u every lane forms, for each of its
+// agents v != u, a* = the latest access of v that conflicts with b and is not exempt,
+// and reports (a*, b) when N(a*) > C_b[v], reading C_b[v] from the clock-version row
+// of b written by the propagation. A location that spans chunks carries the state in:
+// per chunk the state of its last location is reduced, then a segmented max-scan over
+// chunks (two levels) gives each chunk the state at its start.
+#include "gwcp_internal.cuh"
+
+namespace gwcp {
+
+namespace {
+
+constexpr uint32_t CH = 512;       // accesses per chunk (one warp)
+constexpr uint32_t GRP = 32;       // chunks per first-level scan group
+constexpr int CHK_WARPS = 4;
+
+__device__ __forceinline__ bool is_atomic_cls(uint32_t c) { return c >= C_ATOM_CTA; }
+
+// conflict and not exempt: at least one write-class access, and not two atomics with
+// overlapping scopes (same block, or either device-scoped)
+__device__ __forceinline__ bool counts(uint32_t ca, uint32_t cb, bool same_block) {
+  if (ca == C_READ && cb == C_READ) return false;
+  if (is_atomic_cls(ca) && is_atomic_cls(cb) && (ca == C_ATOM_DEV || cb == C_ATOM_DEV || same_block)) return false;
+  return true;
+}
+
+struct ChunkArgs {
+  const uint64_t* key;
+  const uint32_t* idx;
+  const AccInfo* info;
+  uint32_t n;
+  uint32_t n_chunks;
+  uint64_t* T;          // [n_chunks][4 * Wp] packed (index << 32 | epoch), 0 = none
+  const uint32_t* rows;
+  uint64_t* races;
+  uint64_t race_cap;
+  DevStatus* st;
+  Geo g;
+};
+
+__device__ __forceinline__ bool chunk_continues(const ChunkArgs& a, uint32_t c) {
+  // the last location of chunk c goes on into chunk c + 1
+  if (c + 1 >= a.n_chunks) return false;
+  const uint32_t e = (c + 1) * CH;
+  return a.key[e - 1] == a.key[e];
+}
+
+// State of the chunk's last location over the chunk's entries.
+template <int K>
+__global__ void k_tail(ChunkArgs a) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= a.n_chunks) return;
+  const uint32_t Wp = a.g.Wp;
+  uint64_t* T = a.T + size_t(c) * 4 * Wp;
+  uint64_t last[4][K];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int j = 0; j < K; ++j) last[q][j] = 0;
+  if (chunk_continues(a, c)) {
+    const uint32_t lo = c * CH, hi = min(lo + CH, a.n);
+    const uint64_t tk = a.key[hi - 1];
+    for (uint32_t b0 = lo; b0 < hi; b0 += 32) {
+      const uint32_t p = b0 + lane;
+      uint64_t k = ~0ull;
+      AccInfo inf{};
+      uint32_t ix = 0;
+      if (p < hi) {
+        k = a.key[p];
+        ix = a.idx[p];
+        inf = a.info[ix];
+      }
+      const uint32_t nb = min(32u, hi - b0);
+      for (uint32_t i = 0; i < nb; ++i) {
+        if (__shfl_sync(0xffffffffu, k, i) != tk) continue;
+        const uint32_t ag = __shfl_sync(0xffffffffu, inf.agent, i);
+        const uint64_t v = (uint64_t(__shfl_sync(0xffffffffu, ix, i)) << 32) |
+                           __shfl_sync(0xffffffffu, inf.epoch, i);
+        const uint32_t cl = __shfl_sync(0xffffffffu, inf.cls, i);
+        if (uint32_t(lane) == ag / K) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+              if (q == int(cl) && j == int(ag % K)) last[q][j] = v;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int j = 0; j < K; ++j) T[q * Wp + lane * K + j] = last[q][j];
+}
+
+// links for the segmented scan: chunk c folds in chunk c-1's prefix when chunk c-1
+// continues into c and chunk c holds only that location
+__device__ __forceinline__ bool linked(const ChunkArgs& a, uint32_t c) {
+  if (c == 0 || !chunk_continues(a, c - 1)) return false;
+  const uint32_t lo = c * CH, hi = min(lo + CH, a.n);
+  return a.key[lo] == a.key[hi - 1];
+}
+
+__global__ void k_scan1(ChunkArgs a, uint64_t* gagg, uint32_t* gfull) {
+  const uint32_t cols = 4 * a.g.Wp;
+  const uint32_t g0 = blockIdx.x * GRP, g1 = min(g0 + GRP, a.n_chunks);
+  bool full = linked(a, g0);
+  for (uint32_t c = g0 + 1; c < g1; ++c) full = full && linked(a, c);
+  for (uint32_t col = threadIdx.x; col < cols; col += blockDim.x) {
+    uint64_t acc = 0;
+    for (uint32_t c = g0; c < g1; ++c) {
+      uint64_t v = a.T[size_t(c) * cols + col];
+      acc = (c > g0 && linked(a, c)) ? max(acc, v) : v;
+      a.T[size_t(c) * cols + col] = acc;
+    }
+    gagg[size_t(blockIdx.x) * cols + col] = acc;
+  }
+  if (threadIdx.x == 0) gfull[blockIdx.x] = full;
+}
+
+__global__ void k_scan2(ChunkArgs a, uint32_t ngroups, uint64_t* gagg, const uint32_t* gfull) {
+  // gagg[g] becomes the carry into group g
+  const uint32_t cols = 4 * a.g.Wp;
+  const uint32_t col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= cols) return;
+  uint64_t prev_final = 0;
+  for (uint32_t gi = 0; gi < ngroups; ++gi) {
+    const uint64_t agg = gagg[size_t(gi) * cols + col];
+    const bool lk = linked(a, gi * GRP);
+    const uint64_t carry = lk ? prev_final : 0;
+    prev_final = gfull[gi] ? max(prev_final, agg) : agg;
+    gagg[size_t(gi) * cols + col] = carry;
+  }
+}
+
+__global__ void k_scan3(ChunkArgs a, const uint64_t* gagg) {
+  const uint32_t cols = 4 * a.g.Wp;
+  const uint32_t g0 = blockIdx.x * GRP, g1 = min(g0 + GRP, a.n_chunks);
+  for (uint32_t col = threadIdx.x; col < cols; col += blockDim.x) {
+    const uint64_t carry = gagg[size_t(blockIdx.x) * cols + col];
+    if (!carry) continue;
+    for (uint32_t c = g0; c < g1 && linked(a, c); ++c) {
+      uint64_t& v = a.T[size_t(c) * cols + col];
+      v = max(v, carry);
+    }
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(CHK_WARPS * 32) k_check(ChunkArgs a) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= a.n_chunks) return;
+  const Geo& g = a.g;
+  const uint32_t Wp = g.Wp;
+  const uint32_t lo = c * CH, hi = min(lo + CH, a.n);
+  uint64_t last[4][K];
+  uint64_t cur_key;
+  if (c > 0 && chunk_continues(a, c - 1)) {
+    const uint64_t* T = a.T + size_t(c - 1) * 4 * Wp;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int j = 0; j < K; ++j) last[q][j] = T[q * Wp + lane * K + j];
+    cur_key = a.key[lo];
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int j = 0; j < K; ++j) last[q][j] = 0;
+    cur_key = a.key[lo];
+  }
+  uint32_t myblk[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) myblk[j] = (lane * K + j) / g.apb;
+  uint64_t tests = 0;
+  for (uint32_t b0 = lo; b0 < hi; b0 += 32) {
+    const uint32_t p = b0 + lane;
+    uint64_t k = ~0ull;
+    AccInfo inf{};
+    uint32_t ix = 0;
+    if (p < hi) {
+      k = a.key[p];
+      ix = a.idx[p];
+      inf = a.info[ix];
+    }
+    const uint32_t nb = min(32u, hi - b0);
+    for (uint32_t i = 0; i < nb; ++i) {
+      const uint64_t kb = __shfl_sync(0xffffffffu, k, i);
+      const uint32_t ib = __shfl_sync(0xffffffffu, ix, i);
+      const uint32_t eb = __shfl_sync(0xffffffffu, inf.epoch, i);
+      const uint32_t rowb = __shfl_sync(0xffffffffu, inf.row, i);
+      const uint32_t ub = __shfl_sync(0xffffffffu, inf.agent, i);
+      const uint32_t cb = __shfl_sync(0xffffffffu, inf.cls, i);
+      if (kb != cur_key) {
+        cur_key = kb;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int j = 0; j < K; ++j) last[q][j] = 0;
+      }
+      const uint32_t bu = ub / g.apb;
+      uint64_t best[K];
+      bool any = false;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        best[j] = 0;
+        const uint32_t v = lane * K + j;
+        if (v == ub) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (counts(uint32_t(q), cb, myblk[j] == bu)) best[j] = max(best[j], last[q][j]);
+        any |= best[j] != 0;
+      }
+      uint32_t nr = 0;
+      uint64_t out[K];
+      if (any) {
+        uint32_t cv[K];
+        const uint32_t* row = a.rows + size_t(rowb) * Wp + lane * K;
+#pragma unroll
+        for (int j = 0; j < K; ++j) cv[j] = __ldg(row + j);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          if (!best[j]) continue;
+          ++tests;
+          if (uint32_t(best[j]) > cv[j]) out[nr++] = (uint64_t(ib) << 32) | (best[j] >> 32);
+        }
+      }
+      const uint32_t tot = __reduce_add_sync(0xffffffffu, nr);
+      if (tot) {
+        const uint32_t before = warp_inclusive_scan(nr) - nr;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&a.st->n_races, (unsigned long long)tot);
+        base = __shfl_sync(0xffffffffu, base, 0) + before;
+        for (uint32_t q = 0; q < nr; ++q)
+          if (base + q < a.race_cap) a.races[base + q] = out[q];
+      }
+      if (uint32_t(lane) == ub / K) {
+        const uint64_t v = (uint64_t(ib) << 32) | eb;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int j = 0; j < K; ++j)
+            if (q == int(cb) && j == int(ub % K)) last[q][j] = v;
+      }
+    }
+  }
+  tests = __reduce_add_sync(0xffffffffu, uint32_t(tests));
+  if (lane == 0 && tests) atomicAdd(&a.st->partner_tests, (unsigned long long)tests);
+}
+
+inline uint32_t blocks(uint64_t n, uint32_t t) { return uint32_t((n + t - 1) / t); }
+
+template <int K>
+void run_check(const ChunkArgs& a, uint64_t* gagg, uint32_t* gfull, cudaStream_t s, Prof& p, double bytes_per) {
+  const uint32_t nw = a.n_chunks;
+  const uint32_t cols = 4 * a.g.Wp;
+  const uint32_t ng = blocks(nw, GRP);
+  p.begin("i_carry", double(nw) * cols * 8 * 3);
+  k_tail<K><<<blocks(uint64_t(nw) * 32, CHK_WARPS * 32), CHK_WARPS * 32, 0, s>>>(a);
+  count_launch();
+  k_scan1<<<ng, 256, 0, s>>>(a, gagg, gfull);
+  count_launch();
+  k_scan2<<<blocks(cols, 256), 256, 0, s>>>(a, ng, gagg, gfull);
+  count_launch();
+  k_scan3<<<ng, 256, 0, s>>>(a, gagg);
+  count_launch();
+  p.end();
+  p.begin("i_check", double(a.n) * bytes_per);
+  k_check<K><<<blocks(uint64_t(nw) * 32, CHK_WARPS * 32), CHK_WARPS * 32, 0, s>>>(a);
+  count_launch();
+  p.end();
+}
+
+}  // namespace
+
+size_t check_chunks(uint32_t n_acc) { return (n_acc + CH - 1) / CH; }
+size_t check_group_count(uint32_t n_acc) { return (check_chunks(n_acc) + GRP - 1) / GRP; }
+
+void phaseH_sort(Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, cudaStream_t s, Prof& p) {
+  (void)g;
+  p.begin("h_sort", double(z.n_acc) * 12 * 2 * radix_windows(key_mask).size());
+  if (radix_sort_pairs(b.acc_key, b.acc_idx, b.acc_key2, b.acc_idx2, z.n_acc, key_mask, b.scan_tmp, s)) {
+    std::swap(b.acc_key, b.acc_key2);
+    std::swap(b.acc_idx, b.acc_idx2);
+  }
+  p.end();
+}
+
+void phaseI_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
+  if (!z.n_acc) return;
+  ChunkArgs a{};
+  a.key = b.acc_key;
+  a.idx = b.acc_idx;
+  a.info = b.acc_info;
+  a.n = z.n_acc;
+  a.n_chunks = z.n_chunks;
+  a.T = reinterpret_cast<uint64_t*>(b.tails);
+  a.rows = b.rows;
+  a.races = b.races;
+  a.race_cap = z.race_cap;
+  a.st = b.st;
+  a.g = g;
+  uint64_t* gagg = a.T + size_t(z.n_chunks) * 4 * g.Wp;
+  uint32_t* gfull = reinterpret_cast<uint32_t*>(gagg + size_t(check_group_count(z.n_acc)) * 4 * g.Wp);
+  // per access: sorted key + index (12 B), its record (16 B), its clock-version row
+  const double per = 12.0 + 16.0 + 4.0 * g.Wp;
+  switch (g.K) {
+    case 1: run_check<1>(a, gagg, gfull, s, p, per); break;
+    case 2: run_check<2>(a, gagg, gfull, s, p, per); break;
+    case 4: run_check<4>(a, gagg, gfull, s, p, per); break;
+    case 8: run_check<8>(a, gagg, gfull, s, p, per); break;
+    case 16: run_check<16>(a, gagg, gfull, s, p, per); break;
+    case 32: run_check<32>(a, gagg, gfull, s, p, per); break;
+  }
+}
+
+bool phaseI_sort_races(const Bufs& b, const Sizes& z, uint64_t n_races, cudaStream_t s, Prof& p) {
+  const uint64_t n = n_races < z.race_cap ? n_races : z.race_cap;
+  if (n <= 1) return false;
+  uint64_t mask = 0;
+  for (uint64_t v = z.N; v; v >>= 1) mask = (mask << 1) | 1;
+  mask |= mask << 32;
+  p.begin("i_race_sort", double(n) * 8 * 2);
+  bool second = radix_sort_pairs(b.races, nullptr, b.races2, nullptr, n, mask, b.scan_tmp, s);
+  p.end();
+  return second;
+}
+
+}  // namespace gwcp

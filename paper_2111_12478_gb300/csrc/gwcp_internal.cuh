@@ -1,0 +1,298 @@
+// Internal declarations of libgwcp (device buffers, kernels, launch helpers).
+// Shared only among the library's own translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "gwcp.h"
+
+namespace gwcp {
+
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr int kMaxNest = 4;         // deepest lockset a valid trace may hold
+constexpr uint32_t kMaxAgents = 1024;
+constexpr uint32_t kMaxEvents = (1u << 30) - 1;
+constexpr int kMaxLockScopes = 64;  // distinct scope ids one lock may be used with
+
+// S entry kinds (agent-sorted event stream), packed as (kind << 30) | trace index
+enum : uint32_t { K_ACCESS = 0, K_ACQ = 1, K_REL = 2, K_BAR = 3 };
+__host__ __device__ inline uint32_t s_kind(uint32_t s) { return s >> 30; }
+__host__ __device__ inline uint32_t s_idx(uint32_t s) { return s & 0x3FFFFFFFu; }
+
+// access classes
+enum : uint32_t { C_READ = 0, C_WRITE = 1, C_ATOM_CTA = 2, C_ATOM_DEV = 3 };
+
+struct Event {
+  uint32_t agent;
+  uint8_t op, scope, space, flags;
+  uint64_t addr;
+};
+
+// Device-side status and counters (one per context).
+struct DevStatus {
+  int code;                      // GWCP_OK or a GWCP_ERR_*
+  int pad;
+  unsigned long long bad_index;  // first offending event (atomicMin)
+  unsigned long long key_or, key_and;    // over access location keys
+  unsigned long long lock_or, lock_and;  // over acquire/release lock ids
+  unsigned long long n_races;            // races found (may exceed the buffer)
+  unsigned long long dep_pool_used;
+  unsigned long long partner_tests;
+  unsigned long long loop_visits;
+  unsigned long long joins;
+  unsigned long long spare[6];
+};
+
+struct Geo {
+  uint32_t W, apb, B, gran, Wp, K;  // Wp = W rounded up to 32, K = Wp / 32
+};
+
+// Per-access record consumed by the check (indexed by trace index).
+struct AccInfo {
+  uint32_t epoch;  // N_t of the access
+  uint32_t row;    // global clock-version row holding P_t for the access
+  uint32_t agent;
+  uint32_t cls;    // C_READ ... C_ATOM_DEV
+};
+
+// All device buffers of one analysis. Sizes in comments.
+struct Bufs {
+  const Event* ev = nullptr;  // [N]
+  DevStatus* st = nullptr;
+  // phase A: agent counting sort, trace-order compactions
+  uint32_t* hist_a = nullptr;    // [W * ntA + 1]
+  uint32_t* tile_cnt = nullptr;  // [3 * ntA + 3]: accesses, acq/rel, barriers per tile
+  uint32_t* S = nullptr;         // [nS]
+  uint32_t* seg = nullptr;       // [W + 1] start of each agent's segment in S
+  uint32_t* acqrel = nullptr;    // [n_acqrel] trace indices
+  uint32_t* bar = nullptr;       // [n_bar] trace indices
+  uint64_t* acc_key = nullptr;   // [n_acc] (+ alt)
+  uint32_t* acc_idx = nullptr;   // [n_acc] (+ alt)
+  uint64_t* acc_key2 = nullptr;
+  uint32_t* acc_idx2 = nullptr;
+  // phase B: sync list
+  uint32_t* sy_cnt = nullptr;   // [ntS + 1]
+  uint32_t* sy_spos = nullptr;  // [n_sync]
+  uint32_t* sy_idx = nullptr;   // [n_sync]
+  uint32_t* sy_kind = nullptr;  // [n_sync]
+  uint32_t* sy_start = nullptr; // [W + 1]
+  uint32_t* sy_aux = nullptr;   // [n_sync] barrier ordinal for barrier entries
+  // phase C: per-agent sync walk
+  uint32_t* sy_N = nullptr;      // epoch after the entry
+  uint32_t* sy_depth = nullptr;  // lock depth after the entry
+  uint32_t* sy_inner = nullptr;  // sync ordinal of the innermost open acquire after it
+  uint32_t* sy_ver = nullptr;    // version index after the entry
+  uint32_t* sy_match = nullptr;  // REL: its acquire; ACQ: the enclosing acquire
+  uint32_t* sy_relk = nullptr;   // ACQ: the matching release (NONE if never released)
+  uint32_t* incs_cnt = nullptr;  // [n_sync + 1] in-section accesses in the gap after k
+  uint32_t* vcount = nullptr;    // [W + 1] versions per agent -> row base (scanned)
+  // phase D: accesses
+  AccInfo* acc_info = nullptr;   // [N]
+  uint32_t* incs_idx = nullptr;  // [n_incs]
+  uint32_t* incs_ver = nullptr;
+  uint32_t* incs_k = nullptr;    // sync ordinal of the gap the access lies in
+  uint64_t* incs_key = nullptr;
+  uint32_t* incs_wr = nullptr;
+  // phase E: locks and critical sections
+  uint64_t* lk_key = nullptr;  // [n_acqrel] (+ alt)
+  uint32_t* lk_k = nullptr;
+  uint64_t* lk_key2 = nullptr;
+  uint32_t* lk_k2 = nullptr;
+  uint32_t* lk_flags = nullptr;    // [n_acqrel + 1] scan scratch
+  uint32_t* lk_csid = nullptr;     // [n_acqrel + 1]
+  uint32_t* lk_rank = nullptr;     // [n_acqrel + 1]
+  uint32_t* lock_first = nullptr;  // [n_locks + 1] first sorted entry of each lock
+  uint32_t* lock_cs_lo = nullptr;  // [n_locks + 1]
+  uint32_t* cs_of_sync = nullptr;  // [n_sync]
+  uint32_t* cs_agent = nullptr;    // [n_cs]
+  uint32_t* cs_sid = nullptr;
+  uint32_t* cs_epoch = nullptr;
+  uint32_t* cs_rel_idx = nullptr;
+  uint32_t* cs_lock = nullptr;
+  uint32_t* cs_parent = nullptr;
+  uint32_t* acq_dep_off = nullptr;  // [n_cs]
+  uint32_t* acq_dep_cnt = nullptr;
+  uint32_t* dep_pool = nullptr;     // [pool_cap]
+  // phase F: in-section dependencies
+  uint32_t* exp_off = nullptr;   // [n_incs + 1]
+  uint64_t* ex_key = nullptr;    // [n_exp] (+ alt)
+  uint32_t* ex_val = nullptr;
+  uint64_t* ex_key2 = nullptr;
+  uint32_t* ex_val2 = nullptr;
+  uint32_t* ex_rec = nullptr;    // [n_exp] in-section record of each expanded record
+  uint32_t* ex_cs = nullptr;     // [n_exp] held critical section
+  uint32_t* ex_flags = nullptr;  // [n_exp + 1]
+  uint32_t* ex_group = nullptr;  // [n_groups + 1]
+  uint32_t* ex_dep_off = nullptr;  // [n_exp]
+  uint32_t* ex_dep_cnt = nullptr;
+  // phase G: propagation
+  uint32_t* rows = nullptr;     // [n_rows * Wp]
+  uint32_t* psnap = nullptr;    // [n_cs * Wp]
+  uint32_t* hsnap = nullptr;    // [n_cs * Wp]
+  uint32_t* done = nullptr;     // [n_cs]
+  uint32_t* cursor = nullptr;   // [W * n_locks]
+  uint32_t* bar_j = nullptr;    // [n_bar * 2 * Wp] global-barrier joins
+  uint32_t* bar_cnt = nullptr;  // [n_bar]
+  // phase I: check
+  uint32_t* tails = nullptr;    // [n_chunks * 4 * Wp * 2]
+  uint64_t* races = nullptr;    // [race_cap] (later << 32) | earlier
+  uint64_t* races2 = nullptr;
+  // scan scratch
+  uint32_t* scan_tmp = nullptr;
+  size_t scan_tmp_elems = 0;
+};
+
+// ---- primitives (gwcp_prims.cu) ----------------------------------------------------
+// Process-wide count of kernels this library has launched (gwcp_launch_count).
+void count_launch();
+// Exclusive scan of n u32 values (in may equal out); writes the total to *total_dev
+// when non-null. tmp must hold scan_tmp_need(n) elements.
+size_t scan_tmp_need(size_t n);
+void scan_exclusive(const uint32_t* in, uint32_t* out, size_t n, uint32_t* total_dev, uint32_t* tmp,
+                    cudaStream_t s);
+// Stable LSD radix sort of (key, val) pairs on the bits set in `mask`, 8-bit digits.
+// Ping-pongs between (k0, v0) and (k1, v1); returns true if the result is in (k1, v1).
+// tmp must hold radix_tmp_need(n) u32.
+size_t radix_tmp_need(size_t n);
+bool radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, size_t n, uint64_t mask,
+                      uint32_t* tmp, cudaStream_t s);
+// Digit windows covering the bits of `mask` (low bit of each window).
+std::vector<int> radix_windows(uint64_t mask);
+
+// ---- device helpers -----------------------------------------------------------------
+__device__ __forceinline__ void set_error(DevStatus* st, int code, unsigned long long idx) {
+  atomicCAS(&st->code, 0, code);
+  atomicMin(&st->bad_index, idx);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+// Location key of an access: shared memory is per block (reading of the paper's
+// shared-memory paragraph): (1 << 63) | (block << 40) | addr.
+__device__ __forceinline__ uint64_t location_key(const Event& e, uint32_t apb) {
+  if (e.space == GWCP_SPACE_SHARED) return (1ull << 63) | (uint64_t(e.agent / apb) << 40) | e.addr;
+  return e.addr;
+}
+
+__device__ __forceinline__ uint32_t access_class(const Event& e) {
+  if (e.op == GWCP_READ) return C_READ;
+  if (e.op == GWCP_WRITE) return C_WRITE;
+  return e.scope == GWCP_SCOPE_DEVICE ? C_ATOM_DEV : C_ATOM_CTA;
+}
+
+// scope id of a lock use: 0 device, block + 1 block-scoped
+__device__ __forceinline__ uint32_t scope_id(uint32_t agent, uint8_t scope, uint32_t apb) {
+  return scope == GWCP_SCOPE_DEVICE ? 0u : agent / apb + 1u;
+}
+__host__ __device__ __forceinline__ bool scopes_overlap(uint32_t a, uint32_t b) {
+  return a == 0 || b == 0 || a == b;
+}
+
+// Members of a barrier event: first member and count, contiguous except WARP masks at
+// thread granularity (then `mask` has the lane bits relative to `first`).
+struct BarMembers {
+  uint32_t first, count, mask;  // mask == 0 means the contiguous range [first, first+count)
+  bool ok;
+};
+__device__ __forceinline__ BarMembers barrier_members(const Event& e, const Geo& g) {
+  BarMembers m{0, 0, 0, false};
+  if (e.scope == GWCP_SCOPE_CTA) {
+    if (e.addr >= g.B) return m;
+    m.first = uint32_t(e.addr) * g.apb;
+    m.count = g.apb;
+    m.ok = true;
+    return m;
+  }
+  if (e.scope == GWCP_SCOPE_WARP) {
+    if (e.addr == 0 || e.addr > 0xffffffffull) return m;
+    if (g.gran == GWCP_GRAN_WARP) {
+      m.first = e.agent;
+      m.count = 1;
+      m.ok = true;
+      return m;
+    }
+    uint32_t blk = e.agent / g.apb;
+    uint32_t base = blk * g.apb + ((e.agent - blk * g.apb) / 32u) * 32u;
+    uint32_t mask = uint32_t(e.addr);
+    uint32_t hi = 31 - __clz(mask);
+    if (base + hi >= (blk + 1) * g.apb) return m;
+    m.first = base;
+    m.count = __popc(mask);
+    m.mask = mask;
+    m.ok = true;
+  }
+  return m;
+}
+
+// ---- launchers (defined in the phase files) -----------------------------------------
+struct Sizes {
+  uint64_t N = 0;
+  uint32_t ntA = 0, TA = 0;
+  uint32_t nS = 0, n_acc = 0, n_acqrel = 0, n_bar = 0;
+  uint32_t ntS = 0;
+  uint32_t n_sync = 0, n_incs = 0, n_rows = 0, n_cs = 0, n_locks = 0, n_exp = 0, n_groups = 0;
+  uint32_t pool_cap = 0;
+  uint32_t n_chunks = 0;
+  uint64_t race_cap = 0;
+  bool cta_barriers = false;  // every block fits one CTA of walkers
+};
+
+// profiling hook: records an event pair around each launch when enabled
+struct Prof {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  struct Rec {
+    const char* name;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  cudaEvent_t ev();
+  void begin(const char* name, double bytes);
+  void end();
+};
+
+void phaseA_count(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
+void phaseA_scatter(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
+void phaseB_sync(const Bufs& b, const Geo& g, Sizes& z, cudaStream_t s, Prof& p);
+void phaseC_walk(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
+void phaseD_gaps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
+void phaseE_locks(Bufs& b, const Geo& g, const Sizes& z, uint64_t lock_mask, cudaStream_t s, Prof& p);
+void phaseE_walk(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
+void phaseF_incs(const Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, cudaStream_t s, Prof& p);
+void phaseF_walk(Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, cudaStream_t s, Prof& p);
+int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
+void phaseH_sort(Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, cudaStream_t s, Prof& p);
+void phaseI_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
+bool phaseI_sort_races(const Bufs& b, const Sizes& z, uint64_t n_races, cudaStream_t s, Prof& p);
+
+}  // namespace gwcp

@@ -1,0 +1,180 @@
+"""CUDA path vs the CPU oracle, through the C ABI (needs a GB300).
+
+Race sets must be identical (integer work: bit-exact). Clock rows are compared at
+sampled events through gwcp_debug_clock. Invalid traces must fail with the oracle's
+first bad index.
+"""
+import numpy as np
+import pytest
+
+from conftest import GOLDEN_FILES, load_golden
+from oracle import oracle as O
+from paper_2111_12478_gb300 import tracegen as TG
+from paper_2111_12478_gb300.tracegen import ACQ, ATOMIC, BARRIER, CTA, DEVICE, READ, REL, THREAD, WARP_GRAN, WRITE
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2111_12478_gb300 import gwcp
+
+    c = gwcp.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_races(ctx, ev, geo):
+    ctx.load_trace(ev, *geo.astuple())
+    ctx.compute_order()
+    return ctx.report_races()
+
+
+def same(ctx, ev, geo):
+    got = gpu_races(ctx, ev, geo)
+    want = O.run(ev, *geo.astuple()).races
+    assert got.shape == want.shape, (len(got), len(want))
+    assert np.array_equal(got, want)
+    return got
+
+
+@pytest.mark.parametrize("name", GOLDEN_FILES)
+def test_figures(ctx, name):
+    ev, geo, expect = load_golden(name)
+    got = gpu_races(ctx, ev, geo)
+    assert {(int(a), int(b)) for a, b in got} == expect
+
+
+@pytest.mark.parametrize("fam", TG.FAMILIES)
+def test_random_families(ctx, fam):
+    for seed in range(30):
+        for W, apb, gran in [(4, 2, THREAD), (6, 3, THREAD), (8, 8, WARP_GRAN), (64, 64, THREAD), (40, 8, WARP_GRAN)]:
+            ev, geo = TG.random_small(seed, fam, n_events=120, num_agents=W, agents_per_block=apb,
+                                      granularity=gran, n_locks=3, n_keys=5)
+            same(ctx, ev, geo)
+
+
+def test_clock_rows_match_oracle(ctx):
+    for seed in range(6):
+        ev, geo = TG.random_small(seed, "mixed", n_events=200, num_agents=8, agents_per_block=4, n_locks=3,
+                                  n_keys=4)
+        idx = [i for i in range(len(ev)) if ev["op"][i] in (READ, WRITE, ATOMIC, ACQ, REL)]
+        r = O.run(ev, *geo.astuple(), clock_events=idx)
+        gpu_races(ctx, ev, geo)
+        for i in idx:
+            c = ctx.debug_clock(i, 0, geo.num_agents)
+            assert np.array_equal(c, r.clocks_c[i]), (seed, i)
+            if ev["op"][i] == REL:
+                h = ctx.debug_clock(i, 1, geo.num_agents)
+                assert np.array_equal(h, r.clocks_h[i]), (seed, i)
+
+
+def test_edge_cases(ctx):
+    geo = TG.Geometry(4, 2, THREAD)
+    assert len(gpu_races(ctx, np.zeros(0, dtype=TG.EVENT_DTYPE), geo)) == 0
+    b = TG.TraceBuilder()
+    b.wr(0, 0x10)
+    same(ctx, b.build(), geo)                                   # one access
+    b = TG.TraceBuilder()
+    b.acq(0, 1); b.rel(0, 1); b.barrier(0, agent=0); b.fence(1)
+    same(ctx, b.build(), geo)                                   # no accesses
+    b = TG.TraceBuilder()
+    for k in range(4):
+        b.acq(0, k)
+    b.wr(0, 0x20); b.wr(1, 0x20)
+    for k in reversed(range(4)):
+        b.rel(0, k)
+    b.acq(1, 2); b.rd(1, 0x20)                                  # depth 4, open section at the end
+    same(ctx, b.build(), geo)
+    ev, geo1 = TG.random_small(1, "mixed", n_events=80, num_agents=1, agents_per_block=1)
+    same(ctx, ev, geo1)                                         # one agent
+    ev, geo2 = TG.random_small(2, "mixed", n_events=200, num_agents=16, agents_per_block=1, granularity=WARP_GRAN)
+    same(ctx, ev, geo2)                                         # one agent per block
+
+
+@pytest.mark.parametrize("W,apb,gran", [(1024, 32, WARP_GRAN), (256, 16, WARP_GRAN), (96, 96, THREAD),
+                                        (128, 64, THREAD)])
+def test_wide_clocks(ctx, W, apb, gran):
+    ev, geo = TG.random_small(7, "mixed", n_events=3000, num_agents=W, agents_per_block=apb, granularity=gran,
+                              n_locks=6, n_keys=12)
+    same(ctx, ev, geo)
+
+
+def test_invalid_traces_first_bad_index(ctx):
+    from paper_2111_12478_gb300 import gwcp
+
+    cases = [
+        [(0, ACQ, DEVICE, 0, 0, 1), (9, READ, 0, 0, 0, 1)],                         # W1
+        [(0, REL, DEVICE, 0, 0, 1)],                                                 # W2
+        [(0, ACQ, DEVICE, 0, 0, 1), (0, ACQ, DEVICE, 0, 0, 2), (0, REL, DEVICE, 0, 0, 1)],
+        [(0, ACQ, DEVICE, 0, 0, 1), (2, ACQ, CTA, 0, 0, 1), (0, 7, 0, 0, 0, 0)],     # W3 before W1
+        [(0, ACQ, CTA, 0, 0, 1), (1, ACQ, CTA, 0, 0, 1), (1, REL, DEVICE, 0, 0, 5)],  # W3 before W2
+        [(0, ACQ, DEVICE, 0, 0, k) for k in range(5)],                               # nesting > 4
+        [(0, BARRIER, CTA, 0, 0, 7)],
+    ]
+    for rows in cases:
+        ev = np.zeros(len(rows), dtype=TG.EVENT_DTYPE)
+        for i, r in enumerate(rows):
+            ev[i] = r
+        rc, bad = O.validate(ev, 4, 2, THREAD)
+        assert rc == O.ERR_INVALID_TRACE
+        ctx.load_trace(ev, 4, 2, THREAD)
+        with pytest.raises(gwcp.GwcpError) as ei:
+            ctx.compute_order()
+        assert ei.value.code == gwcp.ERR_INVALID_TRACE
+        assert ei.value.bad_index == bad, rows
+
+
+def test_tiny_workload(ctx):
+    for seed in (1, 2, 3):
+        ev, geo, planted = TG.generate(seed, workload="tiny_1blk_64thr_10k")
+        got = same(ctx, ev, geo)
+        assert set(planted.tolist()) <= set(got.ravel().tolist())
+
+
+@pytest.mark.parametrize("n,seed", [(200_000, 1), (200_000, 2), (1_000_000, 3)])
+def test_warp_workload_scaled(ctx, n, seed):
+    ev, geo, _ = TG.generate(seed, n_events=n, workload="8blk_64warp_10M")
+    same(ctx, ev, geo)
+
+
+def test_warp_workload_full_10M(ctx):
+    """The 8-block, 64-warp, 10M-event workload at full size: the whole race set."""
+    ev, geo, planted = TG.generate(1, workload="8blk_64warp_10M")
+    got = same(ctx, ev, geo)
+    pl = set(planted.tolist())
+    assert all(int(a) in pl or int(b) in pl for a, b in got)
+
+
+def test_capacity_and_determinism(ctx):
+    from paper_2111_12478_gb300 import gwcp
+
+    ev, geo, _ = TG.generate(4, n_events=100_000, workload="8blk_64warp_10M")
+    a = gpu_races(ctx, ev, geo)
+    b = gpu_races(ctx, ev, geo)
+    assert np.array_equal(a, b)
+    with gwcp.Context(0, race_capacity=max(1, len(a) // 2)) as small:
+        small.load_trace(ev, *geo.astuple())
+        small.compute_order()
+        with pytest.raises(gwcp.GwcpError) as ei:
+            small.report_races(cap=len(a))
+        assert ei.value.code == gwcp.ERR_CAPACITY
+        assert small.race_count() == len(a)
+
+
+def test_device_input_and_stream(ctx):
+    import torch
+
+    ev, geo, _ = TG.generate(5, n_events=50_000, workload="8blk_64warp_10M")
+    dev = torch.from_numpy(ev.view(np.uint8).copy()).cuda()
+    s = torch.cuda.Stream()
+    ctx.load_trace(dev, *geo.astuple(), stream=s)
+    ctx.compute_order(stream=s)
+    got = ctx.report_races(stream=s)
+    assert np.array_equal(got, O.run(ev, *geo.astuple()).races)
