@@ -153,6 +153,32 @@ int gwcp_profile_get(const gwcp_ctx* ctx, int i, const char** name, float* ms, d
  * [7] vector-clock joins in the propagation. Synchronous. */
 int gwcp_counters(const gwcp_ctx* ctx, uint64_t* out8);
 
+/* Allocation-free analysis of a small trace (the paper has no counterpart: this is an
+ * interface for callers that cannot allocate device memory when they need a trace
+ * analysed, e.g. code running while another component owns the memory pool, or a hook
+ * that must not call cudaMalloc/cudaFree because those can synchronise the device).
+ * Same analysis and same results as gwcp_load_trace(ev_is_device = 1) +
+ * gwcp_compute_order + gwcp_report_races, but every intermediate buffer comes from one
+ * file-scope __device__ scratch array of 96 MiB that every GPU loading the library
+ * holds until the process exits; the call itself allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).
+ *   ev_dev     device array of n events (read only).
+ *   races_dev  device array of races_cap races, written with the first races_cap races
+ *              sorted by (later, earlier); may be NULL when races_cap is 0.
+ *   n_races    host pointer; receives the total number of races.
+ *   first_bad_index  host pointer or NULL; receives the first offending event after
+ *              GWCP_ERR_INVALID_TRACE.
+ * Limits: n <= 262144 events, num_agents <= 256, and the trace's intermediates must
+ * fit the scratch; beyond any of them the call returns GWCP_ERR_UNSUPPORTED and does
+ * nothing else. Returns GWCP_ERR_CAPACITY when races_cap < *n_races.
+ * Runs on the current CUDA device and synchronises cuda_stream before returning. The
+ * first call on a device looks up the scratch array's device address (a one-time
+ * set-up per device); make that first call before any stream capture. All calls share
+ * the one scratch array: calls that overlap on the GPU (other streams or threads) race
+ * on it and must be serialised by the caller. */
+int gwcp_analyze_noalloc(const gwcp_event* ev_dev, uint64_t n, const gwcp_geometry* geo, gwcp_race* races_dev,
+                         uint64_t races_cap, uint64_t* n_races, uint64_t* first_bad_index, void* cuda_stream);
+
 /* Number of kernels this library has launched in this process, on any context. */
 uint64_t gwcp_launch_count(void);
 

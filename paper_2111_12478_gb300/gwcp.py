@@ -20,7 +20,7 @@ ERRORS = {-1: "INVALID_TRACE", -2: "OOM", -3: "CUDA", -4: "CAPACITY", -5: "TIMEO
 ERR_INVALID_TRACE, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_STATE, ERR_ARGS, ERR_UNSUPPORTED = range(-1, -9, -1)
 EXPORTS = ("gwcp_create", "gwcp_load_trace", "gwcp_compute_order", "gwcp_report_races", "gwcp_debug_clock",
            "gwcp_first_bad_index", "gwcp_profile_get", "gwcp_counters", "gwcp_launch_count", "gwcp_destroy",
-           "gwcp_strerror")
+           "gwcp_strerror", "gwcp_analyze_noalloc")
 
 
 class GwcpError(RuntimeError):
@@ -66,6 +66,9 @@ def load_library():
     L.gwcp_profile_get.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(ctypes.c_double)]
     L.gwcp_counters.argtypes = [vp, ctypes.POINTER(u64)]
+    L.gwcp_analyze_noalloc.argtypes = [vp, u64, ctypes.POINTER(Geometry), vp, u64, ctypes.POINTER(u64),
+                                       ctypes.POINTER(u64), vp]
+    L.gwcp_analyze_noalloc.restype = i32
     L.gwcp_launch_count.argtypes = []
     L.gwcp_launch_count.restype = u64
     L.gwcp_destroy.argtypes = [vp]
@@ -203,6 +206,19 @@ class Context:
         keys = ("accesses", "sync_entries", "critical_sections", "in_section_accesses", "clock_versions",
                 "partner_tests", "loop_visits", "joins")
         return dict(zip(keys, [int(v) for v in a]))
+
+
+def analyze_noalloc(ev_dev_ptr: int, n: int, num_agents: int, agents_per_block: int, granularity: int,
+                    races_dev_ptr: int, races_cap: int, stream=None) -> tuple[int, int, int]:
+    """gwcp_analyze_noalloc on device pointers (e.g. torch tensors' data_ptr()); returns
+    (return code, total races, first bad index). Allocates nothing on the device."""
+    L = load_library()
+    geo = Geometry(num_agents, agents_per_block, granularity, 0)
+    nr = ctypes.c_uint64(0)
+    bad = ctypes.c_uint64(0)
+    rc = L.gwcp_analyze_noalloc(ctypes.c_void_p(ev_dev_ptr), n, ctypes.byref(geo), ctypes.c_void_p(races_dev_ptr),
+                                races_cap, ctypes.byref(nr), ctypes.byref(bad), _stream_ptr(stream))
+    return int(rc), int(nr.value), int(bad.value)
 
 
 def analyze(events, num_agents, agents_per_block, granularity, device: int = 0, **kw) -> np.ndarray:
