@@ -250,6 +250,10 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   b.psnap = get<uint32_t>(c, "psnap", (size_t(z.n_cs) + 1) * g.Wp, &oom);
   b.hsnap = get<uint32_t>(c, "hsnap", (size_t(z.n_cs) + 1) * g.Wp, &oom);
   b.done = get<uint32_t>(c, "done", size_t(z.n_cs) + 1, &oom);
+  b.plan = get<uint4>(c, "plan", 2 * (size_t(z.n_sync) + z.n_incs) + 2, &oom);
+  b.recmeta = get<uint4>(c, "recmeta", size_t(z.n_cs) + 1, &oom);
+  b.flat_off = get<uint32_t>(c, "flat_off", ni1, &oom);
+  b.flat = get<uint32_t>(c, "flat", z.pool_cap, &oom);
   b.cursor = get<uint32_t>(c, "cursor", size_t(g.W) * (z.n_locks + 1), &oom);
   const size_t smem = size_t(2) * g.apb * 2 * g.Wp * 4;
   z.cta_barriers = g.apb <= 32 && smem <= 96 * 1024;

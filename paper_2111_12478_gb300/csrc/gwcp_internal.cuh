@@ -129,6 +129,10 @@ struct Bufs {
   uint32_t* ex_dep_off = nullptr;  // [n_exp]
   uint32_t* ex_dep_cnt = nullptr;
   // phase G: propagation
+  uint4* plan = nullptr;        // [2 * (n_sync + n_incs)] one 32-byte entry per clock-changing step
+  uint4* recmeta = nullptr;     // [n_cs + 1] (agent, acquire epoch, release index, scope id)
+  uint32_t* flat_off = nullptr; // [n_incs + 1] dependency list of each in-section access
+  uint32_t* flat = nullptr;     // [pool_cap]
   uint32_t* rows = nullptr;     // [n_rows * Wp]
   uint32_t* psnap = nullptr;    // [n_cs * Wp]
   uint32_t* hsnap = nullptr;    // [n_cs * Wp]

@@ -188,6 +188,10 @@ int analyze(const Event* ev, uint64_t n, const Geo& g, gwcp_race* out, uint64_t 
   b.psnap = A.take<uint32_t>((size_t(z.n_cs) + 1) * g.Wp);
   b.hsnap = A.take<uint32_t>((size_t(z.n_cs) + 1) * g.Wp);
   b.done = A.take<uint32_t>(size_t(z.n_cs) + 1);
+  b.plan = A.take<uint4>(2 * (size_t(z.n_sync) + z.n_incs) + 2);
+  b.recmeta = A.take<uint4>(size_t(z.n_cs) + 1);
+  b.flat_off = A.take<uint32_t>(ni1);
+  b.flat = A.take<uint32_t>(z.pool_cap);
   b.cursor = A.take<uint32_t>(size_t(g.W) * (z.n_locks + 1));
   const size_t smem = size_t(2) * g.apb * 2 * g.Wp * 4;
   z.cta_barriers = g.apb <= 32 && smem <= 96 * 1024;

@@ -35,6 +35,9 @@ struct PropArgs {
   const uint32_t* rowbase;
   const uint32_t *cs_of_sync, *cs_agent, *cs_sid, *cs_epoch, *cs_rel_idx, *cs_lock, *lock_cs_lo;
   const uint32_t *acq_dep_off, *acq_dep_cnt, *pool;
+  const uint32_t* flat;
+  uint4* plan;
+  uint4* recmeta;
   uint32_t* rows;
   uint32_t *psnap, *hsnap, *done, *cursor;
   uint32_t *bar_j, *bar_cnt;
@@ -113,26 +116,32 @@ __device__ __forceinline__ void set_entry(uint32_t (&x)[K], uint32_t v, uint32_t
   }
 }
 
-// Bounded wait for a release's completion flag (lane 0 spins; the warp then reads the
-// snapshot after __syncwarp, which orders it after lane 0's acquire).
-__device__ __forceinline__ bool wait_flag(const uint32_t* flag, bool& abort, DevStatus* st) {
-  if (abort) return false;
-  bool ok = true;
-  if ((threadIdx.x & 31) == 0) {
-    uint32_t it = 0;
-    while (!ld_acquire(flag)) {
-      if (++it > kSpinLimit) {
-        ok = false;
-        break;
-      }
-      __nanosleep(64);
+constexpr uint32_t SENTINEL = 0xFFFFFFFFu;  // no clock entry ever takes this value
+enum : uint32_t { P_ACQ = 0, P_REL = 1, P_BAR = 2, P_INCS = 3 };
+enum : uint32_t { BAR_SINGLE = 0, BAR_CTA = 1, BAR_GLOBAL = 2 };
+
+// Joins a snapshot row written once by another walker. Snapshot rows start filled with
+// SENTINEL; each 32-bit word is written exactly once, so a row with no SENTINEL word is
+// complete. The loop re-reads until then (bounded); no flag or fence is involved.
+template <int K>
+__device__ __forceinline__ void join_snapshot(uint32_t (&x)[K], const uint32_t* row, bool& abort, DevStatus* st) {
+  uint32_t y[K];
+  uint32_t it = 0;
+  for (;;) {
+    load_row<K>(row, y);
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < K; ++j) ok &= y[j] != SENTINEL;
+    if (__all_sync(0xffffffffu, ok) || abort) break;
+    if (++it > kSpinLimit) {
+      if ((threadIdx.x & 31) == 0) atomicCAS(&st->code, 0, GWCP_ERR_TIMEOUT);
+      abort = true;
+      break;
     }
-    if (!ok) atomicCAS(&st->code, 0, GWCP_ERR_TIMEOUT);
+    __nanosleep(32);
   }
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  __syncwarp();
-  if (!ok) abort = true;
-  return ok;
+#pragma unroll
+  for (int j = 0; j < K; ++j) x[j] = max(x[j], y[j]);
 }
 
 template <int K>
@@ -152,170 +161,241 @@ __global__ void __launch_bounds__(1024) k_propagate(PropArgs a) {
   uint32_t P[K], H[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) P[j] = H[j] = 0;
-  set_entry<K>(H, u, 1u);  // H_t = bottom{t := 1}, N_t = 1
+  set_entry<K>(H, u, 1u);  // H_t = bottom{t := 1}
+  uint32_t N = 1;          // N_t
   bool abort = false;
   uint64_t joins = 0, visits = 0;
   uint32_t nbar = 0;
-  const uint32_t rb = a.rowbase[u];
-  store_row<K>(a.rows + size_t(rb) * g.Wp, P);
-
+  store_row<K>(a.rows + size_t(a.rowbase[u]) * g.Wp, P);
   const uint32_t k0 = a.sy_start[u], k1 = a.sy_start[u + 1];
-  uint32_t r = a.incs_off[k0];
-  const uint32_t r1 = a.incs_off[k1];
+  const uint32_t pb = k0 + a.incs_off[k0], pe = k1 + a.incs_off[k1];
+  uint32_t* const cursor_row = a.cursor + size_t(u) * a.n_locks;
 
-  // Algorithm 2 for an in-section access: join L^w (and L^r for writes) of every held
-  // lock, i.e. the H snapshots of the releases found by the per-location walk.
-  auto in_section = [&](uint32_t rr) {
-    for (uint32_t e = a.exp_off[rr]; e < a.exp_off[rr + 1]; ++e) {
-      const uint32_t off = a.ex_dep_off[e], cnt = a.ex_dep_cnt[e];
-      for (uint32_t q = 0; q < cnt; ++q) {
-        const uint32_t d = a.pool[off + q];
-        if (!wait_flag(a.done + d, abort, a.st)) continue;
-        join_row<K>(P, a.hsnap + size_t(d) * g.Wp);
-        ++joins;
-      }
+  for (uint32_t base = pb; base < pe; base += 32) {
+    // one coalesced load of the next 32 plan entries; releases prefetch their cursor
+    const uint32_t pi = base + lane;
+    uint4 ea = make_uint4(0, 0, 0, 0), eb = make_uint4(0, 0, 0, 0);
+    if (pi < pe) {
+      ea = a.plan[2 * size_t(pi)];
+      eb = a.plan[2 * size_t(pi) + 1];
     }
-    store_row<K>(a.rows + size_t(rb + a.incs_ver[rr]) * g.Wp, P);
-  };
-
-  for (uint32_t k = k0; k < k1; ++k) {
-    while (r < r1 && a.incs_k[r] < k) in_section(r++);
-    const uint32_t kind = a.sy_kind[k];
-    if (kind == K_ACQ) {
-      // Algorithm 1, acquire: P_t |= P_<l,s'>, H_t |= H_<l,s'> over overlapping scopes
-      const uint32_t c = a.cs_of_sync[k];
-      const uint32_t off = a.acq_dep_off[c], cnt = a.acq_dep_cnt[c];
-      for (uint32_t q = 0; q < cnt; ++q) {
-        const uint32_t d = a.pool[off + q];
-        if (!wait_flag(a.done + d, abort, a.st)) continue;
-        join_row<K>(P, a.psnap + size_t(d) * g.Wp);
-        join_row<K>(H, a.hsnap + size_t(d) * g.Wp);
-        joins += 2;
-      }
-    } else if (kind == K_REL) {
-      // Algorithm 1, release: pop records of other agents' sections on this lock while
-      // their acquire is ordered before C_t; join the released ones whose scope overlaps
-      const uint32_t c = a.cs_of_sync[k];
-      const uint32_t L = a.cs_lock[c], s = a.cs_sid[c], my_idx = a.sy_idx[k];
-      uint32_t* curp = a.cursor + size_t(u) * a.n_locks + L;
-      uint32_t cur = *curp;
-      const uint32_t lo = a.lock_cs_lo[L], hi = a.lock_cs_lo[L + 1];
-      bool stop = false;
-      while (!stop && lo + cur < hi) {
-        const uint32_t rec = lo + cur + lane;
-        uint32_t ag = NONE, ep = 0, rel = NONE, sd = 0;
-        if (rec < hi) {
-          ag = a.cs_agent[rec];
-          ep = a.cs_epoch[rec];
-          rel = a.cs_rel_idx[rec];
-          sd = a.cs_sid[rec];
-        }
-        const uint32_t nb = min(32u, hi - (lo + cur));
-        for (uint32_t i = 0; i < nb; ++i) {
-          const uint32_t agi = __shfl_sync(0xffffffffu, ag, i);
-          if (agi == u) {
-            ++cur;
-            continue;
-          }
-          ++visits;
-          // acqC <= C_t, tested on the acquiring agent's entry (the acquire's epoch)
-          const uint32_t epi = __shfl_sync(0xffffffffu, ep, i);
-          if (epi > get_entry<K>(P, agi)) {
-            stop = true;
-            break;
-          }
-          ++cur;
-          const uint32_t reli = __shfl_sync(0xffffffffu, rel, i);
-          const uint32_t sdi = __shfl_sync(0xffffffffu, sd, i);
-          if (reli != NONE && reli < my_idx && scopes_overlap(sdi, s)) {
-            const uint32_t recid = lo + cur - 1;
-            if (wait_flag(a.done + recid, abort, a.st)) {
-              join_row<K>(P, a.hsnap + size_t(recid) * g.Wp);
+    uint32_t pre = 0;
+    if (pi < pe && (ea.x & 0xFF) == P_REL) pre = __ldcg(cursor_row + ea.w);
+    const uint32_t nb = min(32u, pe - base);
+    for (uint32_t i = 0; i < nb; ++i) {
+      const uint32_t t = __shfl_sync(0xffffffffu, ea.x, i) & 0xFF;
+      const uint32_t row = __shfl_sync(0xffffffffu, ea.y, i);
+      const uint32_t z = __shfl_sync(0xffffffffu, ea.z, i);
+      const uint32_t w = __shfl_sync(0xffffffffu, ea.w, i);
+      if (t == P_ACQ || t == P_INCS) {
+        // acquire (Algorithm 1): P_t |= P_<l,s'>, H_t |= H_<l,s'> over the overlapping
+        // scopes' latest releases; in-section access (Algorithm 2): P_t |= L^w (| L^r)
+        for (uint32_t q0 = 0; q0 < w; q0 += 32) {
+          const uint32_t* list = t == P_ACQ ? a.pool : a.flat;
+          const uint32_t id = q0 + lane < w ? __ldcg(list + z + q0 + lane) : 0;
+          const uint32_t nq = min(32u, w - q0);
+          for (uint32_t q = 0; q < nq; ++q) {
+            const uint32_t d = __shfl_sync(0xffffffffu, id, q);
+            if (t == P_ACQ) {
+              join_snapshot<K>(P, a.psnap + size_t(d) * g.Wp, abort, a.st);
+              join_snapshot<K>(H, a.hsnap + size_t(d) * g.Wp, abort, a.st);
+              joins += 2;
+            } else {
+              join_snapshot<K>(P, a.hsnap + size_t(d) * g.Wp, abort, a.st);
               ++joins;
             }
           }
         }
-      }
-      if (lane == 0) *curp = cur;
-      store_row<K>(a.psnap + size_t(c) * g.Wp, P);
-      store_row<K>(a.hsnap + size_t(c) * g.Wp, H);
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) st_release(a.done + c, 1u);
-      set_entry<K>(H, u, get_entry<K>(H, u) + 1);  // N_t++, H_t[t]++
-    } else {
-      // Algorithm 1, sync: join C_t and H_t of every agent in the barrier's scope
-      const uint32_t N_before = a.sy_N[k] - 1;
-      uint32_t C[K];
+      } else if (t == P_REL) {
+        // release (Algorithm 1): pop other agents' records on this lock while their
+        // acquire is ordered before C_t; join the released ones whose scope overlaps
+        const uint32_t c = z, L = w;
+        const uint32_t lo = __shfl_sync(0xffffffffu, eb.x, i), hi = __shfl_sync(0xffffffffu, eb.y, i);
+        const uint32_t s = __shfl_sync(0xffffffffu, eb.z, i), my_idx = __shfl_sync(0xffffffffu, eb.w, i);
+        uint32_t cur = __shfl_sync(0xffffffffu, pre, i);
+        bool stop = false;
+        while (!stop && lo + cur < hi) {
+          const uint32_t rec = lo + cur + lane;
+          const uint4 m = rec < hi ? __ldg(a.recmeta + rec) : make_uint4(NONE, 0, NONE, 0);
+          const uint32_t nbr = min(32u, hi - (lo + cur));
+          for (uint32_t j = 0; j < nbr; ++j) {
+            const uint32_t agj = __shfl_sync(0xffffffffu, m.x, j);
+            if (agj == u) {
+              ++cur;
+              continue;
+            }
+            ++visits;
+            // acqC <= C_t tested on the acquiring agent's entry (the acquire's epoch)
+            const uint32_t epj = __shfl_sync(0xffffffffu, m.y, j);
+            if (epj > get_entry<K>(P, agj)) {
+              stop = true;
+              break;
+            }
+            ++cur;
+            const uint32_t relj = __shfl_sync(0xffffffffu, m.z, j);
+            const uint32_t sdj = __shfl_sync(0xffffffffu, m.w, j);
+            if (relj != NONE && relj < my_idx && scopes_overlap(sdj, s)) {
+              join_snapshot<K>(P, a.hsnap + size_t(lo + cur - 1) * g.Wp, abort, a.st);
+              ++joins;
+            }
+          }
+        }
+        if (lane == 0) __stcg(cursor_row + L, cur);
+        if (lane > int(i) && (ea.x & 0xFF) == P_REL && ea.w == L) pre = cur;  // later releases of L
+        store_row<K>(a.psnap + size_t(c) * g.Wp, P);
+        store_row<K>(a.hsnap + size_t(c) * g.Wp, H);
+        set_entry<K>(H, u, N + 1);  // H_t[t]++ (H_t[t] = N_t)
+        ++N;
+      } else {
+        // sync (Algorithm 1): join C_t and H_t over the barrier's scope
+        const uint32_t mode = __shfl_sync(0xffffffffu, eb.x, i);
+        uint32_t C[K];
 #pragma unroll
-      for (int j = 0; j < K; ++j) C[j] = P[j];
-      set_entry<K>(C, u, N_before);
-      const Event e = a.ev[a.sy_idx[k]];
-      const BarMembers bm = barrier_members(e, g);
-      if (bm.count == 1) {
+        for (int j = 0; j < K; ++j) C[j] = P[j];
+        set_entry<K>(C, u, N);
+        if (mode == BAR_SINGLE) {
 #pragma unroll
-        for (int j = 0; j < K; ++j) P[j] = C[j];
-      } else if (a.cta_barriers && e.scope == GWCP_SCOPE_CTA) {
-        uint32_t* buf = xchg + size_t(nbar & 1) * nwarps * 2 * g.Wp;
-        store_row_shared<K>(buf + size_t(warp) * 2 * g.Wp, C);
-        store_row_shared<K>(buf + size_t(warp) * 2 * g.Wp + g.Wp, H);
-        __syncthreads();
+          for (int j = 0; j < K; ++j) P[j] = C[j];
+        } else if (mode == BAR_CTA) {
+          uint32_t* buf = xchg + size_t(nbar & 1) * nwarps * 2 * g.Wp;
+          store_row_shared<K>(buf + size_t(warp) * 2 * g.Wp, C);
+          store_row_shared<K>(buf + size_t(warp) * 2 * g.Wp + g.Wp, H);
+          __syncthreads();
 #pragma unroll
-        for (int j = 0; j < K; ++j) P[j] = H[j] = 0;
-        for (int w = 0; w < nwarps; ++w) {
-          uint32_t c2[K], h2[K];
-          const uint32_t* src = buf + size_t(w) * 2 * g.Wp + lane * K;
+          for (int j = 0; j < K; ++j) P[j] = H[j] = 0;
+          for (int wv = 0; wv < nwarps; ++wv) {
+            const uint32_t* src = buf + size_t(wv) * 2 * g.Wp + lane * K;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+              P[j] = max(P[j], src[j]);
+              H[j] = max(H[j], src[g.Wp + j]);
+            }
+          }
+          joins += 2 * nwarps;
+          ++nbar;
+        } else {
+          const uint32_t bid = z, count = w;
+          uint32_t* J = a.bar_j + size_t(bid) * 2 * g.Wp;
 #pragma unroll
           for (int j = 0; j < K; ++j) {
-            c2[j] = src[j];
-            h2[j] = src[g.Wp + j];
-            P[j] = max(P[j], c2[j]);
-            H[j] = max(H[j], h2[j]);
+            atomicMax(J + lane * K + j, C[j]);
+            atomicMax(J + g.Wp + lane * K + j, H[j]);
           }
-        }
-        joins += 2 * nwarps;
-        ++nbar;
-      } else {
-        const uint32_t bid = a.sy_aux[k];
-        uint32_t* J = a.bar_j + size_t(bid) * 2 * g.Wp;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-          atomicMax(J + lane * K + j, C[j]);
-          atomicMax(J + g.Wp + lane * K + j, H[j]);
-        }
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) atomicAdd(a.bar_cnt + bid, 1u);
-        if (!abort) {
-          bool ok = true;
-          if (lane == 0) {
-            uint32_t it = 0;
-            while (ld_acquire(a.bar_cnt + bid) < bm.count) {
-              if (++it > kSpinLimit) {
-                ok = false;
-                break;
-              }
-              __nanosleep(64);
-            }
-            if (!ok) atomicCAS(&a.st->code, 0, GWCP_ERR_TIMEOUT);
-          }
-          ok = __shfl_sync(0xffffffffu, ok, 0);
+          __threadfence();
           __syncwarp();
-          if (!ok) abort = true;
+          if (lane == 0) atomicAdd(a.bar_cnt + bid, 1u);
+          if (!abort) {
+            bool ok = true;
+            if (lane == 0) {
+              uint32_t it = 0;
+              while (ld_acquire(a.bar_cnt + bid) < count) {
+                if (++it > kSpinLimit) {
+                  ok = false;
+                  break;
+                }
+                __nanosleep(64);
+              }
+              if (!ok) atomicCAS(&a.st->code, 0, GWCP_ERR_TIMEOUT);
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            __syncwarp();
+            if (!ok) abort = true;
+          }
+          load_row<K>(J, P);
+          load_row<K>(J + g.Wp, H);
+          joins += 2;
         }
-        load_row<K>(J, P);
-        load_row<K>(J + g.Wp, H);
-        joins += 2;
+        set_entry<K>(H, u, N + 1);
+        ++N;
       }
-      set_entry<K>(H, u, get_entry<K>(H, u) + 1);
+      store_row<K>(a.rows + size_t(row) * g.Wp, P);
     }
-    store_row<K>(a.rows + size_t(rb + a.sy_ver[k]) * g.Wp, P);
   }
-  while (r < r1) in_section(r++);
   if (lane == 0) {
     atomicAdd(&a.st->joins, (unsigned long long)joins);
     atomicAdd(&a.st->loop_visits, (unsigned long long)visits);
   }
+}
+
+// ---- plan construction -------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t agent_of_sync(const uint32_t* sy_start, uint32_t W, uint32_t k) {
+  uint32_t lo = 0, hi = W + 1;  // last u with sy_start[u] <= k
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (sy_start[mid] <= k)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo - 1;
+}
+
+__global__ void k_recmeta(uint32_t n_cs, const uint32_t* cs_agent, const uint32_t* cs_epoch,
+                          const uint32_t* cs_rel_idx, const uint32_t* cs_sid, uint4* recmeta) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n_cs) recmeta[c] = make_uint4(cs_agent[c], cs_epoch[c], cs_rel_idx[c], cs_sid[c]);
+}
+
+__global__ void k_flatcount(uint32_t n_incs, const uint32_t* exp_off, const uint32_t* ex_dep_cnt, uint32_t* cnt) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_incs) return;
+  uint32_t t = 0;
+  for (uint32_t e = exp_off[r]; e < exp_off[r + 1]; ++e) t += ex_dep_cnt[e];
+  cnt[r] = t;
+}
+
+__global__ void k_flatfill(uint32_t n_incs, const uint32_t* exp_off, const uint32_t* ex_dep_off,
+                           const uint32_t* ex_dep_cnt, const uint32_t* pool, const uint32_t* flat_off,
+                           uint32_t* flat) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_incs) return;
+  uint32_t o = flat_off[r];
+  for (uint32_t e = exp_off[r]; e < exp_off[r + 1]; ++e)
+    for (uint32_t q = 0; q < ex_dep_cnt[e]; ++q) flat[o++] = pool[ex_dep_off[e] + q];
+}
+
+__global__ void k_plan_sync(PropArgs a, const uint32_t* sy_kind_, const uint32_t* sy_ver, const uint32_t* sy_match,
+                            uint32_t n_sync) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_sync) return;
+  const Geo& g = a.g;
+  const uint32_t u = agent_of_sync(a.sy_start, g.W, k);
+  const uint32_t row = a.rowbase[u] + sy_ver[k];
+  const uint32_t kind = sy_kind_[k];
+  uint4 ea, eb = make_uint4(0, 0, 0, 0);
+  if (kind == K_ACQ) {
+    const uint32_t c = a.cs_of_sync[k];
+    ea = make_uint4(P_ACQ, row, a.acq_dep_off[c], a.acq_dep_cnt[c]);
+  } else if (kind == K_REL) {
+    const uint32_t c = a.cs_of_sync[k];
+    const uint32_t L = a.cs_lock[c];
+    ea = make_uint4(P_REL, row, c, L);
+    eb = make_uint4(a.lock_cs_lo[L], a.lock_cs_lo[L + 1], a.cs_sid[c], a.sy_idx[k]);
+  } else {
+    const Event e = a.ev[a.sy_idx[k]];
+    const BarMembers bm = barrier_members(e, g);
+    const uint32_t mode = bm.count == 1 ? BAR_SINGLE
+                          : (a.cta_barriers && e.scope == GWCP_SCOPE_CTA) ? BAR_CTA
+                                                                          : BAR_GLOBAL;
+    ea = make_uint4(P_BAR, row, a.sy_aux[k], bm.count);
+    eb.x = mode;
+  }
+  (void)sy_match;
+  const size_t p = size_t(k) + a.incs_off[k];
+  a.plan[2 * p] = ea;
+  a.plan[2 * p + 1] = eb;
+}
+
+__global__ void k_plan_incs(PropArgs a, const uint32_t* incs_k, const uint32_t* incs_ver, const uint32_t* flat_off,
+                            uint32_t n_incs) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_incs) return;
+  const uint32_t k = incs_k[r];
+  const uint32_t u = agent_of_sync(a.sy_start, a.g.W, k);
+  const size_t p = size_t(k) + 1 + r;
+  a.plan[2 * p] = make_uint4(P_INCS, a.rowbase[u] + incs_ver[r], flat_off[r], flat_off[r + 1] - flat_off[r]);
+  a.plan[2 * p + 1] = make_uint4(0, 0, 0, 0);
 }
 
 template <int K>
@@ -377,6 +457,34 @@ int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s
   a.bar_cnt = b.bar_cnt;
   a.n_locks = z.n_locks;
   a.cta_barriers = z.cta_barriers;
+  a.flat = b.flat;
+  a.plan = b.plan;
+  a.recmeta = b.recmeta;
+  // plan: per-agent stream of clock-changing steps with their static data resolved
+  p.begin("g_plan", double(z.n_sync + z.n_incs) * 64 + double(z.n_cs) * 2 * g.Wp * 4);
+  if (z.n_cs) {
+    k_recmeta<<<(z.n_cs + 255) / 256, 256, 0, s>>>(z.n_cs, b.cs_agent, b.cs_epoch, b.cs_rel_idx, b.cs_sid,
+                                                    b.recmeta);
+    count_launch();
+    // snapshot rows start as SENTINEL: a reader accepts a row once none is left
+    cudaMemsetAsync(b.psnap, 0xFF, size_t(z.n_cs) * g.Wp * 4, s);
+    cudaMemsetAsync(b.hsnap, 0xFF, size_t(z.n_cs) * g.Wp * 4, s);
+  }
+  if (z.n_incs) {
+    k_flatcount<<<(z.n_incs + 255) / 256, 256, 0, s>>>(z.n_incs, b.exp_off, b.ex_dep_cnt, b.flat_off);
+    count_launch();
+    scan_exclusive(b.flat_off, b.flat_off, size_t(z.n_incs) + 1, nullptr, b.scan_tmp, s);
+    k_flatfill<<<(z.n_incs + 255) / 256, 256, 0, s>>>(z.n_incs, b.exp_off, b.ex_dep_off, b.ex_dep_cnt, b.dep_pool,
+                                                       b.flat_off, b.flat);
+    count_launch();
+    k_plan_incs<<<(z.n_incs + 255) / 256, 256, 0, s>>>(a, b.incs_k, b.incs_ver, b.flat_off, z.n_incs);
+    count_launch();
+  }
+  if (z.n_sync) {
+    k_plan_sync<<<(z.n_sync + 255) / 256, 256, 0, s>>>(a, b.sy_kind, b.sy_ver, b.sy_match, z.n_sync);
+    count_launch();
+  }
+  p.end();
   uint32_t grid, threads;
   size_t smem = 0;
   if (z.cta_barriers) {
