@@ -120,28 +120,96 @@ constexpr uint32_t SENTINEL = 0xFFFFFFFFu;  // no clock entry ever takes this va
 enum : uint32_t { P_ACQ = 0, P_REL = 1, P_BAR = 2, P_INCS = 3 };
 enum : uint32_t { BAR_SINGLE = 0, BAR_CTA = 1, BAR_GLOBAL = 2 };
 
-// Joins a snapshot row written once by another walker. Snapshot rows start filled with
-// SENTINEL; each 32-bit word is written exactly once, so a row with no SENTINEL word is
-// complete. The loop re-reads until then (bounded); no flag or fence is involved.
+// Snapshot rows are written once by another walker. They start filled with SENTINEL;
+// each 32-bit word is written exactly once, so a row with no SENTINEL word is complete.
+// That also makes L1-cached reads safe: a stale line can only hold SENTINEL words and is
+// then re-read from L2. No flag or fence is involved.
 template <int K>
-__device__ __forceinline__ void join_snapshot(uint32_t (&x)[K], const uint32_t* row, bool& abort, DevStatus* st) {
-  uint32_t y[K];
+__device__ __forceinline__ void load_row_l1(const uint32_t* row, uint32_t (&x)[K]) {
+  const uint32_t* p = row + (threadIdx.x & 31) * K;
+  if constexpr (K == 1) {
+    x[0] = __ldca(p);
+  } else if constexpr (K == 2) {
+    uint2 a = __ldca(reinterpret_cast<const uint2*>(p));
+    x[0] = a.x;
+    x[1] = a.y;
+  } else {
+#pragma unroll
+    for (int j = 0; j < K; j += 4) {
+      uint4 a = __ldca(reinterpret_cast<const uint4*>(p + j));
+      x[j] = a.x;
+      x[j + 1] = a.y;
+      x[j + 2] = a.z;
+      x[j + 3] = a.w;
+    }
+  }
+}
+
+template <int K>
+__device__ __forceinline__ bool row_complete(const uint32_t (&y)[K]) {
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < K; ++j) ok &= y[j] != SENTINEL;
+  return __all_sync(0xffffffffu, ok);
+}
+
+// re-read from L2 until complete (bounded)
+template <int K>
+__device__ __noinline__ void wait_row(const uint32_t* row, uint32_t (&y)[K], bool& abort, DevStatus* st) {
   uint32_t it = 0;
   for (;;) {
     load_row<K>(row, y);
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < K; ++j) ok &= y[j] != SENTINEL;
-    if (__all_sync(0xffffffffu, ok) || abort) break;
+    if (row_complete<K>(y) || abort) return;
     if (++it > kSpinLimit) {
       if ((threadIdx.x & 31) == 0) atomicCAS(&st->code, 0, GWCP_ERR_TIMEOUT);
       abort = true;
-      break;
+      return;
     }
     __nanosleep(32);
   }
+}
+
+// x |= the rows at base + ids[q] * Wp, all loads issued before any is used
+template <int K, int M>
+__device__ __forceinline__ void join_rows(uint32_t (&x)[K], const uint32_t* base, const uint32_t (&ids)[M], int n,
+                                          uint32_t Wp, bool& abort, DevStatus* st) {
+  uint32_t y[M][K];
 #pragma unroll
-  for (int j = 0; j < K; ++j) x[j] = max(x[j], y[j]);
+  for (int q = 0; q < M; ++q)
+    if (q < n) load_row_l1<K>(base + size_t(ids[q]) * Wp, y[q]);
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    if (q < n) {
+      if (!row_complete<K>(y[q])) wait_row<K>(base + size_t(ids[q]) * Wp, y[q], abort, st);
+#pragma unroll
+      for (int j = 0; j < K; ++j) x[j] = max(x[j], y[q][j]);
+    }
+  }
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+template <int K>
+__device__ __forceinline__ void prefetch_row(const uint32_t* row) {
+  constexpr int kLines = (K * 32 * 4 + 127) / 128;
+  const char* c = reinterpret_cast<const char*>(row);
+#pragma unroll
+  for (int l = 0; l < kLines; ++l) prefetch_l1(c + l * 128);
+}
+
+// P entry v of every lane's own agent index (lane-varying v), by K shuffles
+template <int K>
+__device__ __forceinline__ uint32_t lookup_entry(const uint32_t (&x)[K], uint32_t v) {
+  uint32_t r = 0;
+  const int src = int(min(v, 32u * K - 1) / K);
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const uint32_t t = __shfl_sync(0xffffffffu, x[j], src);
+    if (j == int(v % K)) r = t;
+  }
+  return r;
 }
 
 template <int K>
@@ -172,15 +240,32 @@ __global__ void __launch_bounds__(1024) k_propagate(PropArgs a) {
   uint32_t* const cursor_row = a.cursor + size_t(u) * a.n_locks;
 
   for (uint32_t base = pb; base < pe; base += 32) {
-    // one coalesced load of the next 32 plan entries; releases prefetch their cursor
+    // one coalesced load of the next 32 plan entries; each lane prefetches what its
+    // entry will read: the snapshot rows of inline dependencies, a release's cursor,
+    // first record and that record's snapshot
     const uint32_t pi = base + lane;
     uint4 ea = make_uint4(0, 0, 0, 0), eb = make_uint4(0, 0, 0, 0);
     if (pi < pe) {
       ea = a.plan[2 * size_t(pi)];
       eb = a.plan[2 * size_t(pi) + 1];
     }
+    const uint32_t my_t = ea.x & 0xFF;
     uint32_t pre = 0;
-    if (pi < pe && (ea.x & 0xFF) == P_REL) pre = __ldcg(cursor_row + ea.w);
+    if (pi < pe) {
+      if (my_t == P_REL) {
+        pre = __ldcg(cursor_row + ea.w);
+        if (eb.x + pre < eb.y) {
+          prefetch_l1(a.recmeta + eb.x + pre);
+          prefetch_row<K>(a.hsnap + size_t(eb.x + pre) * g.Wp);
+        }
+      } else if ((my_t == P_ACQ || my_t == P_INCS) && ea.w <= 4) {
+        const uint32_t ids[4] = {eb.x, eb.y, eb.z, eb.w};
+        for (uint32_t q = 0; q < ea.w; ++q) {
+          if (my_t == P_ACQ) prefetch_row<K>(a.psnap + size_t(ids[q]) * g.Wp);
+          prefetch_row<K>(a.hsnap + size_t(ids[q]) * g.Wp);
+        }
+      }
+    }
     const uint32_t nb = min(32u, pe - base);
     for (uint32_t i = 0; i < nb; ++i) {
       const uint32_t t = __shfl_sync(0xffffffffu, ea.x, i) & 0xFF;
@@ -190,25 +275,34 @@ __global__ void __launch_bounds__(1024) k_propagate(PropArgs a) {
       if (t == P_ACQ || t == P_INCS) {
         // acquire (Algorithm 1): P_t |= P_<l,s'>, H_t |= H_<l,s'> over the overlapping
         // scopes' latest releases; in-section access (Algorithm 2): P_t |= L^w (| L^r)
-        for (uint32_t q0 = 0; q0 < w; q0 += 32) {
-          const uint32_t* list = t == P_ACQ ? a.pool : a.flat;
-          const uint32_t id = q0 + lane < w ? __ldcg(list + z + q0 + lane) : 0;
-          const uint32_t nq = min(32u, w - q0);
-          for (uint32_t q = 0; q < nq; ++q) {
-            const uint32_t d = __shfl_sync(0xffffffffu, id, q);
-            if (t == P_ACQ) {
-              join_snapshot<K>(P, a.psnap + size_t(d) * g.Wp, abort, a.st);
-              join_snapshot<K>(H, a.hsnap + size_t(d) * g.Wp, abort, a.st);
-              joins += 2;
-            } else {
-              join_snapshot<K>(P, a.hsnap + size_t(d) * g.Wp, abort, a.st);
-              ++joins;
-            }
+        const uint32_t* list = t == P_ACQ ? a.pool : a.flat;
+        for (uint32_t q0 = 0; q0 < w; q0 += 4) {
+          uint32_t ids[4];
+          if (w <= 4) {
+            ids[0] = __shfl_sync(0xffffffffu, eb.x, i);
+            ids[1] = __shfl_sync(0xffffffffu, eb.y, i);
+            ids[2] = __shfl_sync(0xffffffffu, eb.z, i);
+            ids[3] = __shfl_sync(0xffffffffu, eb.w, i);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ids[q] = q0 + q < w ? __ldcg(list + z + q0 + q) : 0;
+          }
+          const int n = int(min(4u, w - q0));
+          if (t == P_ACQ) {
+            join_rows<K, 4>(P, a.psnap, ids, n, g.Wp, abort, a.st);
+            join_rows<K, 4>(H, a.hsnap, ids, n, g.Wp, abort, a.st);
+            joins += 2 * n;
+          } else {
+            join_rows<K, 4>(P, a.hsnap, ids, n, g.Wp, abort, a.st);
+            joins += n;
           }
         }
       } else if (t == P_REL) {
         // release (Algorithm 1): pop other agents' records on this lock while their
-        // acquire is ordered before C_t; join the released ones whose scope overlaps
+        // acquire is ordered before C_t; join the released ones whose scope overlaps.
+        // Waves: every record before the first one failing the test against the
+        // current P passes (P only grows), so their snapshots are joined together;
+        // the failing record is tested again only if the wave changed P.
         const uint32_t c = z, L = w;
         const uint32_t lo = __shfl_sync(0xffffffffu, eb.x, i), hi = __shfl_sync(0xffffffffu, eb.y, i);
         const uint32_t s = __shfl_sync(0xffffffffu, eb.z, i), my_idx = __shfl_sync(0xffffffffu, eb.w, i);
@@ -216,32 +310,48 @@ __global__ void __launch_bounds__(1024) k_propagate(PropArgs a) {
         bool stop = false;
         while (!stop && lo + cur < hi) {
           const uint32_t rec = lo + cur + lane;
-          const uint4 m = rec < hi ? __ldg(a.recmeta + rec) : make_uint4(NONE, 0, NONE, 0);
           const uint32_t nbr = min(32u, hi - (lo + cur));
-          for (uint32_t j = 0; j < nbr; ++j) {
-            const uint32_t agj = __shfl_sync(0xffffffffu, m.x, j);
-            if (agj == u) {
-              ++cur;
-              continue;
+          const uint4 m = rec < hi ? __ldg(a.recmeta + rec) : make_uint4(NONE, 0, NONE, 0);
+          const bool mine = m.x == u;
+          const bool joinable = !mine && m.z != NONE && m.z < my_idx && scopes_overlap(m.w, s);
+          uint32_t start = 0;
+          while (start < nbr) {
+            const uint32_t pv = lookup_entry<K>(P, m.x);
+            const bool in = uint32_t(lane) >= start && uint32_t(lane) < nbr;
+            const uint32_t fail = __ballot_sync(0xffffffffu, in && !mine && m.y > pv);
+            const uint32_t f = fail ? uint32_t(__ffs(fail) - 1) : nbr;  // first failing record
+            const uint32_t wave = __ballot_sync(0xffffffffu, in && uint32_t(lane) < f && joinable);
+            visits += __popc(__ballot_sync(0xffffffffu, in && uint32_t(lane) <= f && !mine));
+            uint32_t wm = wave;
+            while (wm) {
+              uint32_t ids[4];
+              int n = 0;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                ids[q] = 0;
+                if (wm) {
+                  ids[q] = lo + cur + (__ffs(wm) - 1);
+                  wm &= wm - 1;
+                  ++n;
+                }
+              }
+              join_rows<K, 4>(P, a.hsnap, ids, n, g.Wp, abort, a.st);
+              joins += n;
             }
-            ++visits;
-            // acqC <= C_t tested on the acquiring agent's entry (the acquire's epoch)
-            const uint32_t epj = __shfl_sync(0xffffffffu, m.y, j);
-            if (epj > get_entry<K>(P, agj)) {
-              stop = true;
+            if (f == nbr) {
+              start = nbr;
+            } else if (wave) {
+              start = f;  // P grew: test the failing record again
+            } else {
+              stop = true;  // P unchanged: the record stays unordered
+              start = f;
               break;
             }
-            ++cur;
-            const uint32_t relj = __shfl_sync(0xffffffffu, m.z, j);
-            const uint32_t sdj = __shfl_sync(0xffffffffu, m.w, j);
-            if (relj != NONE && relj < my_idx && scopes_overlap(sdj, s)) {
-              join_snapshot<K>(P, a.hsnap + size_t(lo + cur - 1) * g.Wp, abort, a.st);
-              ++joins;
-            }
           }
+          cur += start;
         }
         if (lane == 0) __stcg(cursor_row + L, cur);
-        if (lane > int(i) && (ea.x & 0xFF) == P_REL && ea.w == L) pre = cur;  // later releases of L
+        if (lane > int(i) && my_t == P_REL && ea.w == L) pre = cur;  // later releases of L
         store_row<K>(a.psnap + size_t(c) * g.Wp, P);
         store_row<K>(a.hsnap + size_t(c) * g.Wp, H);
         set_entry<K>(H, u, N + 1);  // H_t[t]++ (H_t[t] = N_t)
@@ -366,7 +476,11 @@ __global__ void k_plan_sync(PropArgs a, const uint32_t* sy_kind_, const uint32_t
   uint4 ea, eb = make_uint4(0, 0, 0, 0);
   if (kind == K_ACQ) {
     const uint32_t c = a.cs_of_sync[k];
-    ea = make_uint4(P_ACQ, row, a.acq_dep_off[c], a.acq_dep_cnt[c]);
+    const uint32_t off = a.acq_dep_off[c], cnt = a.acq_dep_cnt[c];
+    ea = make_uint4(P_ACQ, row, off, cnt);
+    if (cnt <= 4)  // up to four dependency ids ride in the entry itself
+      eb = make_uint4(cnt > 0 ? a.pool[off] : 0, cnt > 1 ? a.pool[off + 1] : 0, cnt > 2 ? a.pool[off + 2] : 0,
+                      cnt > 3 ? a.pool[off + 3] : 0);
   } else if (kind == K_REL) {
     const uint32_t c = a.cs_of_sync[k];
     const uint32_t L = a.cs_lock[c];
@@ -394,8 +508,11 @@ __global__ void k_plan_incs(PropArgs a, const uint32_t* incs_k, const uint32_t* 
   const uint32_t k = incs_k[r];
   const uint32_t u = agent_of_sync(a.sy_start, a.g.W, k);
   const size_t p = size_t(k) + 1 + r;
-  a.plan[2 * p] = make_uint4(P_INCS, a.rowbase[u] + incs_ver[r], flat_off[r], flat_off[r + 1] - flat_off[r]);
-  a.plan[2 * p + 1] = make_uint4(0, 0, 0, 0);
+  const uint32_t off = flat_off[r], cnt = flat_off[r + 1] - off;
+  a.plan[2 * p] = make_uint4(P_INCS, a.rowbase[u] + incs_ver[r], off, cnt);
+  a.plan[2 * p + 1] = cnt <= 4 ? make_uint4(cnt > 0 ? a.flat[off] : 0, cnt > 1 ? a.flat[off + 1] : 0,
+                                            cnt > 2 ? a.flat[off + 2] : 0, cnt > 3 ? a.flat[off + 3] : 0)
+                               : make_uint4(0, 0, 0, 0);
 }
 
 template <int K>
