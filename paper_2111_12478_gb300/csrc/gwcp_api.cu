@@ -23,15 +23,15 @@ cudaEvent_t Prof::ev() {
   }
   return pool[used++];
 }
-void Prof::begin(const char* name, double bytes) {
+void Prof::begin(const char* name, double bytes, cudaStream_t on_stream) {
   if (!on) return;
-  Rec r{name, ev(), ev(), bytes};
-  cudaEventRecord(r.a, s);
+  Rec r{name, ev(), ev(), bytes, on_stream ? on_stream : s};
+  cudaEventRecord(r.a, r.s);
   recs.push_back(r);
 }
 void Prof::end() {
   if (!on || recs.empty()) return;
-  cudaEventRecord(recs.back().b, s);
+  cudaEventRecord(recs.back().b, recs.back().s);
 }
 }  // namespace gwcp
 
@@ -57,6 +57,8 @@ struct gwcp_ctx {
   uint64_t n_races = 0;
   unsigned long long bad_index = ~0ull;
   uint64_t counters[8] = {};
+  cudaStream_t side = nullptr;  // runs the access grouping beside the propagation
+  cudaEvent_t fork = nullptr, join = nullptr;
   std::vector<float> prof_ms;
   std::vector<double> prof_bytes;
   std::vector<const char*> prof_names;
@@ -274,12 +276,21 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   }
 
   phaseD_gaps(b, g, z, s, c->prof);
+  // the access grouping and the check's carries do not depend on clock values: they run
+  // on a side stream, with their own scratch, while the propagation runs on s
+  uint32_t* side_tmp = get<uint32_t>(c, "side_tmp", radix_tmp_need(size_t(z.n_acc) + 1) + 64, &oom);
+  if (oom) return GWCP_ERR_OOM;
+  cudaEventRecord(c->fork, s);
+  cudaStreamWaitEvent(c->side, c->fork, 0);
+  phaseH_sort(b, g, z, key_mask, side_tmp, c->side, c->prof);
+  phaseI_carry(b, g, z, c->side, c->prof);
+  cudaEventRecord(c->join, c->side);
   phaseF_incs(b, g, z, key_mask, s, c->prof);
   phaseF_walk(b, g, z, key_mask, s, c->prof);
   z.n_groups = z.n_exp;  // upper bound; the kernel reads the exact count on the device
   phaseF_deps(b, z, s, c->prof);
-  phaseH_sort(b, g, z, key_mask, s, c->prof);
   int prc = phaseG_propagate(b, g, z, s, c->prof);
+  cudaStreamWaitEvent(s, c->join, 0);
   if (prc) return prc;
   phaseI_check(b, g, z, s, c->prof);
   {
@@ -319,7 +330,10 @@ int gwcp_create(gwcp_ctx** out, int device, const gwcp_options* opt) {
   c->device = device;
   if (opt) c->opt = *opt;
   if (cudaMallocHost(&c->st_host, sizeof(DevStatus)) != cudaSuccess ||
-      cudaMallocHost(&c->cnt_host, 16 * sizeof(uint32_t)) != cudaSuccess) {
+      cudaMallocHost(&c->cnt_host, 16 * sizeof(uint32_t)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
     gwcp_destroy(c);
     return GWCP_ERR_OOM;
   }
@@ -506,6 +520,9 @@ void gwcp_destroy(gwcp_ctx* c) {
   if (c->st_host) cudaFreeHost(c->st_host);
   if (c->cnt_host) cudaFreeHost(c->cnt_host);
   for (auto e : c->prof.pool) cudaEventDestroy(e);
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->join) cudaEventDestroy(c->join);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }
 

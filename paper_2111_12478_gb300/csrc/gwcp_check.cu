@@ -112,7 +112,8 @@ __device__ __forceinline__ bool linked(const ChunkArgs& a, uint32_t c) {
 __global__ void k_scan1(ChunkArgs a, uint64_t* gagg, uint32_t* gfull) {
   const uint32_t cols = 4 * a.g.Wp;
   const uint32_t g0 = blockIdx.x * GRP, g1 = min(g0 + GRP, a.n_chunks);
-  bool full = linked(a, g0);
+  const bool first_linked = linked(a, g0);
+  bool full = first_linked;
   for (uint32_t c = g0 + 1; c < g1; ++c) full = full && linked(a, c);
   for (uint32_t col = threadIdx.x; col < cols; col += blockDim.x) {
     uint64_t acc = 0;
@@ -123,21 +124,32 @@ __global__ void k_scan1(ChunkArgs a, uint64_t* gagg, uint32_t* gfull) {
     }
     gagg[size_t(blockIdx.x) * cols + col] = acc;
   }
-  if (threadIdx.x == 0) gfull[blockIdx.x] = full;
+  if (threadIdx.x == 0) gfull[blockIdx.x] = uint32_t(full) | (uint32_t(first_linked) << 1);
 }
 
 __global__ void k_scan2(ChunkArgs a, uint32_t ngroups, uint64_t* gagg, const uint32_t* gfull) {
-  // gagg[g] becomes the carry into group g
+  // gagg[g] becomes the carry into group g. The loads of a window of groups are issued
+  // together; only the running value is carried from group to group.
+  constexpr int U = 8;
   const uint32_t cols = 4 * a.g.Wp;
   const uint32_t col = blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= cols) return;
   uint64_t prev_final = 0;
-  for (uint32_t gi = 0; gi < ngroups; ++gi) {
-    const uint64_t agg = gagg[size_t(gi) * cols + col];
-    const bool lk = linked(a, gi * GRP);
-    const uint64_t carry = lk ? prev_final : 0;
-    prev_final = gfull[gi] ? max(prev_final, agg) : agg;
-    gagg[size_t(gi) * cols + col] = carry;
+  for (uint32_t g0 = 0; g0 < ngroups; g0 += U) {
+    uint64_t agg[U];
+    uint32_t fl[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      agg[q] = g0 + q < ngroups ? gagg[size_t(g0 + q) * cols + col] : 0;
+      fl[q] = g0 + q < ngroups ? gfull[g0 + q] : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      if (g0 + q >= ngroups) break;
+      const uint64_t carry = (fl[q] & 2) ? prev_final : 0;  // group starts linked to the previous one
+      prev_final = (fl[q] & 1) ? max(prev_final, agg[q]) : agg[q];
+      gagg[size_t(g0 + q) * cols + col] = carry;
+    }
   }
 }
 
@@ -260,11 +272,11 @@ __global__ void __launch_bounds__(CHK_WARPS * 32) k_check(ChunkArgs a) {
 inline uint32_t blocks(uint64_t n, uint32_t t) { return uint32_t((n + t - 1) / t); }
 
 template <int K>
-void run_check(const ChunkArgs& a, uint64_t* gagg, uint32_t* gfull, cudaStream_t s, Prof& p, double bytes_per) {
+void run_carry(const ChunkArgs& a, uint64_t* gagg, uint32_t* gfull, cudaStream_t s, Prof& p) {
   const uint32_t nw = a.n_chunks;
   const uint32_t cols = 4 * a.g.Wp;
   const uint32_t ng = blocks(nw, GRP);
-  p.begin("i_carry", double(nw) * cols * 8 * 3);
+  p.begin("i_carry", double(nw) * cols * 8 * 3, s);
   k_tail<K><<<blocks(uint64_t(nw) * 32, CHK_WARPS * 32), CHK_WARPS * 32, 0, s>>>(a);
   count_launch();
   k_scan1<<<ng, 256, 0, s>>>(a, gagg, gfull);
@@ -274,7 +286,12 @@ void run_check(const ChunkArgs& a, uint64_t* gagg, uint32_t* gfull, cudaStream_t
   k_scan3<<<ng, 256, 0, s>>>(a, gagg);
   count_launch();
   p.end();
-  p.begin("i_check", double(a.n) * bytes_per);
+}
+
+template <int K>
+void run_check(const ChunkArgs& a, cudaStream_t s, Prof& p, double bytes_per) {
+  const uint32_t nw = a.n_chunks;
+  p.begin("i_check", double(a.n) * bytes_per, s);
   k_check<K><<<blocks(uint64_t(nw) * 32, CHK_WARPS * 32), CHK_WARPS * 32, 0, s>>>(a);
   count_launch();
   p.end();
@@ -285,18 +302,17 @@ void run_check(const ChunkArgs& a, uint64_t* gagg, uint32_t* gfull, cudaStream_t
 size_t check_chunks(uint32_t n_acc) { return (n_acc + CH - 1) / CH; }
 size_t check_group_count(uint32_t n_acc) { return (check_chunks(n_acc) + GRP - 1) / GRP; }
 
-void phaseH_sort(Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, cudaStream_t s, Prof& p) {
+void phaseH_sort(Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, uint32_t* tmp, cudaStream_t s, Prof& p) {
   (void)g;
-  p.begin("h_sort", double(z.n_acc) * 12 * 2 * radix_windows(key_mask).size());
-  if (radix_sort_pairs(b.acc_key, b.acc_idx, b.acc_key2, b.acc_idx2, z.n_acc, key_mask, b.scan_tmp, s)) {
+  p.begin("h_sort", double(z.n_acc) * 12 * 3 * radix_windows(key_mask).size(), s);
+  if (radix_sort_pairs(b.acc_key, b.acc_idx, b.acc_key2, b.acc_idx2, z.n_acc, key_mask, tmp, s)) {
     std::swap(b.acc_key, b.acc_key2);
     std::swap(b.acc_idx, b.acc_idx2);
   }
   p.end();
 }
 
-void phaseI_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
-  if (!z.n_acc) return;
+static ChunkArgs chunk_args(const Bufs& b, const Geo& g, const Sizes& z) {
   ChunkArgs a{};
   a.key = b.acc_key;
   a.idx = b.acc_idx;
@@ -309,17 +325,36 @@ void phaseI_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, P
   a.race_cap = z.race_cap;
   a.st = b.st;
   a.g = g;
+  return a;
+}
+
+void phaseI_carry(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
+  if (!z.n_acc) return;
+  const ChunkArgs a = chunk_args(b, g, z);
   uint64_t* gagg = a.T + size_t(z.n_chunks) * 4 * g.Wp;
   uint32_t* gfull = reinterpret_cast<uint32_t*>(gagg + size_t(check_group_count(z.n_acc)) * 4 * g.Wp);
+  switch (g.K) {
+    case 1: run_carry<1>(a, gagg, gfull, s, p); break;
+    case 2: run_carry<2>(a, gagg, gfull, s, p); break;
+    case 4: run_carry<4>(a, gagg, gfull, s, p); break;
+    case 8: run_carry<8>(a, gagg, gfull, s, p); break;
+    case 16: run_carry<16>(a, gagg, gfull, s, p); break;
+    case 32: run_carry<32>(a, gagg, gfull, s, p); break;
+  }
+}
+
+void phaseI_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
+  if (!z.n_acc) return;
+  const ChunkArgs a = chunk_args(b, g, z);
   // per access: sorted key + index (12 B), its record (16 B), its clock-version row
   const double per = 12.0 + 16.0 + 4.0 * g.Wp;
   switch (g.K) {
-    case 1: run_check<1>(a, gagg, gfull, s, p, per); break;
-    case 2: run_check<2>(a, gagg, gfull, s, p, per); break;
-    case 4: run_check<4>(a, gagg, gfull, s, p, per); break;
-    case 8: run_check<8>(a, gagg, gfull, s, p, per); break;
-    case 16: run_check<16>(a, gagg, gfull, s, p, per); break;
-    case 32: run_check<32>(a, gagg, gfull, s, p, per); break;
+    case 1: run_check<1>(a, s, p, per); break;
+    case 2: run_check<2>(a, s, p, per); break;
+    case 4: run_check<4>(a, s, p, per); break;
+    case 8: run_check<8>(a, s, p, per); break;
+    case 16: run_check<16>(a, s, p, per); break;
+    case 32: run_check<32>(a, s, p, per); break;
   }
 }
 

@@ -276,12 +276,13 @@ struct Prof {
     const char* name;
     cudaEvent_t a, b;
     double bytes;
+    cudaStream_t s;
   };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   cudaEvent_t ev();
-  void begin(const char* name, double bytes);
+  void begin(const char* name, double bytes, cudaStream_t on = nullptr);  // nullptr: the default stream s
   void end();
 };
 
@@ -295,7 +296,10 @@ void phaseE_walk(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Pr
 void phaseF_incs(const Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, cudaStream_t s, Prof& p);
 void phaseF_walk(Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, cudaStream_t s, Prof& p);
 int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
-void phaseH_sort(Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, cudaStream_t s, Prof& p);
+// access grouping; tmp is the sort scratch (it may run beside other work on stream s)
+void phaseH_sort(Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, uint32_t* tmp, cudaStream_t s, Prof& p);
+// per-chunk carries of the check (needs the sorted accesses and AccInfo, not the clocks)
+void phaseI_carry(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 void phaseI_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 bool phaseI_sort_races(const Bufs& b, const Sizes& z, uint64_t n_races, cudaStream_t s, Prof& p);
 

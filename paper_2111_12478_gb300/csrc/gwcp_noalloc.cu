@@ -235,8 +235,9 @@ int analyze(const Event* ev, uint64_t n, const Geo& g, gwcp_race* out, uint64_t 
   phaseF_walk(b, g, z, key_mask, s, prof);
   z.n_groups = z.n_exp;
   phaseF_deps(b, z, s, prof);
-  phaseH_sort(b, g, z, key_mask, s, prof);
+  phaseH_sort(b, g, z, key_mask, b.scan_tmp, s, prof);
   if (int rc = phaseG_propagate(b, g, z, s, prof)) return rc;
+  phaseI_carry(b, g, z, s, prof);
   phaseI_check(b, g, z, s, prof);
   if (int rc = read_back(s, &st, b.st, v, nullptr, 0)) return rc;
   if (st.code) {

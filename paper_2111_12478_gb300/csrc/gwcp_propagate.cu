@@ -187,6 +187,33 @@ __device__ __forceinline__ void join_rows(uint32_t (&x)[K], const uint32_t* base
   }
 }
 
+// x |= rows of base_x, y |= rows of base_y for the same ids: all loads issued first
+template <int K, int M>
+__device__ __forceinline__ void join_rows2(uint32_t (&x)[K], const uint32_t* base_x, uint32_t (&y)[K],
+                                           const uint32_t* base_y, const uint32_t (&ids)[M], int n, uint32_t Wp,
+                                           bool& abort, DevStatus* st) {
+  uint32_t rx[M][K], ry[M][K];
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    if (q < n) {
+      load_row_l1<K>(base_x + size_t(ids[q]) * Wp, rx[q]);
+      load_row_l1<K>(base_y + size_t(ids[q]) * Wp, ry[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    if (q < n) {
+      if (!row_complete<K>(rx[q])) wait_row<K>(base_x + size_t(ids[q]) * Wp, rx[q], abort, st);
+      if (!row_complete<K>(ry[q])) wait_row<K>(base_y + size_t(ids[q]) * Wp, ry[q], abort, st);
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        x[j] = max(x[j], rx[q][j]);
+        y[j] = max(y[j], ry[q][j]);
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
@@ -289,8 +316,7 @@ __global__ void __launch_bounds__(1024) k_propagate(PropArgs a) {
           }
           const int n = int(min(4u, w - q0));
           if (t == P_ACQ) {
-            join_rows<K, 4>(P, a.psnap, ids, n, g.Wp, abort, a.st);
-            join_rows<K, 4>(H, a.hsnap, ids, n, g.Wp, abort, a.st);
+            join_rows2<K, 4>(P, a.psnap, H, a.hsnap, ids, n, g.Wp, abort, a.st);
             joins += 2 * n;
           } else {
             join_rows<K, 4>(P, a.hsnap, ids, n, g.Wp, abort, a.st);
@@ -312,6 +338,10 @@ __global__ void __launch_bounds__(1024) k_propagate(PropArgs a) {
           const uint32_t rec = lo + cur + lane;
           const uint32_t nbr = min(32u, hi - (lo + cur));
           const uint4 m = rec < hi ? __ldg(a.recmeta + rec) : make_uint4(NONE, 0, NONE, 0);
+          // the first record's snapshot, loaded beside its metadata: used if it is joined
+          uint32_t spec[K];
+          load_row_l1<K>(a.hsnap + size_t(lo + cur) * g.Wp, spec);
+          bool spec_live = true;
           const bool mine = m.x == u;
           const bool joinable = !mine && m.z != NONE && m.z < my_idx && scopes_overlap(m.w, s);
           uint32_t start = 0;
@@ -323,6 +353,14 @@ __global__ void __launch_bounds__(1024) k_propagate(PropArgs a) {
             const uint32_t wave = __ballot_sync(0xffffffffu, in && uint32_t(lane) < f && joinable);
             visits += __popc(__ballot_sync(0xffffffffu, in && uint32_t(lane) <= f && !mine));
             uint32_t wm = wave;
+            if (spec_live && (wm & 1u)) {  // record lo + cur: its row is already loaded
+              if (!row_complete<K>(spec)) wait_row<K>(a.hsnap + size_t(lo + cur) * g.Wp, spec, abort, a.st);
+#pragma unroll
+              for (int j = 0; j < K; ++j) P[j] = max(P[j], spec[j]);
+              ++joins;
+              wm &= ~1u;
+            }
+            spec_live = false;
             while (wm) {
               uint32_t ids[4];
               int n = 0;
