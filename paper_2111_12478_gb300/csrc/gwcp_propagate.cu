@@ -122,29 +122,8 @@ enum : uint32_t { BAR_SINGLE = 0, BAR_CTA = 1, BAR_GLOBAL = 2 };
 
 // Snapshot rows are written once by another walker. They start filled with SENTINEL;
 // each 32-bit word is written exactly once, so a row with no SENTINEL word is complete.
-// That also makes L1-cached reads safe: a stale line can only hold SENTINEL words and is
-// then re-read from L2. No flag or fence is involved.
-template <int K>
-__device__ __forceinline__ void load_row_l1(const uint32_t* row, uint32_t (&x)[K]) {
-  const uint32_t* p = row + (threadIdx.x & 31) * K;
-  if constexpr (K == 1) {
-    x[0] = __ldca(p);
-  } else if constexpr (K == 2) {
-    uint2 a = __ldca(reinterpret_cast<const uint2*>(p));
-    x[0] = a.x;
-    x[1] = a.y;
-  } else {
-#pragma unroll
-    for (int j = 0; j < K; j += 4) {
-      uint4 a = __ldca(reinterpret_cast<const uint4*>(p + j));
-      x[j] = a.x;
-      x[j + 1] = a.y;
-      x[j + 2] = a.z;
-      x[j + 3] = a.w;
-    }
-  }
-}
-
+// Rows are always read through L2 (ld.cg, cp.async.cg), never cached in L1. No flag or
+// fence is involved.
 template <int K>
 __device__ __forceinline__ bool row_complete(const uint32_t (&y)[K]) {
   bool ok = true;
@@ -176,7 +155,7 @@ __device__ __forceinline__ void join_rows(uint32_t (&x)[K], const uint32_t* base
   uint32_t y[M][K];
 #pragma unroll
   for (int q = 0; q < M; ++q)
-    if (q < n) load_row_l1<K>(base + size_t(ids[q]) * Wp, y[q]);
+    if (q < n) load_row<K>(base + size_t(ids[q]) * Wp, y[q]);
 #pragma unroll
   for (int q = 0; q < M; ++q) {
     if (q < n) {
@@ -196,8 +175,8 @@ __device__ __forceinline__ void join_rows2(uint32_t (&x)[K], const uint32_t* bas
 #pragma unroll
   for (int q = 0; q < M; ++q) {
     if (q < n) {
-      load_row_l1<K>(base_x + size_t(ids[q]) * Wp, rx[q]);
-      load_row_l1<K>(base_y + size_t(ids[q]) * Wp, ry[q]);
+      load_row<K>(base_x + size_t(ids[q]) * Wp, rx[q]);
+      load_row<K>(base_y + size_t(ids[q]) * Wp, ry[q]);
     }
   }
 #pragma unroll
@@ -214,18 +193,6 @@ __device__ __forceinline__ void join_rows2(uint32_t (&x)[K], const uint32_t* bas
   }
 }
 
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
-template <int K>
-__device__ __forceinline__ void prefetch_row(const uint32_t* row) {
-  constexpr int kLines = (K * 32 * 4 + 127) / 128;
-  const char* c = reinterpret_cast<const char*>(row);
-#pragma unroll
-  for (int l = 0; l < kLines; ++l) prefetch_l1(c + l * 128);
-}
-
 // P entry v of every lane's own agent index (lane-varying v), by K shuffles
 template <int K>
 __device__ __forceinline__ uint32_t lookup_entry(const uint32_t (&x)[K], uint32_t v) {
@@ -239,12 +206,55 @@ __device__ __forceinline__ uint32_t lookup_entry(const uint32_t (&x)[K], uint32_
   return r;
 }
 
+// cp.async (LDGSTS): 16-byte copy global -> shared through L2 only (no L1 line that
+// could hold a row before its release wrote it)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// stage one clock row (Wc words) into shared memory: lane l copies 16-byte chunk l
+template <int Wc>
+__device__ __forceinline__ void stage_row(uint32_t* dst, const uint32_t* src) {
+  const int lane = threadIdx.x & 31;
+  if (lane < Wc / 4) cp_async16(dst + 4 * lane, src + 4 * lane);
+}
+
 template <int K>
-__global__ void __launch_bounds__(1024) k_propagate(PropArgs a) {
-  extern __shared__ uint32_t xchg[];  // CTA barriers: [2 buffers][warps][C | H][Wp]
+__device__ __forceinline__ void read_row_shared(const uint32_t* row, uint32_t (&y)[K]) {
+  const uint32_t* p = row + (threadIdx.x & 31) * K;
+#pragma unroll
+  for (int j = 0; j < K; ++j) y[j] = p[j];
+}
+
+// shared-memory words per ring slot: four rows, or 32 section records + one row; then
+// a 4-word header (kind, staged cursor, row count)
+template <int K>
+__host__ __device__ constexpr int slot_words() {
+  return (((4 * 32 * K > 128 + 32 * K) ? 4 * 32 * K : 128 + 32 * K) + 4 + 3) & ~3;
+}
+
+// One warp per agent walks the agent's plan (its clock-changing steps in trace order).
+// R > 0: a ring of R shared-memory slots per warp; while entry p is processed, the
+// copies for entry p + R - 1 are in flight (one commit group per entry).
+template <int K, int R, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_propagate(PropArgs a) {
+  constexpr int Wc = 32 * K;
+  constexpr int SLOT = slot_words<K>();
+  constexpr int RR = R > 0 ? R : 1;
+  extern __shared__ __align__(16) uint32_t sm[];
   const Geo& g = a.g;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const uint32_t u = a.cta_barriers ? blockIdx.x * g.apb + warp : blockIdx.x * 32 + warp;
+  uint32_t* const xchg = sm;  // CTA barriers: [2 buffers][warps][C | H][Wp]
+  const uint32_t xchg_words = a.cta_barriers ? 2u * nwarps * 2 * Wc : 0u;
+  uint32_t* const ring = sm + xchg_words + (R > 0 ? size_t(warp) * RR * SLOT : 0);  // unused when R = 0
   // one read of the status per CTA, so all warps of a CTA agree on whether to run
   __shared__ int start_code;
   if (threadIdx.x == 0) start_code = *(volatile int*)&a.st->code;
@@ -261,204 +271,294 @@ __global__ void __launch_bounds__(1024) k_propagate(PropArgs a) {
   bool abort = false;
   uint64_t joins = 0, visits = 0;
   uint32_t nbar = 0;
-  store_row<K>(a.rows + size_t(a.rowbase[u]) * g.Wp, P);
+  store_row<K>(a.rows + size_t(a.rowbase[u]) * Wc, P);
   const uint32_t k0 = a.sy_start[u], k1 = a.sy_start[u + 1];
   const uint32_t pb = k0 + a.incs_off[k0], pe = k1 + a.incs_off[k1];
   uint32_t* const cursor_row = a.cursor + size_t(u) * a.n_locks;
 
-  for (uint32_t base = pb; base < pe; base += 32) {
-    // one coalesced load of the next 32 plan entries; each lane prefetches what its
-    // entry will read: the snapshot rows of inline dependencies, a release's cursor,
-    // first record and that record's snapshot
-    const uint32_t pi = base + lane;
-    uint4 ea = make_uint4(0, 0, 0, 0), eb = make_uint4(0, 0, 0, 0);
+  // plan entries in registers: the current batch of 32 and the next one; a release
+  // entry's lane also holds its cursor (forwarded when an earlier release of the same
+  // lock moves it)
+  uint4 ea, eb, ea2, eb2;
+  uint32_t pre, pre2;
+  auto load_batch = [&](uint32_t b0, uint4& xa, uint4& xb, uint32_t& xp) {
+    const uint32_t pi = b0 + lane;
+    xa = make_uint4(0, 0, 0, 0);
+    xb = make_uint4(0, 0, 0, 0);
+    xp = 0;
     if (pi < pe) {
-      ea = a.plan[2 * size_t(pi)];
-      eb = a.plan[2 * size_t(pi) + 1];
+      xa = a.plan[2 * size_t(pi)];
+      xb = a.plan[2 * size_t(pi) + 1];
+      if ((xa.x & 0xFF) == P_REL) xp = __ldcg(cursor_row + xa.w);
     }
-    const uint32_t my_t = ea.x & 0xFF;
-    uint32_t pre = 0;
-    if (pi < pe) {
-      if (my_t == P_REL) {
-        pre = __ldcg(cursor_row + ea.w);
-        if (eb.x + pre < eb.y) {
-          prefetch_l1(a.recmeta + eb.x + pre);
-          prefetch_row<K>(a.hsnap + size_t(eb.x + pre) * g.Wp);
+  };
+  uint32_t base = pb;
+  load_batch(base, ea, eb, pre);
+  load_batch(base + 32, ea2, eb2, pre2);
+
+  auto stage = [&](uint32_t p) {
+    if constexpr (R > 0) {
+      if (p < pe) {
+        const bool second = p >= base + 32;
+        const int src = int((p - base) & 31);
+        const uint32_t t2 = __shfl_sync(0xffffffffu, second ? ea2.x : ea.x, src) & 0xFF;
+        const uint32_t w2 = __shfl_sync(0xffffffffu, second ? ea2.w : ea.w, src);
+        const uint32_t x0 = __shfl_sync(0xffffffffu, second ? eb2.x : eb.x, src);
+        const uint32_t x1 = __shfl_sync(0xffffffffu, second ? eb2.y : eb.y, src);
+        const uint32_t x2 = __shfl_sync(0xffffffffu, second ? eb2.z : eb.z, src);
+        const uint32_t x3 = __shfl_sync(0xffffffffu, second ? eb2.w : eb.w, src);
+        const uint32_t pr = __shfl_sync(0xffffffffu, second ? pre2 : pre, src);
+        uint32_t* slot = ring + (p % R) * SLOT;
+        uint32_t kind = 0, nrows = 0, cur_staged = 0;
+        if (t2 == P_ACQ && w2 >= 1 && w2 <= 2) {
+          stage_row<Wc>(slot, a.psnap + size_t(x0) * Wc);
+          stage_row<Wc>(slot + Wc, a.hsnap + size_t(x0) * Wc);
+          if (w2 == 2) {
+            stage_row<Wc>(slot + 2 * Wc, a.psnap + size_t(x1) * Wc);
+            stage_row<Wc>(slot + 3 * Wc, a.hsnap + size_t(x1) * Wc);
+          }
+          kind = 1;
+          nrows = 2 * w2;
+        } else if (t2 == P_INCS && w2 >= 1 && w2 <= 4) {
+          const uint32_t ids[4] = {x0, x1, x2, x3};
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (q < int(w2)) stage_row<Wc>(slot + q * Wc, a.hsnap + size_t(ids[q]) * Wc);
+          kind = 1;
+          nrows = w2;
+        } else if (t2 == P_REL) {
+          const uint32_t lo = x0, hi = x1;
+          cur_staged = pr;
+          if (lo + pr + lane < hi) cp_async16(slot + 4 * lane, a.recmeta + lo + pr + lane);
+          if (lo + pr < hi) stage_row<Wc>(slot + 128, a.hsnap + size_t(lo + pr) * Wc);
+          kind = 2;
         }
-      } else if ((my_t == P_ACQ || my_t == P_INCS) && ea.w <= 4) {
-        const uint32_t ids[4] = {eb.x, eb.y, eb.z, eb.w};
-        for (uint32_t q = 0; q < ea.w; ++q) {
-          if (my_t == P_ACQ) prefetch_row<K>(a.psnap + size_t(ids[q]) * g.Wp);
-          prefetch_row<K>(a.hsnap + size_t(ids[q]) * g.Wp);
+        if (lane == 0) {
+          slot[SLOT - 4] = kind;
+          slot[SLOT - 3] = cur_staged;
+          slot[SLOT - 2] = nrows;
         }
       }
+      cp_async_commit();
     }
-    const uint32_t nb = min(32u, pe - base);
-    for (uint32_t i = 0; i < nb; ++i) {
-      const uint32_t t = __shfl_sync(0xffffffffu, ea.x, i) & 0xFF;
-      const uint32_t row = __shfl_sync(0xffffffffu, ea.y, i);
-      const uint32_t z = __shfl_sync(0xffffffffu, ea.z, i);
-      const uint32_t w = __shfl_sync(0xffffffffu, ea.w, i);
-      if (t == P_ACQ || t == P_INCS) {
-        // acquire (Algorithm 1): P_t |= P_<l,s'>, H_t |= H_<l,s'> over the overlapping
-        // scopes' latest releases; in-section access (Algorithm 2): P_t |= L^w (| L^r)
-        const uint32_t* list = t == P_ACQ ? a.pool : a.flat;
-        for (uint32_t q0 = 0; q0 < w; q0 += 4) {
-          uint32_t ids[4];
-          if (w <= 4) {
-            ids[0] = __shfl_sync(0xffffffffu, eb.x, i);
-            ids[1] = __shfl_sync(0xffffffffu, eb.y, i);
-            ids[2] = __shfl_sync(0xffffffffu, eb.z, i);
-            ids[3] = __shfl_sync(0xffffffffu, eb.w, i);
+  };
+  for (int q = 0; q < R - 1; ++q) stage(pb + q);
+
+  for (uint32_t p = pb; p < pe; ++p) {
+    const uint32_t i = p - base;
+    __syncwarp();
+    stage(p + R - 1);
+    uint32_t skind = 0;
+    const uint32_t* slot = ring + (R > 0 ? (p % RR) : 0) * SLOT;
+    if constexpr (R > 0) {
+      cp_async_wait<(R > 0 ? R - 1 : 0)>();
+      __syncwarp();
+      skind = slot[SLOT - 4];
+    }
+    const uint32_t t = __shfl_sync(0xffffffffu, ea.x, i) & 0xFF;
+    const uint32_t row = __shfl_sync(0xffffffffu, ea.y, i);
+    const uint32_t z = __shfl_sync(0xffffffffu, ea.z, i);
+    const uint32_t w = __shfl_sync(0xffffffffu, ea.w, i);
+    if ((t == P_ACQ || t == P_INCS) && skind == 1) {
+      // staged rows: validate (an incomplete one is re-read from L2), then join
+      const int nrows = int(slot[SLOT - 2]);
+      const uint32_t ids[4] = {__shfl_sync(0xffffffffu, eb.x, i), __shfl_sync(0xffffffffu, eb.y, i),
+                               __shfl_sync(0xffffffffu, eb.z, i), __shfl_sync(0xffffffffu, eb.w, i)};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (q < nrows) {
+          uint32_t y[K];
+          read_row_shared<K>(slot + q * Wc, y);
+          const bool acq = t == P_ACQ;
+          const uint32_t* src = acq ? ((q & 1) ? a.hsnap : a.psnap) + size_t(ids[q >> 1]) * Wc
+                                    : a.hsnap + size_t(ids[q]) * Wc;
+          if (!row_complete<K>(y)) wait_row<K>(src, y, abort, a.st);
+          if (acq && (q & 1)) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) H[j] = max(H[j], y[j]);
           } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) ids[q] = q0 + q < w ? __ldcg(list + z + q0 + q) : 0;
+            for (int j = 0; j < K; ++j) P[j] = max(P[j], y[j]);
           }
-          const int n = int(min(4u, w - q0));
-          if (t == P_ACQ) {
-            join_rows2<K, 4>(P, a.psnap, H, a.hsnap, ids, n, g.Wp, abort, a.st);
-            joins += 2 * n;
-          } else {
-            join_rows<K, 4>(P, a.hsnap, ids, n, g.Wp, abort, a.st);
+        }
+      }
+      joins += nrows;
+    } else if (t == P_ACQ || t == P_INCS) {
+      // acquire (Algorithm 1): P_t |= P_<l,s'>, H_t |= H_<l,s'> over the overlapping
+      // scopes' latest releases; in-section access (Algorithm 2): P_t |= L^w (| L^r)
+      const uint32_t* list = t == P_ACQ ? a.pool : a.flat;
+      for (uint32_t q0 = 0; q0 < w; q0 += 4) {
+        uint32_t ids[4];
+        if (w <= 4) {
+          ids[0] = __shfl_sync(0xffffffffu, eb.x, i);
+          ids[1] = __shfl_sync(0xffffffffu, eb.y, i);
+          ids[2] = __shfl_sync(0xffffffffu, eb.z, i);
+          ids[3] = __shfl_sync(0xffffffffu, eb.w, i);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ids[q] = q0 + q < w ? __ldcg(list + z + q0 + q) : 0;
+        }
+        const int n = int(min(4u, w - q0));
+        if (t == P_ACQ) {
+          join_rows2<K, 4>(P, a.psnap, H, a.hsnap, ids, n, Wc, abort, a.st);
+          joins += 2 * n;
+        } else {
+          join_rows<K, 4>(P, a.hsnap, ids, n, Wc, abort, a.st);
+          joins += n;
+        }
+      }
+    } else if (t == P_REL) {
+      // release (Algorithm 1): pop other agents' records on this lock while their
+      // acquire is ordered before C_t; join the released ones whose scope overlaps.
+      // Waves: every record before the first one failing the test against the current
+      // P passes (P only grows), so their snapshots are joined together; the failing
+      // record is tested again only if the wave changed P.
+      const uint32_t c = z, L = w;
+      const uint32_t lo = __shfl_sync(0xffffffffu, eb.x, i), hi = __shfl_sync(0xffffffffu, eb.y, i);
+      const uint32_t s = __shfl_sync(0xffffffffu, eb.z, i), my_idx = __shfl_sync(0xffffffffu, eb.w, i);
+      uint32_t cur = __shfl_sync(0xffffffffu, pre, i);
+      bool staged = skind == 2 && slot[SLOT - 3] == cur;
+      bool stop = false;
+      while (!stop && lo + cur < hi) {
+        const uint32_t rec = lo + cur + lane;
+        const uint32_t nbr = min(32u, hi - (lo + cur));
+        uint4 m = make_uint4(NONE, 0, NONE, 0);
+        uint32_t spec[K];
+        if (staged) {  // the first 32 records and the first one's snapshot are in the slot
+          if (rec < hi) m = *reinterpret_cast<const uint4*>(slot + 4 * lane);
+          read_row_shared<K>(slot + 128, spec);
+        } else {
+          if (rec < hi) m = __ldg(a.recmeta + rec);
+          load_row<K>(a.hsnap + size_t(lo + cur) * Wc, spec);
+        }
+        staged = false;
+        bool spec_live = true;
+        const bool mine = m.x == u;
+        const bool joinable = !mine && m.z != NONE && m.z < my_idx && scopes_overlap(m.w, s);
+        uint32_t start = 0;
+        while (start < nbr) {
+          const uint32_t pv = lookup_entry<K>(P, m.x);
+          const bool in = uint32_t(lane) >= start && uint32_t(lane) < nbr;
+          const uint32_t fail = __ballot_sync(0xffffffffu, in && !mine && m.y > pv);
+          const uint32_t f = fail ? uint32_t(__ffs(fail) - 1) : nbr;  // first failing record
+          const uint32_t wave = __ballot_sync(0xffffffffu, in && uint32_t(lane) < f && joinable);
+          visits += __popc(__ballot_sync(0xffffffffu, in && uint32_t(lane) <= f && !mine));
+          uint32_t wm = wave;
+          if (spec_live && (wm & 1u)) {  // record lo + cur: its row is already loaded
+            if (!row_complete<K>(spec)) wait_row<K>(a.hsnap + size_t(lo + cur) * Wc, spec, abort, a.st);
+#pragma unroll
+            for (int j = 0; j < K; ++j) P[j] = max(P[j], spec[j]);
+            ++joins;
+            wm &= ~1u;
+          }
+          spec_live = false;
+          while (wm) {
+            uint32_t ids[4];
+            int n = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              ids[q] = 0;
+              if (wm) {
+                ids[q] = lo + cur + (__ffs(wm) - 1);
+                wm &= wm - 1;
+                ++n;
+              }
+            }
+            join_rows<K, 4>(P, a.hsnap, ids, n, Wc, abort, a.st);
             joins += n;
           }
-        }
-      } else if (t == P_REL) {
-        // release (Algorithm 1): pop other agents' records on this lock while their
-        // acquire is ordered before C_t; join the released ones whose scope overlaps.
-        // Waves: every record before the first one failing the test against the
-        // current P passes (P only grows), so their snapshots are joined together;
-        // the failing record is tested again only if the wave changed P.
-        const uint32_t c = z, L = w;
-        const uint32_t lo = __shfl_sync(0xffffffffu, eb.x, i), hi = __shfl_sync(0xffffffffu, eb.y, i);
-        const uint32_t s = __shfl_sync(0xffffffffu, eb.z, i), my_idx = __shfl_sync(0xffffffffu, eb.w, i);
-        uint32_t cur = __shfl_sync(0xffffffffu, pre, i);
-        bool stop = false;
-        while (!stop && lo + cur < hi) {
-          const uint32_t rec = lo + cur + lane;
-          const uint32_t nbr = min(32u, hi - (lo + cur));
-          const uint4 m = rec < hi ? __ldg(a.recmeta + rec) : make_uint4(NONE, 0, NONE, 0);
-          // the first record's snapshot, loaded beside its metadata: used if it is joined
-          uint32_t spec[K];
-          load_row_l1<K>(a.hsnap + size_t(lo + cur) * g.Wp, spec);
-          bool spec_live = true;
-          const bool mine = m.x == u;
-          const bool joinable = !mine && m.z != NONE && m.z < my_idx && scopes_overlap(m.w, s);
-          uint32_t start = 0;
-          while (start < nbr) {
-            const uint32_t pv = lookup_entry<K>(P, m.x);
-            const bool in = uint32_t(lane) >= start && uint32_t(lane) < nbr;
-            const uint32_t fail = __ballot_sync(0xffffffffu, in && !mine && m.y > pv);
-            const uint32_t f = fail ? uint32_t(__ffs(fail) - 1) : nbr;  // first failing record
-            const uint32_t wave = __ballot_sync(0xffffffffu, in && uint32_t(lane) < f && joinable);
-            visits += __popc(__ballot_sync(0xffffffffu, in && uint32_t(lane) <= f && !mine));
-            uint32_t wm = wave;
-            if (spec_live && (wm & 1u)) {  // record lo + cur: its row is already loaded
-              if (!row_complete<K>(spec)) wait_row<K>(a.hsnap + size_t(lo + cur) * g.Wp, spec, abort, a.st);
-#pragma unroll
-              for (int j = 0; j < K; ++j) P[j] = max(P[j], spec[j]);
-              ++joins;
-              wm &= ~1u;
-            }
-            spec_live = false;
-            while (wm) {
-              uint32_t ids[4];
-              int n = 0;
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                ids[q] = 0;
-                if (wm) {
-                  ids[q] = lo + cur + (__ffs(wm) - 1);
-                  wm &= wm - 1;
-                  ++n;
-                }
-              }
-              join_rows<K, 4>(P, a.hsnap, ids, n, g.Wp, abort, a.st);
-              joins += n;
-            }
-            if (f == nbr) {
-              start = nbr;
-            } else if (wave) {
-              start = f;  // P grew: test the failing record again
-            } else {
-              stop = true;  // P unchanged: the record stays unordered
-              start = f;
-              break;
-            }
+          if (f == nbr) {
+            start = nbr;
+          } else if (wave) {
+            start = f;  // P grew: test the failing record again
+          } else {
+            stop = true;  // P unchanged: the record stays unordered
+            start = f;
+            break;
           }
-          cur += start;
         }
-        if (lane == 0) __stcg(cursor_row + L, cur);
-        if (lane > int(i) && my_t == P_REL && ea.w == L) pre = cur;  // later releases of L
-        store_row<K>(a.psnap + size_t(c) * g.Wp, P);
-        store_row<K>(a.hsnap + size_t(c) * g.Wp, H);
-        set_entry<K>(H, u, N + 1);  // H_t[t]++ (H_t[t] = N_t)
-        ++N;
-      } else {
-        // sync (Algorithm 1): join C_t and H_t over the barrier's scope
-        const uint32_t mode = __shfl_sync(0xffffffffu, eb.x, i);
-        uint32_t C[K];
+        cur += start;
+      }
+      if (lane == 0) __stcg(cursor_row + L, cur);
+      // later releases of L, in this batch and the next, start from the new cursor
+      if (lane > int(i) && (ea.x & 0xFF) == P_REL && ea.w == L) pre = cur;
+      if ((ea2.x & 0xFF) == P_REL && ea2.w == L) pre2 = cur;
+      store_row<K>(a.psnap + size_t(c) * Wc, P);
+      store_row<K>(a.hsnap + size_t(c) * Wc, H);
+      set_entry<K>(H, u, N + 1);  // H_t[t]++ (H_t[t] = N_t)
+      ++N;
+    } else {
+      // sync (Algorithm 1): join C_t and H_t over the barrier's scope
+      const uint32_t mode = __shfl_sync(0xffffffffu, eb.x, i);
+      uint32_t C[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) C[j] = P[j];
-        set_entry<K>(C, u, N);
-        if (mode == BAR_SINGLE) {
+      for (int j = 0; j < K; ++j) C[j] = P[j];
+      set_entry<K>(C, u, N);
+      if (mode == BAR_SINGLE) {
 #pragma unroll
-          for (int j = 0; j < K; ++j) P[j] = C[j];
-        } else if (mode == BAR_CTA) {
-          uint32_t* buf = xchg + size_t(nbar & 1) * nwarps * 2 * g.Wp;
-          store_row_shared<K>(buf + size_t(warp) * 2 * g.Wp, C);
-          store_row_shared<K>(buf + size_t(warp) * 2 * g.Wp + g.Wp, H);
-          __syncthreads();
+        for (int j = 0; j < K; ++j) P[j] = C[j];
+      } else if (mode == BAR_CTA) {
+        uint32_t* buf = xchg + size_t(nbar & 1) * nwarps * 2 * Wc;
+        store_row_shared<K>(buf + size_t(warp) * 2 * Wc, C);
+        store_row_shared<K>(buf + size_t(warp) * 2 * Wc + Wc, H);
+        __syncthreads();
 #pragma unroll
-          for (int j = 0; j < K; ++j) P[j] = H[j] = 0;
-          for (int wv = 0; wv < nwarps; ++wv) {
-            const uint32_t* src = buf + size_t(wv) * 2 * g.Wp + lane * K;
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-              P[j] = max(P[j], src[j]);
-              H[j] = max(H[j], src[g.Wp + j]);
-            }
-          }
-          joins += 2 * nwarps;
-          ++nbar;
-        } else {
-          const uint32_t bid = z, count = w;
-          uint32_t* J = a.bar_j + size_t(bid) * 2 * g.Wp;
+        for (int j = 0; j < K; ++j) P[j] = H[j] = 0;
+        for (int wv = 0; wv < nwarps; ++wv) {
+          const uint32_t* srcp = buf + size_t(wv) * 2 * Wc + lane * K;
 #pragma unroll
           for (int j = 0; j < K; ++j) {
-            atomicMax(J + lane * K + j, C[j]);
-            atomicMax(J + g.Wp + lane * K + j, H[j]);
+            P[j] = max(P[j], srcp[j]);
+            H[j] = max(H[j], srcp[Wc + j]);
           }
-          __threadfence();
-          __syncwarp();
-          if (lane == 0) atomicAdd(a.bar_cnt + bid, 1u);
-          if (!abort) {
-            bool ok = true;
-            if (lane == 0) {
-              uint32_t it = 0;
-              while (ld_acquire(a.bar_cnt + bid) < count) {
-                if (++it > kSpinLimit) {
-                  ok = false;
-                  break;
-                }
-                __nanosleep(64);
-              }
-              if (!ok) atomicCAS(&a.st->code, 0, GWCP_ERR_TIMEOUT);
-            }
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            __syncwarp();
-            if (!ok) abort = true;
-          }
-          load_row<K>(J, P);
-          load_row<K>(J + g.Wp, H);
-          joins += 2;
         }
-        set_entry<K>(H, u, N + 1);
-        ++N;
+        joins += 2 * nwarps;
+        ++nbar;
+      } else {
+        const uint32_t bid = z, count = w;
+        uint32_t* J = a.bar_j + size_t(bid) * 2 * Wc;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          atomicMax(J + lane * K + j, C[j]);
+          atomicMax(J + Wc + lane * K + j, H[j]);
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicAdd(a.bar_cnt + bid, 1u);
+        if (!abort) {
+          bool ok = true;
+          if (lane == 0) {
+            uint32_t it = 0;
+            while (ld_acquire(a.bar_cnt + bid) < count) {
+              if (++it > kSpinLimit) {
+                ok = false;
+                break;
+              }
+              __nanosleep(64);
+            }
+            if (!ok) atomicCAS(&a.st->code, 0, GWCP_ERR_TIMEOUT);
+          }
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          __syncwarp();
+          if (!ok) abort = true;
+        }
+        load_row<K>(J, P);
+        load_row<K>(J + Wc, H);
+        joins += 2;
       }
-      store_row<K>(a.rows + size_t(row) * g.Wp, P);
+      set_entry<K>(H, u, N + 1);
+      ++N;
+    }
+    store_row<K>(a.rows + size_t(row) * Wc, P);
+    if (i == 31) {  // next batch
+      base += 32;
+      ea = ea2;
+      eb = eb2;
+      pre = pre2;
+      load_batch(base + 32, ea2, eb2, pre2);
     }
   }
+  if constexpr (R > 0) cp_async_wait<0>();
   if (lane == 0) {
     atomicAdd(&a.st->joins, (unsigned long long)joins);
     atomicAdd(&a.st->loop_visits, (unsigned long long)visits);
@@ -553,9 +653,10 @@ __global__ void k_plan_incs(PropArgs a, const uint32_t* incs_k, const uint32_t* 
                                : make_uint4(0, 0, 0, 0);
 }
 
-template <int K>
-int launch(const PropArgs& a, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t s) {
-  auto kern = k_propagate<K>;
+template <int K, int R, int MAXT>
+int launch(const PropArgs& a, uint32_t grid, uint32_t threads, size_t smem_xchg, cudaStream_t s) {
+  auto kern = k_propagate<K, R, MAXT>;
+  const size_t smem = smem_xchg + (R > 0 ? size_t(threads / 32) * R * slot_words<K>() * 4 : 0);
   if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)))
     return GWCP_ERR_UNSUPPORTED;
   int dev = 0, sms = 0, per_sm = 0;
@@ -571,6 +672,18 @@ int launch(const PropArgs& a, uint32_t grid, uint32_t threads, size_t smem, cuda
     return GWCP_ERR_CUDA;
   count_launch();
   return GWCP_OK;
+}
+
+// ring depth: deepest that keeps a CTA's shared memory within budget
+template <int K>
+int launch_k(const PropArgs& a, uint32_t grid, uint32_t threads, size_t smem_xchg, cudaStream_t s) {
+  const size_t per_slot = size_t(threads / 32) * slot_words<K>() * 4;
+  constexpr size_t kBudget = 160 * 1024;
+  if constexpr (K <= 4) {
+    if (threads <= 256 && smem_xchg + 8 * per_slot <= kBudget) return launch<K, 8, 256>(a, grid, threads, smem_xchg, s);
+    if (smem_xchg + 2 * per_slot <= kBudget) return launch<K, 2, 1024>(a, grid, threads, smem_xchg, s);
+  }
+  return launch<K, 0, 1024>(a, grid, threads, smem_xchg, s);
 }
 
 }  // namespace
@@ -654,12 +767,12 @@ int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s
   p.begin("g_propagate", double(z.n_rows) * g.Wp * 4 + double(z.n_cs) * 2 * g.Wp * 4);
   int rc;
   switch (g.K) {
-    case 1: rc = launch<1>(a, grid, threads, smem, s); break;
-    case 2: rc = launch<2>(a, grid, threads, smem, s); break;
-    case 4: rc = launch<4>(a, grid, threads, smem, s); break;
-    case 8: rc = launch<8>(a, grid, threads, smem, s); break;
-    case 16: rc = launch<16>(a, grid, threads, smem, s); break;
-    case 32: rc = launch<32>(a, grid, threads, smem, s); break;
+    case 1: rc = launch_k<1>(a, grid, threads, smem, s); break;
+    case 2: rc = launch_k<2>(a, grid, threads, smem, s); break;
+    case 4: rc = launch_k<4>(a, grid, threads, smem, s); break;
+    case 8: rc = launch_k<8>(a, grid, threads, smem, s); break;
+    case 16: rc = launch_k<16>(a, grid, threads, smem, s); break;
+    case 32: rc = launch_k<32>(a, grid, threads, smem, s); break;
     default: rc = GWCP_ERR_UNSUPPORTED;
   }
   p.end();
