@@ -183,6 +183,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   b.cs_sid = get<uint32_t>(c, "cs_sid", na1, &oom);
   b.cs_epoch = get<uint32_t>(c, "cs_epoch", na1, &oom);
   b.cs_rel_idx = get<uint32_t>(c, "cs_rel_idx", na1, &oom);
+  b.cs_rel_epoch = get<uint32_t>(c, "cs_rel_epoch", na1, &oom);
   b.cs_lock = get<uint32_t>(c, "cs_lock", na1, &oom);
   b.cs_parent = get<uint32_t>(c, "cs_parent", na1, &oom);
   b.acq_dep_off = get<uint32_t>(c, "acq_dep_off", na1, &oom);

@@ -111,6 +111,7 @@ struct Bufs {
   uint32_t* cs_sid = nullptr;
   uint32_t* cs_epoch = nullptr;
   uint32_t* cs_rel_idx = nullptr;
+  uint32_t* cs_rel_epoch = nullptr;  // N of the releasing agent at the release
   uint32_t* cs_lock = nullptr;
   uint32_t* cs_parent = nullptr;
   uint32_t* acq_dep_off = nullptr;  // [n_cs]

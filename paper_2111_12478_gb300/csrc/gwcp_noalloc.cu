@@ -145,7 +145,8 @@ int analyze(const Event* ev, uint64_t n, const Geo& g, gwcp_race* out, uint64_t 
   b.lk_key = A.take<uint64_t>(na1);
   b.lk_key2 = A.take<uint64_t>(na1);
   uint32_t** lk[] = {&b.lk_k, &b.lk_k2, &b.lk_flags, &b.lk_csid, &b.lk_rank, &b.cs_agent, &b.cs_sid,
-                     &b.cs_epoch, &b.cs_rel_idx, &b.cs_lock, &b.cs_parent, &b.acq_dep_off, &b.acq_dep_cnt};
+                     &b.cs_epoch, &b.cs_rel_idx, &b.cs_rel_epoch, &b.cs_lock, &b.cs_parent, &b.acq_dep_off,
+                     &b.acq_dep_cnt};
   for (uint32_t** q : lk) *q = A.take<uint32_t>(na1);
   b.lock_first = A.take<uint32_t>(na1 + 1);
   b.lock_cs_lo = A.take<uint32_t>(na1 + 1);

@@ -447,7 +447,8 @@ __global__ void k_e_assign(const Event* ev, Geo g, const uint32_t* kk, uint32_t 
                            const uint32_t* csid, const uint32_t* newscan, const uint32_t* sy_kind,
                            const uint32_t* sy_idx, const uint32_t* sy_N, const uint32_t* sy_relk,
                            uint32_t* cs_of_sync, uint32_t* cs_agent, uint32_t* cs_sid, uint32_t* cs_epoch,
-                           uint32_t* cs_rel_idx, uint32_t* cs_lock, uint32_t* lock_first, uint32_t* lock_cs_lo) {
+                           uint32_t* cs_rel_idx, uint32_t* cs_rel_epoch, uint32_t* cs_lock, uint32_t* lock_first,
+                           uint32_t* lock_cs_lo) {
   uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n) return;
   const uint32_t k = kk[m];
@@ -469,6 +470,7 @@ __global__ void k_e_assign(const Event* ev, Geo g, const uint32_t* kk, uint32_t 
   cs_epoch[c] = sy_N[k];
   cs_lock[c] = lr;
   cs_rel_idx[c] = sy_relk[k] != NONE ? sy_idx[sy_relk[k]] : NONE;
+  cs_rel_epoch[c] = sy_relk[k] != NONE ? sy_N[sy_relk[k]] - 1 : 0;  // N before the release's increment
 }
 
 __global__ void k_e_assign_rel(const uint32_t* kk, uint32_t n, const uint32_t* sy_kind, const uint32_t* sy_match,
@@ -790,7 +792,7 @@ void phaseE_walk(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Pr
   const uint32_t* newscan = b.lk_flags;
   k_e_assign<<<blocks(n, 256), 256, 0, s>>>(b.ev, g, b.lk_k, n, newflag, b.lk_csid, newscan, b.sy_kind, b.sy_idx,
                                             b.sy_N, b.sy_relk, b.cs_of_sync, b.cs_agent, b.cs_sid, b.cs_epoch,
-                                            b.cs_rel_idx, b.cs_lock, b.lock_first, b.lock_cs_lo);
+                                            b.cs_rel_idx, b.cs_rel_epoch, b.cs_lock, b.lock_first, b.lock_cs_lo);
   count_launch();
   k_e_assign_rel<<<blocks(n, 256), 256, 0, s>>>(b.lk_k, n, b.sy_kind, b.sy_match, b.cs_of_sync, b.cs_parent);
   count_launch();

@@ -33,7 +33,7 @@ struct PropArgs {
   const uint32_t *sy_start, *sy_idx, *sy_kind, *sy_N, *sy_ver, *sy_aux;
   const uint32_t *incs_off, *incs_ver, *incs_k, *exp_off, *ex_dep_off, *ex_dep_cnt;
   const uint32_t* rowbase;
-  const uint32_t *cs_of_sync, *cs_agent, *cs_sid, *cs_epoch, *cs_rel_idx, *cs_lock, *lock_cs_lo;
+  const uint32_t *cs_of_sync, *cs_agent, *cs_sid, *cs_epoch, *cs_rel_idx, *cs_lock, *lock_cs_lo, *cs_rel_epoch;
   const uint32_t *acq_dep_off, *acq_dep_cnt, *pool;
   const uint32_t* flat;
   uint4* plan;
@@ -244,7 +244,7 @@ __host__ __device__ constexpr int slot_words() {
 // R > 0: a ring of R shared-memory slots per warp; while entry p is processed, the
 // copies for entry p + R - 1 are in flight (one commit group per entry).
 template <int K, int R, int MAXT>
-__global__ void __launch_bounds__(MAXT) k_propagate(PropArgs a) {
+__global__ void __launch_bounds__(MAXT, 1) k_propagate(PropArgs a) {
   constexpr int Wc = 32 * K;
   constexpr int SLOT = slot_words<K>();
   constexpr int RR = R > 0 ? R : 1;
@@ -255,6 +255,8 @@ __global__ void __launch_bounds__(MAXT) k_propagate(PropArgs a) {
   uint32_t* const xchg = sm;  // CTA barriers: [2 buffers][warps][C | H][Wp]
   const uint32_t xchg_words = a.cta_barriers ? 2u * nwarps * 2 * Wc : 0u;
   uint32_t* const ring = sm + xchg_words + (R > 0 ? size_t(warp) * RR * SLOT : 0);  // unused when R = 0
+  // per-warp scratch for folding joined release epochs into jn (stale words never exceed jn)
+  uint32_t* const jn_tmp = sm + xchg_words + (R > 0 ? size_t(nwarps) * RR * SLOT : 0) + size_t(warp) * Wc;
   // one read of the status per CTA, so all warps of a CTA agree on whether to run
   __shared__ int start_code;
   if (threadIdx.x == 0) start_code = *(volatile int*)&a.st->code;
@@ -262,10 +264,16 @@ __global__ void __launch_bounds__(MAXT) k_propagate(PropArgs a) {
   if (start_code) return;
   const bool active = a.cta_barriers ? (uint32_t(warp) < g.apb) : (u < g.W);
   if (!active) return;
+  for (int j = lane; j < Wc; j += 32) jn_tmp[j] = 0;
+  __syncwarp();
 
   uint32_t P[K], H[K];
+  // jn[v]: latest release epoch of agent v whose H snapshot is already joined into P.
+  // H of one agent only grows along its timeline, so a release of v with epoch <= jn[v]
+  // is dominated and its join is a no-op.
+  uint32_t jn[K];
 #pragma unroll
-  for (int j = 0; j < K; ++j) P[j] = H[j] = 0;
+  for (int j = 0; j < K; ++j) P[j] = H[j] = jn[j] = 0;
   set_entry<K>(H, u, 1u);  // H_t = bottom{t := 1}
   uint32_t N = 1;          // N_t
   bool abort = false;
@@ -433,17 +441,32 @@ __global__ void __launch_bounds__(MAXT) k_propagate(PropArgs a) {
         }
         staged = false;
         bool spec_live = true;
-        const bool mine = m.x == u;
-        const bool joinable = !mine && m.z != NONE && m.z < my_idx && scopes_overlap(m.w, s);
+        const uint32_t mag = m.x == NONE ? NONE : (m.x & 0xFFFF);
+        const uint32_t msid = m.x >> 16;
+        const bool mine = mag == u;
+        const bool joinable = !mine && m.z != NONE && m.z < my_idx && scopes_overlap(msid, s);
         uint32_t start = 0;
         while (start < nbr) {
-          const uint32_t pv = lookup_entry<K>(P, m.x);
+          const uint32_t pv = lookup_entry<K>(P, mag);
+          const uint32_t jv = lookup_entry<K>(jn, mag);
           const bool in = uint32_t(lane) >= start && uint32_t(lane) < nbr;
           const uint32_t fail = __ballot_sync(0xffffffffu, in && !mine && m.y > pv);
           const uint32_t f = fail ? uint32_t(__ffs(fail) - 1) : nbr;  // first failing record
-          const uint32_t wave = __ballot_sync(0xffffffffu, in && uint32_t(lane) < f && joinable);
+          const uint32_t popped = __ballot_sync(0xffffffffu, in && uint32_t(lane) < f && joinable);
+          // of the popped releases, join only those not dominated, and per agent only
+          // the latest (records of one agent are in acquire order)
+          const bool cand = ((popped >> lane) & 1u) && m.w > jv;
+          const uint32_t same = __match_any_sync(0xffffffffu, cand ? mag : 0xFFFFFFFFu);
+          const uint32_t wave = __ballot_sync(0xffffffffu, cand && (same >> lane) <= 1u);
           visits += __popc(__ballot_sync(0xffffffffu, in && uint32_t(lane) <= f && !mine));
           uint32_t wm = wave;
+          if (wave) {  // record the joined releases' epochs: distinct agents scatter, owners fold
+            if ((wave >> lane) & 1u) jn_tmp[mag] = m.w;
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < K; ++j) jn[j] = max(jn[j], jn_tmp[lane * K + j]);
+            __syncwarp();
+          }
           if (spec_live && (wm & 1u)) {  // record lo + cur: its row is already loaded
             if (!row_complete<K>(spec)) wait_row<K>(a.hsnap + size_t(lo + cur) * Wc, spec, abort, a.st);
 #pragma unroll
@@ -579,10 +602,13 @@ __device__ __forceinline__ uint32_t agent_of_sync(const uint32_t* sy_start, uint
   return lo - 1;
 }
 
+// section record as the release loop reads it: (agent | scope id << 16, acquire epoch,
+// release index, release epoch)
 __global__ void k_recmeta(uint32_t n_cs, const uint32_t* cs_agent, const uint32_t* cs_epoch,
-                          const uint32_t* cs_rel_idx, const uint32_t* cs_sid, uint4* recmeta) {
+                          const uint32_t* cs_rel_idx, const uint32_t* cs_sid, const uint32_t* cs_rel_epoch,
+                          uint4* recmeta) {
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < n_cs) recmeta[c] = make_uint4(cs_agent[c], cs_epoch[c], cs_rel_idx[c], cs_sid[c]);
+  if (c < n_cs) recmeta[c] = make_uint4(cs_agent[c] | (cs_sid[c] << 16), cs_epoch[c], cs_rel_idx[c], cs_rel_epoch[c]);
 }
 
 __global__ void k_flatcount(uint32_t n_incs, const uint32_t* exp_off, const uint32_t* ex_dep_cnt, uint32_t* cnt) {
@@ -656,7 +682,8 @@ __global__ void k_plan_incs(PropArgs a, const uint32_t* incs_k, const uint32_t* 
 template <int K, int R, int MAXT>
 int launch(const PropArgs& a, uint32_t grid, uint32_t threads, size_t smem_xchg, cudaStream_t s) {
   auto kern = k_propagate<K, R, MAXT>;
-  const size_t smem = smem_xchg + (R > 0 ? size_t(threads / 32) * R * slot_words<K>() * 4 : 0);
+  const size_t smem = smem_xchg + (R > 0 ? size_t(threads / 32) * R * slot_words<K>() * 4 : 0) +
+                     size_t(threads / 32) * 32 * K * 4;
   if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)))
     return GWCP_ERR_UNSUPPORTED;
   int dev = 0, sms = 0, per_sm = 0;
@@ -678,7 +705,7 @@ int launch(const PropArgs& a, uint32_t grid, uint32_t threads, size_t smem_xchg,
 template <int K>
 int launch_k(const PropArgs& a, uint32_t grid, uint32_t threads, size_t smem_xchg, cudaStream_t s) {
   const size_t per_slot = size_t(threads / 32) * slot_words<K>() * 4;
-  constexpr size_t kBudget = 160 * 1024;
+  const size_t kBudget = 160 * 1024 - size_t(threads / 32) * 32 * K * 4;
   if constexpr (K <= 4) {
     if (threads <= 256 && smem_xchg + 8 * per_slot <= kBudget) return launch<K, 8, 256>(a, grid, threads, smem_xchg, s);
     if (smem_xchg + 2 * per_slot <= kBudget) return launch<K, 2, 1024>(a, grid, threads, smem_xchg, s);
@@ -712,6 +739,7 @@ int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s
   a.cs_epoch = b.cs_epoch;
   a.cs_rel_idx = b.cs_rel_idx;
   a.cs_lock = b.cs_lock;
+  a.cs_rel_epoch = b.cs_rel_epoch;
   a.lock_cs_lo = b.lock_cs_lo;
   a.acq_dep_off = b.acq_dep_off;
   a.acq_dep_cnt = b.acq_dep_cnt;
@@ -732,7 +760,7 @@ int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s
   p.begin("g_plan", double(z.n_sync + z.n_incs) * 64 + double(z.n_cs) * 2 * g.Wp * 4);
   if (z.n_cs) {
     k_recmeta<<<(z.n_cs + 255) / 256, 256, 0, s>>>(z.n_cs, b.cs_agent, b.cs_epoch, b.cs_rel_idx, b.cs_sid,
-                                                    b.recmeta);
+                                                    b.cs_rel_epoch, b.recmeta);
     count_launch();
     // snapshot rows start as SENTINEL: a reader accepts a row once none is left
     cudaMemsetAsync(b.psnap, 0xFF, size_t(z.n_cs) * g.Wp * 4, s);
