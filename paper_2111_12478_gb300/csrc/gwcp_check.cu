@@ -21,16 +21,6 @@ constexpr uint32_t CH = 512;       // accesses per chunk (one warp)
 constexpr uint32_t GRP = 32;       // chunks per first-level scan group
 constexpr int CHK_WARPS = 4;
 
-__device__ __forceinline__ bool is_atomic_cls(uint32_t c) { return c >= C_ATOM_CTA; }
-
-// conflict and not exempt: at least one write-class access, and not two atomics with
-// overlapping scopes (same block, or either device-scoped)
-__device__ __forceinline__ bool counts(uint32_t ca, uint32_t cb, bool same_block) {
-  if (ca == C_READ && cb == C_READ) return false;
-  if (is_atomic_cls(ca) && is_atomic_cls(cb) && (ca == C_ATOM_DEV || cb == C_ATOM_DEV || same_block)) return false;
-  return true;
-}
-
 struct ChunkArgs {
   const uint64_t* key;
   const uint32_t* idx;
@@ -52,6 +42,23 @@ __device__ __forceinline__ bool chunk_continues(const ChunkArgs& a, uint32_t c) 
   return a.key[e - 1] == a.key[e];
 }
 
+// last[cl][ag % K] := v on the lane that owns agent ag. Below K = 32 the slot is chosen
+// by one bit over classes and one over the lane's K agents, a select per slot, which keeps
+// the table in registers; 4 * 32 slots do not fit there and are indexed in local memory.
+template <int K>
+__device__ __forceinline__ void put_slot(uint64_t (&last)[4][K], int lane, uint32_t ag, uint32_t cl, uint64_t v) {
+  if constexpr (K >= 32) {
+    if (uint32_t(lane) == ag / K) last[cl][ag % K] = v;
+  } else {
+    const uint32_t qsel = uint32_t(lane) == ag / K ? 1u << cl : 0u;
+    const uint32_t jsel = 1u << (ag % K);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int j = 0; j < K; ++j) last[q][j] = ((qsel >> q) & (jsel >> j) & 1u) ? v : last[q][j];
+  }
+}
+
 // State of the chunk's last location over the chunk's entries.
 template <int K>
 __global__ void k_tail(ChunkArgs a) {
@@ -70,28 +77,22 @@ __global__ void k_tail(ChunkArgs a) {
     const uint64_t tk = a.key[hi - 1];
     for (uint32_t b0 = lo; b0 < hi; b0 += 32) {
       const uint32_t p = b0 + lane;
-      uint64_t k = ~0ull;
-      AccInfo inf{};
-      uint32_t ix = 0;
-      if (p < hi) {
-        k = a.key[p];
+      bool mine = false;
+      uint32_t ix = 0, ep = 0, who = 0;
+      if (p < hi && a.key[p] == tk) {
+        mine = true;
         ix = a.idx[p];
-        inf = a.info[ix];
+        const AccInfo inf = a.info[ix];
+        ep = inf.epoch;
+        who = inf.who;
       }
-      const uint32_t nb = min(32u, hi - b0);
-      for (uint32_t i = 0; i < nb; ++i) {
-        if (__shfl_sync(0xffffffffu, k, i) != tk) continue;
-        const uint32_t ag = __shfl_sync(0xffffffffu, inf.agent, i);
-        const uint64_t v = (uint64_t(__shfl_sync(0xffffffffu, ix, i)) << 32) |
-                           __shfl_sync(0xffffffffu, inf.epoch, i);
-        const uint32_t cl = __shfl_sync(0xffffffffu, inf.cls, i);
-        if (uint32_t(lane) == ag / K) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-              if (q == int(cl) && j == int(ag % K)) last[q][j] = v;
-        }
+      uint32_t m = __ballot_sync(0xffffffffu, mine);
+      while (m) {
+        const int i = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t wb = __shfl_sync(0xffffffffu, who, i);
+        const uint64_t v = (uint64_t(__shfl_sync(0xffffffffu, ix, i)) << 32) | __shfl_sync(0xffffffffu, ep, i);
+        put_slot<K>(last, lane, who_agent(wb), who_class(wb), v);
       }
     }
   }
@@ -166,6 +167,18 @@ __global__ void k_scan3(ChunkArgs a, const uint64_t* gagg) {
   }
 }
 
+// classes a later access of class cb conflicts with and is not exempt from, as a 4-bit
+// mask over (read, write, block atomic, device atomic); `same` = the two agents share a
+// block (then two block-scoped atomics are exempt)
+__device__ __forceinline__ uint32_t conflict_mask(uint32_t cb, bool same) {
+  switch (cb) {
+    case C_READ: return 0b1110;
+    case C_WRITE: return 0b1111;
+    case C_ATOM_CTA: return same ? 0b0011 : 0b0111;
+    default: return 0b0011;  // device atomic: exempt against every atomic
+  }
+}
+
 template <int K>
 __global__ void __launch_bounds__(CHK_WARPS * 32) k_check(ChunkArgs a) {
   const int lane = threadIdx.x & 31;
@@ -174,66 +187,70 @@ __global__ void __launch_bounds__(CHK_WARPS * 32) k_check(ChunkArgs a) {
   const Geo& g = a.g;
   const uint32_t Wp = g.Wp;
   const uint32_t lo = c * CH, hi = min(lo + CH, a.n);
+  const uint32_t lt = lanemask_lt();
   uint64_t last[4][K];
-  uint64_t cur_key;
   if (c > 0 && chunk_continues(a, c - 1)) {
     const uint64_t* T = a.T + size_t(c - 1) * 4 * Wp;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int j = 0; j < K; ++j) last[q][j] = T[q * Wp + lane * K + j];
-    cur_key = a.key[lo];
   } else {
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int j = 0; j < K; ++j) last[q][j] = 0;
-    cur_key = a.key[lo];
   }
   uint32_t myblk[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) myblk[j] = (lane * K + j) / g.apb;
-  uint64_t tests = 0;
+  uint64_t prev_key = a.key[lo];  // the chunk's first location continues the carried state
+  uint32_t tests = 0;
   for (uint32_t b0 = lo; b0 < hi; b0 += 32) {
     const uint32_t p = b0 + lane;
     uint64_t k = ~0ull;
-    AccInfo inf{};
-    uint32_t ix = 0;
+    uint32_t ix = 0, ep = 0, rw = 0, who = 0;
     if (p < hi) {
       k = a.key[p];
       ix = a.idx[p];
-      inf = a.info[ix];
+      const AccInfo inf = a.info[ix];
+      ep = inf.epoch;
+      rw = inf.row;
+      who = inf.who;
     }
+    // accesses that start a new location in this round, found once for all 32
+    uint64_t kprev = __shfl_up_sync(0xffffffffu, k, 1);
+    if (lane == 0) kprev = prev_key;
+    const uint32_t starts = __ballot_sync(0xffffffffu, p < hi && k != kprev);
+    prev_key = __shfl_sync(0xffffffffu, k, 31);
     const uint32_t nb = min(32u, hi - b0);
     for (uint32_t i = 0; i < nb; ++i) {
-      const uint64_t kb = __shfl_sync(0xffffffffu, k, i);
-      const uint32_t ib = __shfl_sync(0xffffffffu, ix, i);
-      const uint32_t eb = __shfl_sync(0xffffffffu, inf.epoch, i);
-      const uint32_t rowb = __shfl_sync(0xffffffffu, inf.row, i);
-      const uint32_t ub = __shfl_sync(0xffffffffu, inf.agent, i);
-      const uint32_t cb = __shfl_sync(0xffffffffu, inf.cls, i);
-      if (kb != cur_key) {
-        cur_key = kb;
+      if ((starts >> i) & 1u) {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
           for (int j = 0; j < K; ++j) last[q][j] = 0;
       }
-      const uint32_t bu = ub / g.apb;
+      const uint32_t ib = __shfl_sync(0xffffffffu, ix, i);
+      const uint32_t eb = __shfl_sync(0xffffffffu, ep, i);
+      const uint32_t rowb = __shfl_sync(0xffffffffu, rw, i);
+      const uint32_t wb = __shfl_sync(0xffffffffu, who, i);
+      const uint32_t ub = who_agent(wb), cb = who_class(wb), bu = who_block(wb);
+      const uint32_t m_diff = conflict_mask(cb, false), m_same = conflict_mask(cb, true);
       uint64_t best[K];
       bool any = false;
 #pragma unroll
       for (int j = 0; j < K; ++j) {
-        best[j] = 0;
-        const uint32_t v = lane * K + j;
-        if (v == ub) continue;
+        const uint32_t m = myblk[j] == bu ? m_same : m_diff;
+        uint64_t b = 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (counts(uint32_t(q), cb, myblk[j] == bu)) best[j] = max(best[j], last[q][j]);
+        for (int q = 0; q < 4; ++q) b = ((m >> q) & 1u) ? max(b, last[q][j]) : b;
+        best[j] = (lane * K + j == ub) ? 0 : b;
         any |= best[j] != 0;
       }
-      uint32_t nr = 0;
-      uint64_t out[K];
+      bool race[K];
+#pragma unroll
+      for (int j = 0; j < K; ++j) race[j] = false;
       if (any) {
         uint32_t cv[K];
         const uint32_t* row = a.rows + size_t(rowb) * Wp + lane * K;
@@ -241,31 +258,34 @@ __global__ void __launch_bounds__(CHK_WARPS * 32) k_check(ChunkArgs a) {
         for (int j = 0; j < K; ++j) cv[j] = __ldg(row + j);
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-          if (!best[j]) continue;
-          ++tests;
-          if (uint32_t(best[j]) > cv[j]) out[nr++] = (uint64_t(ib) << 32) | (best[j] >> 32);
+          tests += best[j] != 0;
+          race[j] = best[j] != 0 && uint32_t(best[j]) > cv[j];  // N(a*) > C_b[v]
         }
       }
-      const uint32_t tot = __reduce_add_sync(0xffffffffu, nr);
-      if (tot) {
-        const uint32_t before = warp_inclusive_scan(nr) - nr;
+      // emit (a*, b) pairs: one ballot per register slot, positions by popcount
+      uint32_t cnt = 0, bal[K];
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        bal[j] = __ballot_sync(0xffffffffu, race[j]);
+        cnt += __popc(bal[j]);
+      }
+      if (cnt) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&a.st->n_races, (unsigned long long)tot);
-        base = __shfl_sync(0xffffffffu, base, 0) + before;
-        for (uint32_t q = 0; q < nr; ++q)
-          if (base + q < a.race_cap) a.races[base + q] = out[q];
-      }
-      if (uint32_t(lane) == ub / K) {
-        const uint64_t v = (uint64_t(ib) << 32) | eb;
+        if (lane == 0) base = atomicAdd(&a.st->n_races, (unsigned long long)cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int j = 0; j < K; ++j)
-            if (q == int(cb) && j == int(ub % K)) last[q][j] = v;
+        for (int j = 0; j < K; ++j) {
+          if (race[j]) {
+            const unsigned long long pos = base + __popc(bal[j] & lt);
+            if (pos < a.race_cap) a.races[pos] = (uint64_t(ib) << 32) | (best[j] >> 32);
+          }
+          base += __popc(bal[j]);
+        }
       }
+      put_slot<K>(last, lane, ub, cb, (uint64_t(ib) << 32) | eb);
     }
   }
-  tests = __reduce_add_sync(0xffffffffu, uint32_t(tests));
+  tests = __reduce_add_sync(0xffffffffu, tests);
   if (lane == 0 && tests) atomicAdd(&a.st->partner_tests, (unsigned long long)tests);
 }
 

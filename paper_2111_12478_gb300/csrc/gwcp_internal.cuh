@@ -54,9 +54,12 @@ struct Geo {
 struct AccInfo {
   uint32_t epoch;  // N_t of the access
   uint32_t row;    // global clock-version row holding P_t for the access
-  uint32_t agent;
-  uint32_t cls;    // C_READ ... C_ATOM_DEV
+  uint32_t who;    // agent | class << 10 | block << 12 (agent, block < 1024)
+  uint32_t pad;
 };
+__host__ __device__ inline uint32_t who_agent(uint32_t w) { return w & 0x3FFu; }
+__host__ __device__ inline uint32_t who_class(uint32_t w) { return (w >> 10) & 3u; }
+__host__ __device__ inline uint32_t who_block(uint32_t w) { return w >> 12; }
 
 // All device buffers of one analysis. Sizes in comments.
 struct Bufs {

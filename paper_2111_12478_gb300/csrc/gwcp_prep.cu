@@ -422,7 +422,7 @@ __global__ void k_d_fill(const Event* ev, Geo g, uint32_t n_sync, const uint32_t
     const Event e = ev[idx];
     const uint32_t cls = access_class(e);
     const uint32_t ver = incs ? vbase + j : vbase;
-    acc_info[idx] = AccInfo{epoch, rb + ver, u, cls};
+    acc_info[idx] = AccInfo{epoch, rb + ver, u | (cls << 10) | ((u / g.apb) << 12), 0};
     if (incs) {
       const uint32_t r = incs_off[k] + j - 1;
       incs_idx[r] = idx;
