@@ -132,38 +132,20 @@ __device__ __forceinline__ bool row_complete(const uint32_t (&y)[K]) {
   return __all_sync(0xffffffffu, ok);
 }
 
-// re-read from L2 until complete (bounded). The slow path stays out of line and hands the
-// row back by value, so the callers' row arrays and abort flag never need an address and
-// stay in registers.
+// re-read from L2 until complete (bounded)
 template <int K>
-struct WaitResult {
-  uint32_t y[K];
-  uint32_t aborted;
-};
-
-template <int K>
-__device__ __noinline__ WaitResult<K> wait_row_slow(const uint32_t* row, uint32_t aborted, DevStatus* st) {
-  WaitResult<K> r;
-  r.aborted = aborted;
+__device__ __noinline__ void wait_row(const uint32_t* row, uint32_t (&y)[K], bool& abort, DevStatus* st) {
   uint32_t it = 0;
   for (;;) {
-    load_row<K>(row, r.y);
-    if (row_complete<K>(r.y) || r.aborted) return r;
+    load_row<K>(row, y);
+    if (row_complete<K>(y) || abort) return;
     if (++it > kSpinLimit) {
       if ((threadIdx.x & 31) == 0) atomicCAS(&st->code, 0, GWCP_ERR_TIMEOUT);
-      r.aborted = 1;
-      return r;
+      abort = true;
+      return;
     }
     __nanosleep(32);
   }
-}
-
-template <int K>
-__device__ __forceinline__ void wait_row(const uint32_t* row, uint32_t (&y)[K], bool& abort, DevStatus* st) {
-  const WaitResult<K> r = wait_row_slow<K>(row, abort ? 1u : 0u, st);
-#pragma unroll
-  for (int j = 0; j < K; ++j) y[j] = r.y[j];
-  abort = r.aborted != 0;
 }
 
 // x |= the rows at base + ids[q] * Wp, all loads issued before any is used
