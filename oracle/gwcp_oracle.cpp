@@ -52,6 +52,7 @@
 //       acqC[agent] <= C_t[agent] would have answered differently.
 
 #include <algorithm>
+#include <array>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -482,13 +483,14 @@ class Analysis {
       }
       hist.push_back(HistEntry{i, u, cls, N_[u]});
     } else {
-      std::vector<Last>& last = last_[x];
-      if (last.empty()) last.resize(size_t(g_.W) * 4);
-      for (uint32_t v = 0; v < g_.W; ++v) {
+      // agents that never accessed x have no latest access there: only those that did
+      // are visited (in agent order)
+      std::map<uint32_t, std::array<Last, 4>>& last = last_[x];
+      for (const auto& [v, lv] : last) {
         if (v == u) continue;
         const Last* best = nullptr;
         for (int c = 0; c < 4; ++c) {
-          const Last& l = last[size_t(v) * 4 + c];
+          const Last& l = lv[c];
           if (l.idx == ~uint64_t(0)) continue;
           if (!is_write_class(c) && !write) continue;  // two reads never conflict
           if (exempt(c, g_.block(v))) continue;
@@ -498,7 +500,7 @@ class Analysis {
         res_->partner_tests++;
         if (best->epoch > cb[v]) pairs_.emplace_back(best->idx, i);  // A5
       }
-      Last& mine = last[size_t(u) * 4 + cls];
+      Last& mine = last[u][cls];
       mine.idx = i;
       mine.epoch = N_[u];
     }
@@ -529,7 +531,7 @@ class Analysis {
   std::unordered_map<uint64_t, LockState> locks_;
   std::map<std::pair<uint64_t, uint64_t>, size_t> cursor_;
   std::unordered_map<LKey, LClocks, LKeyHash> lmap_;
-  std::unordered_map<uint64_t, std::vector<Last>> last_;
+  std::unordered_map<uint64_t, std::map<uint32_t, std::array<Last, 4>>> last_;  // location -> agent -> class
   std::unordered_map<uint64_t, std::vector<HistEntry>> hist_;
   std::vector<std::pair<uint64_t, uint64_t>> pairs_;
 };
