@@ -48,7 +48,10 @@ extern "C" {
  *   W3 per lock, two critical sections whose scopes overlap (either is device-scoped,
  *      or both are block-scoped in one block) never interleave;
  *   W4 one BARRIER event per barrier instance.
- * Limits of this implementation: n < 2^30 events; num_agents <= 1024.
+ * Limits of this implementation: n < 2^30 events; num_agents <= 1024, or up to 8192 at
+ * GWCP_GRAN_WARP with agents_per_block <= 32 (clocks wider than 1024 entries are kept as
+ * tables of 256-entry tiles); a lock may be used with at most 64 scope ids, or 320 when
+ * the trace has more than 63 blocks. Other geometries return GWCP_ERR_UNSUPPORTED.
  */
 enum {
   GWCP_READ = 0,
@@ -121,9 +124,10 @@ int gwcp_load_trace(gwcp_ctx* ctx, const gwcp_event* ev, uint64_t n, const gwcp_
 /* Runs the whole analysis on the device: decode and validation, epoch assignment,
  * critical-section annotation, clock propagation (Algorithms 1-2), access grouping, the
  * per-location race check and race compaction. Kernels are enqueued on cuda_stream; the
- * call synchronises that stream twice to size its buffers from device-side counts.
- * Validation errors found before the propagation are returned here; a device-side
- * timeout is returned by gwcp_report_races. */
+ * call synchronises that stream three times: twice to size its buffers from device-side
+ * counts and once at the end for the status. Validation errors, a device-side timeout
+ * (GWCP_ERR_TIMEOUT) and exhausted device memory (GWCP_ERR_OOM) are returned here and
+ * again by gwcp_report_races. */
 int gwcp_compute_order(gwcp_ctx* ctx, void* cuda_stream);
 
 /* Waits for the analysis on cuda_stream and copies up to `cap` races into host memory

@@ -13,7 +13,7 @@ unsigned long long launch_count();
 size_t check_chunks(uint32_t n_acc);
 size_t check_group_count(uint32_t n_acc);
 void phaseE_scan(const Bufs& b, const Sizes& z, cudaStream_t s, Prof& p);
-void phaseF_deps(const Bufs& b, const Sizes& z, cudaStream_t s, Prof& p);
+void phaseF_deps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 
 cudaEvent_t Prof::ev() {
   if (used == pool.size()) {
@@ -57,6 +57,7 @@ struct gwcp_ctx {
   uint64_t n_races = 0;
   unsigned long long bad_index = ~0ull;
   uint64_t counters[8] = {};
+  uint64_t tile_cap_hint = 0;  // wide clocks: pool size that the last run needed
   cudaStream_t side = nullptr;  // runs the access grouping beside the propagation
   cudaEvent_t fork = nullptr, join = nullptr;
   std::vector<float> prof_ms;
@@ -67,6 +68,7 @@ struct gwcp_ctx {
 namespace {
 
 const uint32_t kNoneHost = 0xFFFFFFFFu;
+const int kRerun = 1;  // run() result: the tile pool was grown, run again
 
 template <typename T>
 T* get(gwcp_ctx* c, const char* name, size_t count, bool* oom) {
@@ -108,6 +110,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   z = Sizes{};
   z.N = c->n;
   z.TA = g.Wp <= 256 ? 2048 : 8192;
+  while (uint64_t(g.W) * ((z.N + z.TA - 1) / z.TA) > (1ull << 26)) z.TA <<= 1;  // bounded agent histogram
   z.ntA = uint32_t((z.N + z.TA - 1) / z.TA);
   b.ev = c->ev_dev;
   b.st = get<DevStatus>(c, "st", 1, &oom);
@@ -210,7 +213,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   z.n_cs = z.n_acqrel ? c->cnt_host[2] : 0;
   z.n_locks = z.n_acqrel ? c->cnt_host[3] : 0;
   z.n_exp = c->cnt_host[4];
-  const uint32_t slots = std::min<uint32_t>(g.B + 1, kMaxLockScopes);
+  const uint32_t slots = std::min<uint32_t>(g.B + 1, lock_scope_cap(g.B));
   z.pool_cap = z.n_cs * slots + z.n_exp * 2 * slots + 64;
   b.dep_pool = get<uint32_t>(c, "dep_pool", z.pool_cap, &oom);
   z.race_cap = c->opt.race_capacity ? c->opt.race_capacity : std::max<uint64_t>(1u << 20, z.N);
@@ -249,9 +252,15 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   b.ex_group = get<uint32_t>(c, "ex_group", ne1 + 1, &oom);
   b.ex_dep_off = get<uint32_t>(c, "ex_dep_off", ne1, &oom);
   b.ex_dep_cnt = get<uint32_t>(c, "ex_dep_cnt", ne1, &oom);
-  b.rows = get<uint32_t>(c, "rows", size_t(z.n_rows) * g.Wp, &oom);
-  b.psnap = get<uint32_t>(c, "psnap", (size_t(z.n_cs) + 1) * g.Wp, &oom);
-  b.hsnap = get<uint32_t>(c, "hsnap", (size_t(z.n_cs) + 1) * g.Wp, &oom);
+  b.rows = get<uint32_t>(c, "rows", size_t(z.n_rows) * g.RW, &oom);
+  b.psnap = get<uint32_t>(c, "psnap", (size_t(z.n_cs) + 1) * g.RW, &oom);
+  b.hsnap = get<uint32_t>(c, "hsnap", (size_t(z.n_cs) + 1) * g.RW, &oom);
+  if (g.nT) {
+    // tile pool: a few new tiles per clock version; grown and rerun on exhaustion
+    const uint64_t want = 2ull * (uint64_t(z.n_rows) + z.n_cs) + uint64_t(z.n_bar) * (g.apb + 2) + 65536;
+    z.tile_cap = std::max<uint64_t>(c->tile_cap_hint, want);
+    b.tiles = get<uint32_t>(c, "tiles", size_t(z.tile_cap) * kTileW, &oom);
+  }
   b.done = get<uint32_t>(c, "done", size_t(z.n_cs) + 1, &oom);
   b.plan = get<uint4>(c, "plan", 2 * (size_t(z.n_sync) + z.n_incs) + 2, &oom);
   b.recmeta = get<uint4>(c, "recmeta", size_t(z.n_cs) + 1, &oom);
@@ -259,17 +268,37 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   b.flat = get<uint32_t>(c, "flat", z.pool_cap, &oom);
   b.cursor = get<uint32_t>(c, "cursor", size_t(g.W) * (z.n_locks + 1), &oom);
   const size_t smem = size_t(2) * g.apb * 2 * g.Wp * 4;
-  z.cta_barriers = g.apb <= 32 && smem <= 96 * 1024;
+  z.cta_barriers = g.nT ? true : (g.apb <= 32 && smem <= 96 * 1024);
   const bool global_bars = !z.cta_barriers || g.gran == GWCP_GRAN_THREAD;
   b.bar_j = get<uint32_t>(c, "bar_j", global_bars ? size_t(z.n_bar) * 2 * g.Wp : 1, &oom);
   b.bar_cnt = get<uint32_t>(c, "bar_cnt", global_bars ? z.n_bar : 1, &oom);
-  z.n_chunks = uint32_t(check_chunks(z.n_acc));
-  const size_t ng = check_group_count(z.n_acc);
-  b.tails = get<uint32_t>(c, "tails", (size_t(z.n_chunks) + ng) * 4 * g.Wp * 2 + ng + 8, &oom);
+  if (g.nT) {
+    const size_t na = size_t(z.n_acc) + 1;
+    b.wc_flag = get<uint32_t>(c, "wc_flag", na, &oom);
+    b.wc_run = get<uint32_t>(c, "wc_run", na, &oom);
+    b.wc_key = get<uint64_t>(c, "wc_key", na, &oom);
+    b.wc_val = get<uint32_t>(c, "wc_val", na, &oom);
+    b.wc_key2 = get<uint64_t>(c, "wc_key2", na, &oom);
+    b.wc_val2 = get<uint32_t>(c, "wc_val2", na, &oom);
+    b.wc_gflag = get<uint32_t>(c, "wc_gflag", na, &oom);
+    b.wc_gexcl = get<uint32_t>(c, "wc_gexcl", na, &oom);
+    b.wc_grp_lo = get<uint32_t>(c, "wc_grp_lo", na, &oom);
+    b.wc_grp_agent = get<uint32_t>(c, "wc_grp_agent", na, &oom);
+    b.wc_rc = get<uint32_t>(c, "wc_rc", 4 * na + 2, &oom);
+  } else {
+    z.n_chunks = uint32_t(check_chunks(z.n_acc));
+    const size_t ng = check_group_count(z.n_acc);
+    b.tails = get<uint32_t>(c, "tails", (size_t(z.n_chunks) + ng) * 4 * g.Wp * 2 + ng + 8, &oom);
+  }
   b.races = get<uint64_t>(c, "races", z.race_cap, &oom);
   b.races2 = get<uint64_t>(c, "races2", z.race_cap, &oom);
   if (oom) return GWCP_ERR_OOM;
   cudaMemsetAsync(b.done, 0, (size_t(z.n_cs) + 1) * 4, s);
+  if (g.nT) {  // tile 0 is the zero tile; ids are handed out from 1
+    cudaMemsetAsync(b.tiles, 0, kTileW * 4, s);
+    const unsigned long long one = 1;
+    cudaMemcpyAsync(&b.st->spare[2], &one, sizeof(one), cudaMemcpyHostToDevice, s);
+  }
   cudaMemsetAsync(b.cursor, 0, size_t(g.W) * (z.n_locks + 1) * 4, s);
   if (global_bars && z.n_bar) {
     cudaMemsetAsync(b.bar_j, 0, size_t(z.n_bar) * 2 * g.Wp * 4, s);
@@ -279,27 +308,38 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   phaseD_gaps(b, g, z, s, c->prof);
   // the access grouping and the check's carries do not depend on clock values: they run
   // on a side stream, with their own scratch, while the propagation runs on s
-  uint32_t* side_tmp = get<uint32_t>(c, "side_tmp", radix_tmp_need(size_t(z.n_acc) + 1) + 64, &oom);
+  uint32_t* side_tmp = get<uint32_t>(
+      c, "side_tmp", std::max(radix_tmp_need(size_t(z.n_acc) + 1), scan_tmp_need(size_t(z.n_acc) * 4 + 2)) + 64, &oom);
   if (oom) return GWCP_ERR_OOM;
   cudaEventRecord(c->fork, s);
   cudaStreamWaitEvent(c->side, c->fork, 0);
   phaseH_sort(b, g, z, key_mask, side_tmp, c->side, c->prof);
-  phaseI_carry(b, g, z, c->side, c->prof);
+  if (g.nT)
+    phaseI_wide_group(b, g, z, side_tmp, c->side, c->prof);
+  else
+    phaseI_carry(b, g, z, c->side, c->prof);
   cudaEventRecord(c->join, c->side);
   phaseF_incs(b, g, z, key_mask, s, c->prof);
   phaseF_walk(b, g, z, key_mask, s, c->prof);
   z.n_groups = z.n_exp;  // upper bound; the kernel reads the exact count on the device
-  phaseF_deps(b, z, s, c->prof);
+  phaseF_deps(b, g, z, s, c->prof);
   int prc = phaseG_propagate(b, g, z, s, c->prof);
   cudaStreamWaitEvent(s, c->join, 0);
   if (prc) return prc;
-  phaseI_check(b, g, z, s, c->prof);
+  if (g.nT)
+    phaseI_wide_check(b, g, z, s, c->prof);
+  else
+    phaseI_check(b, g, z, s, c->prof);
   {
     int rc = read_status(c, s, nullptr, 0);
     if (rc) return rc;
   }
   code = c->st_host->code;
   c->bad_index = c->st_host->bad_index;
+  if (code == GWCP_ERR_OOM && g.nT && c->st_host->spare[2] > z.tile_cap) {
+    c->tile_cap_hint = 2 * z.tile_cap;  // the tile pool ran out: the caller runs again
+    return kRerun;
+  }
   if (code) return code;
   c->n_races = c->st_host->n_races;
   c->races_second = phaseI_sort_races(b, z, c->n_races, s, c->prof);
@@ -348,7 +388,11 @@ int gwcp_load_trace(gwcp_ctx* c, const gwcp_event* ev, uint64_t n, const gwcp_ge
   if (n > kMaxEvents || geo->num_agents == 0 || geo->agents_per_block == 0 || geo->reserved != 0 ||
       geo->num_agents % geo->agents_per_block != 0 || geo->granularity > 1)
     return GWCP_ERR_ARGS;
-  if (geo->num_agents > kMaxAgents) return GWCP_ERR_UNSUPPORTED;
+  // clocks of more than kMaxAgents entries are tile tables: warp granularity, and a block
+  // of agents fits one CTA of walkers
+  if (geo->num_agents > kMaxAgents &&
+      (geo->num_agents > kMaxAgentsWide || geo->granularity != GWCP_GRAN_WARP || geo->agents_per_block > 32))
+    return GWCP_ERR_UNSUPPORTED;
   cudaSetDevice(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Geo g{};
@@ -360,6 +404,14 @@ int gwcp_load_trace(gwcp_ctx* c, const gwcp_event* ev, uint64_t n, const gwcp_ge
   while (k * 32 < g.W) k <<= 1;
   g.K = k;
   g.Wp = 32 * k;
+  g.nT = 0;
+  g.RW = g.Wp;
+  if (g.W > kMaxAgents) {
+    g.nT = (g.W + kTileW - 1) / kTileW;
+    g.Wp = g.nT * kTileW;
+    g.K = g.Wp / 32;
+    g.RW = kTabW;
+  }
   c->g = g;
   c->n = n;
   c->computed = false;
@@ -399,6 +451,8 @@ int gwcp_compute_order(gwcp_ctx* c, void* stream) {
     return GWCP_OK;
   }
   int rc = run(c, static_cast<cudaStream_t>(stream));
+  for (int attempt = 0; rc == kRerun && attempt < 6; ++attempt) rc = run(c, static_cast<cudaStream_t>(stream));
+  if (rc == kRerun) rc = GWCP_ERR_OOM;
   c->computed = true;
   c->compute_rc = rc;
   return rc;
@@ -442,6 +496,21 @@ int gwcp_report_races(gwcp_ctx* c, gwcp_race* out, uint64_t cap, uint64_t* n_rac
   return cap < c->n_races ? GWCP_ERR_CAPACITY : GWCP_OK;
 }
 
+namespace {
+// a published clock (Wp words, or a table of tile ids for wide clocks) into out[Wp]
+void read_clock(gwcp_ctx* c, const uint32_t* src, uint32_t* out) {
+  const Geo& g = c->g;
+  if (!g.nT) {
+    cudaMemcpy(out, src, size_t(g.Wp) * 4, cudaMemcpyDeviceToHost);
+    return;
+  }
+  uint32_t ids[kTabW];
+  cudaMemcpy(ids, src, sizeof(ids), cudaMemcpyDeviceToHost);
+  for (uint32_t t = 0; t < g.nT; ++t)
+    cudaMemcpy(out + size_t(t) * kTileW, c->b.tiles + size_t(ids[t]) * kTileW, kTileW * 4, cudaMemcpyDeviceToHost);
+}
+}  // namespace
+
 int gwcp_debug_clock(gwcp_ctx* c, uint64_t idx, int which, uint32_t* out) {
   if (!c || !out) return GWCP_ERR_ARGS;
   if (!c->computed || c->compute_rc) return GWCP_ERR_STATE;
@@ -459,7 +528,7 @@ int gwcp_debug_clock(gwcp_ctx* c, uint64_t idx, int which, uint32_t* out) {
     if (which != 0) return GWCP_ERR_UNSUPPORTED;
     AccInfo inf;
     cudaMemcpy(&inf, b.acc_info + idx, sizeof(inf), cudaMemcpyDeviceToHost);
-    src = b.rows + size_t(inf.row) * g.Wp;
+    src = b.rows + size_t(inf.row) * g.RW;
     own = inf.epoch;
   } else if (e.op == GWCP_ACQ || e.op == GWCP_REL) {
     uint32_t k0, k1;
@@ -477,18 +546,17 @@ int gwcp_debug_clock(gwcp_ctx* c, uint64_t idx, int which, uint32_t* out) {
     cudaMemcpy(&cs, b.cs_of_sync + k, 4, cudaMemcpyDeviceToHost);
     own = e.op == GWCP_REL ? N - 1 : N;
     if (which == 0) {
-      src = b.rows + size_t(rb + ver) * g.Wp;
+      src = b.rows + size_t(rb + ver) * g.RW;
     } else {
       if (e.op != GWCP_REL || cs == kNoneHost) return GWCP_ERR_UNSUPPORTED;
-      src = b.hsnap + size_t(cs) * g.Wp;
-      cudaMemcpy(row.data(), src, g.Wp * 4, cudaMemcpyDeviceToHost);
+      read_clock(c, b.hsnap + size_t(cs) * g.RW, row.data());
       std::memcpy(out, row.data(), g.W * 4);
       return cuda_rc();
     }
   } else {
     return GWCP_ERR_UNSUPPORTED;
   }
-  cudaMemcpy(row.data(), src, g.Wp * 4, cudaMemcpyDeviceToHost);
+  read_clock(c, src, row.data());
   row[e.agent] = own;
   std::memcpy(out, row.data(), g.W * 4);
   return cuda_rc();

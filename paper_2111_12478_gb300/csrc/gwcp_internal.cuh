@@ -13,9 +13,17 @@ namespace gwcp {
 
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr int kMaxNest = 4;         // deepest lockset a valid trace may hold
-constexpr uint32_t kMaxAgents = 1024;
+constexpr uint32_t kMaxAgents = 1024;      // clocks held in registers
+constexpr uint32_t kMaxAgentsWide = 8192;  // clocks as tables of copy-on-write tiles
+constexpr uint32_t kTileW = 256;           // entries per clock tile
+constexpr uint32_t kTabW = 32;             // words per published tile table (nT <= 32)
 constexpr uint32_t kMaxEvents = (1u << 30) - 1;
-constexpr int kMaxLockScopes = 64;  // distinct scope ids one lock may be used with
+// distinct scope ids one lock may be used with: 64, or 320 when the trace has more than
+// 63 blocks (a block-scoped lock may be used in every block)
+constexpr int kLockScopesSmall = 64, kLockScopesLarge = 320;
+__host__ __device__ inline uint32_t lock_scope_cap(uint32_t blocks) {
+  return blocks + 1 <= uint32_t(kLockScopesSmall) ? kLockScopesSmall : kLockScopesLarge;
+}
 
 // S entry kinds (agent-sorted event stream), packed as (kind << 30) | trace index
 enum : uint32_t { K_ACCESS = 0, K_ACQ = 1, K_REL = 2, K_BAR = 3 };
@@ -47,19 +55,24 @@ struct DevStatus {
 };
 
 struct Geo {
-  uint32_t W, apb, B, gran, Wp, K;  // Wp = W rounded up to 32, K = Wp / 32
+  uint32_t W, apb, B, gran, Wp, K;  // Wp = W rounded up to 32 * K, K = Wp / 32 (a power of two)
+  uint32_t nT;  // wide clocks: tiles of kTileW entries (0: clocks in registers)
+  uint32_t RW;  // words per published clock: Wp, or kTabW tile ids when nT > 0
 };
 
 // Per-access record consumed by the check (indexed by trace index).
 struct AccInfo {
   uint32_t epoch;  // N_t of the access
   uint32_t row;    // global clock-version row holding P_t for the access
-  uint32_t who;    // agent | class << 10 | block << 12 (agent, block < 1024)
+  uint32_t who;    // agent | class << 13 | block << 15 (agent, block < 8192)
   uint32_t pad;
 };
-__host__ __device__ inline uint32_t who_agent(uint32_t w) { return w & 0x3FFu; }
-__host__ __device__ inline uint32_t who_class(uint32_t w) { return (w >> 10) & 3u; }
-__host__ __device__ inline uint32_t who_block(uint32_t w) { return w >> 12; }
+__host__ __device__ inline uint32_t make_who(uint32_t agent, uint32_t cls, uint32_t block) {
+  return agent | (cls << 13) | (block << 15);
+}
+__host__ __device__ inline uint32_t who_agent(uint32_t w) { return w & 0x1FFFu; }
+__host__ __device__ inline uint32_t who_class(uint32_t w) { return (w >> 13) & 3u; }
+__host__ __device__ inline uint32_t who_block(uint32_t w) { return w >> 15; }
 
 // All device buffers of one analysis. Sizes in comments.
 struct Bufs {
@@ -137,15 +150,28 @@ struct Bufs {
   uint4* recmeta = nullptr;     // [n_cs + 1] (agent, acquire epoch, release index, scope id)
   uint32_t* flat_off = nullptr; // [n_incs + 1] dependency list of each in-section access
   uint32_t* flat = nullptr;     // [pool_cap]
-  uint32_t* rows = nullptr;     // [n_rows * Wp]
-  uint32_t* psnap = nullptr;    // [n_cs * Wp]
-  uint32_t* hsnap = nullptr;    // [n_cs * Wp]
+  uint32_t* rows = nullptr;     // [n_rows * RW]
+  uint32_t* psnap = nullptr;    // [n_cs * RW]
+  uint32_t* hsnap = nullptr;    // [n_cs * RW]
+  uint32_t* tiles = nullptr;    // wide clocks: [tile_cap * kTileW] tile pool, tile 0 = zeros
   uint32_t* done = nullptr;     // [n_cs]
   uint32_t* cursor = nullptr;   // [W * n_locks]
   uint32_t* bar_j = nullptr;    // [n_bar * 2 * Wp] global-barrier joins
   uint32_t* bar_cnt = nullptr;  // [n_bar]
   // phase I: check
   uint32_t* tails = nullptr;    // [n_chunks * 4 * Wp * 2]
+  // wide clocks: accesses regrouped by (location, class, agent)
+  uint32_t* wc_flag = nullptr;   // [n_acc] location-run starts in key order
+  uint32_t* wc_run = nullptr;    // [n_acc + 1] exclusive scan of wc_flag
+  uint64_t* wc_key = nullptr;    // [n_acc] (run << 15 | class << 13 | agent) (+ alt)
+  uint32_t* wc_val = nullptr;    // [n_acc] key-order position (+ alt)
+  uint64_t* wc_key2 = nullptr;
+  uint32_t* wc_val2 = nullptr;
+  uint32_t* wc_gflag = nullptr;  // [n_acc] group starts
+  uint32_t* wc_gexcl = nullptr;  // [n_acc + 1]
+  uint32_t* wc_grp_lo = nullptr;     // [n_groups + 1]
+  uint32_t* wc_grp_agent = nullptr;  // [n_groups]
+  uint32_t* wc_rc = nullptr;     // [4 * n_acc + 2] first group of each (run, class)
   uint64_t* races = nullptr;    // [race_cap] (later << 32) | earlier
   uint64_t* races2 = nullptr;
   // scan scratch
@@ -269,6 +295,7 @@ struct Sizes {
   uint32_t pool_cap = 0;
   uint32_t n_chunks = 0;
   uint64_t race_cap = 0;
+  uint64_t tile_cap = 0;      // wide clocks: tiles in the pool
   bool cta_barriers = false;  // every block fits one CTA of walkers
 };
 
@@ -306,5 +333,10 @@ void phaseH_sort(Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, uint3
 void phaseI_carry(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 void phaseI_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 bool phaseI_sort_races(const Bufs& b, const Sizes& z, uint64_t n_races, cudaStream_t s, Prof& p);
+// wide clocks (gwcp_wide.cu): the walker over tile tables (after the plan is built), the
+// regrouping of accesses (beside the propagation) and the per-access partner check
+int phaseG_wide(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s);
+void phaseI_wide_group(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t s, Prof& p);
+void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 
 }  // namespace gwcp

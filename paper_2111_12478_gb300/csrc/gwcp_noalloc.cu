@@ -18,7 +18,7 @@
 
 namespace gwcp {
 void phaseE_scan(const Bufs& b, const Sizes& z, cudaStream_t s, Prof& p);
-void phaseF_deps(const Bufs& b, const Sizes& z, cudaStream_t s, Prof& p);
+void phaseF_deps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 size_t check_chunks(uint32_t n_acc);
 size_t check_group_count(uint32_t n_acc);
 }  // namespace gwcp
@@ -171,7 +171,7 @@ int analyze(const Event* ev, uint64_t n, const Geo& g, gwcp_race* out, uint64_t 
   z.n_cs = z.n_acqrel ? v[2] : 0;
   z.n_locks = z.n_acqrel ? v[3] : 0;
   z.n_exp = v[4];
-  const uint32_t slots = std::min<uint32_t>(g.B + 1, kMaxLockScopes);
+  const uint32_t slots = std::min<uint32_t>(g.B + 1, lock_scope_cap(g.B));
   z.pool_cap = z.n_cs * slots + z.n_exp * 2 * slots + 64;
   b.dep_pool = A.take<uint32_t>(z.pool_cap);
   const size_t ni1 = size_t(z.n_incs) + 1;
@@ -235,7 +235,7 @@ int analyze(const Event* ev, uint64_t n, const Geo& g, gwcp_race* out, uint64_t 
   phaseF_incs(b, g, z, key_mask, s, prof);
   phaseF_walk(b, g, z, key_mask, s, prof);
   z.n_groups = z.n_exp;
-  phaseF_deps(b, z, s, prof);
+  phaseF_deps(b, g, z, s, prof);
   phaseH_sort(b, g, z, key_mask, b.scan_tmp, s, prof);
   if (int rc = phaseG_propagate(b, g, z, s, prof)) return rc;
   phaseI_carry(b, g, z, s, prof);
@@ -285,6 +285,8 @@ extern "C" int gwcp_analyze_noalloc(const gwcp_event* ev_dev, uint64_t n, const 
   while (k * 32 < g.W) k <<= 1;
   g.K = k;
   g.Wp = 32 * k;
+  g.nT = 0;
+  g.RW = g.Wp;
   return analyze(reinterpret_cast<const Event*>(ev_dev), n, g, races_dev, races_cap, n_races, first_bad_index,
                  static_cast<cudaStream_t>(cuda_stream), scratch);
 }

@@ -21,7 +21,7 @@ namespace gwcp {
 
 namespace {
 
-constexpr int A_WARPS = 4;
+constexpr int A_WARPS = 4;  // warps per CTA of phase A while their histograms fit 48 KB
 
 __device__ bool validate_w1(const Event& e, const Geo& g) {
   if (e.agent >= g.W || e.op > GWCP_FENCE || e.scope > GWCP_SCOPE_WARP || e.space > GWCP_SPACE_SHARED) return false;
@@ -51,7 +51,7 @@ __global__ void k_a_count(const Event* ev, uint64_t N, Geo g, uint32_t TA, uint3
                           uint32_t* tile_cnt, DevStatus* st) {
   extern __shared__ uint32_t sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t tile = blockIdx.x * A_WARPS + warp;
+  const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + warp;
   uint32_t* cnt = sm + warp * g.Wp;
   for (uint32_t u = lane; u < g.Wp; u += 32) cnt[u] = 0;
   __syncwarp();
@@ -118,7 +118,7 @@ __global__ void k_a_scatter(const Event* ev, uint64_t N, Geo g, uint32_t TA, uin
                             uint32_t* acqrel, uint32_t* bar) {
   extern __shared__ uint32_t sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t tile = blockIdx.x * A_WARPS + warp;
+  const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + warp;
   if (tile >= ntA) return;
   uint32_t* cnt = sm + warp * g.Wp;
   for (uint32_t u = lane; u < g.W; u += 32) cnt[u] = hist[size_t(u) * ntA + tile];
@@ -422,7 +422,7 @@ __global__ void k_d_fill(const Event* ev, Geo g, uint32_t n_sync, const uint32_t
     const Event e = ev[idx];
     const uint32_t cls = access_class(e);
     const uint32_t ver = incs ? vbase + j : vbase;
-    acc_info[idx] = AccInfo{epoch, rb + ver, u | (cls << 10) | ((u / g.apb) << 12), 0};
+    acc_info[idx] = AccInfo{epoch, rb + ver, make_who(u, cls, u / g.apb), 0};
     if (incs) {
       const uint32_t r = incs_off[k] + j - 1;
       incs_idx[r] = idx;
@@ -492,6 +492,7 @@ struct LockSlot {
 
 // One thread per lock: acquire joins (the latest release on each overlapping scope),
 // W3 (overlapping critical sections never interleave).
+template <int MAXS>
 __global__ void k_e_walk(const uint32_t* kk, const uint32_t* lock_first, uint32_t n_locks, const uint32_t* csid,
                          const uint32_t* sy_kind, const uint32_t* sy_idx, const uint32_t* cs_of_sync,
                          const uint32_t* cs_sid, uint32_t* acq_dep_off, uint32_t* acq_dep_cnt, uint32_t* pool,
@@ -499,12 +500,12 @@ __global__ void k_e_walk(const uint32_t* kk, const uint32_t* lock_first, uint32_
   uint32_t lr = blockIdx.x * blockDim.x + threadIdx.x;
   const int code = st->code;
   if (lr >= n_locks || (code && code != GWCP_ERR_INVALID_TRACE)) return;
-  LockSlot sl[kMaxLockScopes];
+  LockSlot sl[MAXS];
   int ns = 0;
   auto slot = [&](uint32_t sid) -> int {
     for (int q = 0; q < ns; ++q)
       if (sl[q].sid == sid) return q;
-    if (ns == kMaxLockScopes) return -1;
+    if (ns == MAXS) return -1;
     sl[ns] = LockSlot{sid, NONE, NONE, 0};
     return ns++;
   };
@@ -529,7 +530,7 @@ __global__ void k_e_walk(const uint32_t* kk, const uint32_t* lock_first, uint32_
         set_error(st, GWCP_ERR_INVALID_TRACE, idx);
         return;
       }
-      uint32_t deps[kMaxLockScopes];
+      uint32_t deps[MAXS];
       uint32_t nd = 0;
       const uint32_t rel0 = q0 >= 0 ? sl[q0].latest_rel : NONE;
       if (q0 >= 0 && sl[q0].latest_cs != NONE) deps[nd++] = sl[q0].latest_cs;
@@ -616,6 +617,7 @@ struct ObjSlot {
 // in-section access joins, per overlapping scope (Algorithm 2). L^w_<l,s>,x is the
 // join of H over earlier releases on <l,s> whose section wrote x; those H only grow
 // along one scoped lock, so the latest such release is the whole join.
+template <int MAXS>
 __global__ void k_f_walk(const uint32_t* val, const uint32_t* starts, uint32_t max_groups, const uint32_t* ex_rec,
                          const uint32_t* ex_cs, const uint32_t* incs_wr, const uint32_t* cs_sid,
                          const uint32_t* cs_rel_idx, uint32_t* ex_dep_off, uint32_t* ex_dep_cnt, uint32_t* pool,
@@ -623,7 +625,7 @@ __global__ void k_f_walk(const uint32_t* val, const uint32_t* starts, uint32_t m
   uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t n_groups = uint32_t(st->spare[0]);  // exact count, written by the group scan
   if (gi >= max_groups || gi >= n_groups || st->code) return;
-  ObjSlot sl[kMaxLockScopes];
+  ObjSlot sl[MAXS];
   int ns = 0;
   for (uint32_t m = starts[gi]; m < starts[gi + 1]; ++m) {
     const uint32_t e = val[m];
@@ -635,7 +637,7 @@ __global__ void k_f_walk(const uint32_t* val, const uint32_t* starts, uint32_t m
     for (int r = 0; r < ns; ++r)
       if (sl[r].sid == s) q = r;
     if (q < 0) {
-      if (ns == kMaxLockScopes) {
+      if (ns == MAXS) {
         set_error(st, GWCP_ERR_UNSUPPORTED, 0);
         return;
       }
@@ -650,7 +652,7 @@ __global__ void k_f_walk(const uint32_t* val, const uint32_t* starts, uint32_t m
       sl[q].cur = c;
       sl[q].cur_w = sl[q].cur_r = 0;
     }
-    uint32_t deps[2 * kMaxLockScopes];
+    uint32_t deps[2 * MAXS];
     uint32_t nd = 0;
     // latest completed section on scope slot r that wrote (w) or read (!w) x
     auto latest = [&](int r, bool w) -> uint32_t {
@@ -694,11 +696,19 @@ __global__ void k_f_walk(const uint32_t* val, const uint32_t* starts, uint32_t m
 
 inline uint32_t blocks(uint64_t n, uint32_t t) { return uint32_t((n + t - 1) / t); }
 
+// phase A warps per CTA: each holds a Wp-word histogram in shared memory (<= 48 KB per CTA)
+inline uint32_t a_warps(const Geo& g) {
+  uint32_t w = A_WARPS;
+  while (w > 1 && size_t(w) * g.Wp * 4 > 48 * 1024) w >>= 1;
+  return w;
+}
+
 }  // namespace
 
 void phaseA_count(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   p.begin("a_count", double(z.N) * 16);
-  k_a_count<<<blocks(z.ntA, A_WARPS), A_WARPS * 32, A_WARPS * g.Wp * 4, s>>>(b.ev, z.N, g, z.TA, z.ntA, b.hist_a,
+  const uint32_t aw = a_warps(g);
+  k_a_count<<<blocks(z.ntA, aw), aw * 32, aw * g.Wp * 4, s>>>(b.ev, z.N, g, z.TA, z.ntA, b.hist_a,
                                                                           b.tile_cnt, b.st);
   count_launch();
   p.end();
@@ -712,7 +722,8 @@ void phaseA_count(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, P
 
 void phaseA_scatter(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   p.begin("a_scatter", double(z.N) * 16 + double(z.nS) * 4 + double(z.n_acc) * 12);
-  k_a_scatter<<<blocks(z.ntA, A_WARPS), A_WARPS * 32, A_WARPS * g.Wp * 4, s>>>(
+  const uint32_t aw = a_warps(g);
+  k_a_scatter<<<blocks(z.ntA, aw), aw * 32, aw * g.Wp * 4, s>>>(
       b.ev, z.N, g, z.TA, z.ntA, b.hist_a, b.tile_cnt, b.S, b.acc_key, b.acc_idx, b.acqrel, b.bar);
   count_launch();
   k_a_segments<<<blocks(g.W + 1, 256), 256, 0, s>>>(b.hist_a, g.W, z.ntA, z.nS, b.seg);
@@ -796,9 +807,10 @@ void phaseE_walk(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Pr
   count_launch();
   k_e_assign_rel<<<blocks(n, 256), 256, 0, s>>>(b.lk_k, n, b.sy_kind, b.sy_match, b.cs_of_sync, b.cs_parent);
   count_launch();
-  k_e_walk<<<blocks(z.n_locks, 128), 128, 0, s>>>(b.lk_k, b.lock_first, z.n_locks, b.lk_csid, b.sy_kind, b.sy_idx,
-                                                  b.cs_of_sync, b.cs_sid, b.acq_dep_off, b.acq_dep_cnt, b.dep_pool,
-                                                  z.pool_cap, b.st);
+  auto ew = lock_scope_cap(g.B) == kLockScopesSmall ? k_e_walk<kLockScopesSmall> : k_e_walk<kLockScopesLarge>;
+  ew<<<blocks(z.n_locks, 128), 128, 0, s>>>(b.lk_k, b.lock_first, z.n_locks, b.lk_csid, b.sy_kind, b.sy_idx,
+                                            b.cs_of_sync, b.cs_sid, b.acq_dep_off, b.acq_dep_cnt, b.dep_pool,
+                                            z.pool_cap, b.st);
   count_launch();
   p.end();
 }
@@ -850,12 +862,13 @@ void phaseF_walk(Bufs& bb, const Geo& g, const Sizes& z, uint64_t key_mask, cuda
   p.end();
 }
 
-void phaseF_deps(const Bufs& b, const Sizes& z, cudaStream_t s, Prof& p) {
+void phaseF_deps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   if (!z.n_groups) return;
   p.begin("f_deps", double(z.n_exp) * 32);
-  k_f_walk<<<blocks(z.n_groups, 128), 128, 0, s>>>(b.ex_val, b.ex_group, z.n_groups, b.ex_rec, b.ex_cs, b.incs_wr,
-                                                   b.cs_sid, b.cs_rel_idx, b.ex_dep_off, b.ex_dep_cnt, b.dep_pool,
-                                                   z.pool_cap, b.st);
+  auto fw = lock_scope_cap(g.B) == kLockScopesSmall ? k_f_walk<kLockScopesSmall> : k_f_walk<kLockScopesLarge>;
+  fw<<<blocks(z.n_groups, 128), 128, 0, s>>>(b.ex_val, b.ex_group, z.n_groups, b.ex_rec, b.ex_cs, b.incs_wr,
+                                             b.cs_sid, b.cs_rel_idx, b.ex_dep_off, b.ex_dep_cnt, b.dep_pool,
+                                             z.pool_cap, b.st);
   count_launch();
   p.end();
 }

@@ -757,14 +757,14 @@ int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s
   a.plan = b.plan;
   a.recmeta = b.recmeta;
   // plan: per-agent stream of clock-changing steps with their static data resolved
-  p.begin("g_plan", double(z.n_sync + z.n_incs) * 64 + double(z.n_cs) * 2 * g.Wp * 4);
+  p.begin("g_plan", double(z.n_sync + z.n_incs) * 64 + double(z.n_cs) * 2 * g.RW * 4);
   if (z.n_cs) {
     k_recmeta<<<(z.n_cs + 255) / 256, 256, 0, s>>>(z.n_cs, b.cs_agent, b.cs_epoch, b.cs_rel_idx, b.cs_sid,
                                                     b.cs_rel_epoch, b.recmeta);
     count_launch();
     // snapshot rows start as SENTINEL: a reader accepts a row once none is left
-    cudaMemsetAsync(b.psnap, 0xFF, size_t(z.n_cs) * g.Wp * 4, s);
-    cudaMemsetAsync(b.hsnap, 0xFF, size_t(z.n_cs) * g.Wp * 4, s);
+    cudaMemsetAsync(b.psnap, 0xFF, size_t(z.n_cs) * g.RW * 4, s);
+    cudaMemsetAsync(b.hsnap, 0xFF, size_t(z.n_cs) * g.RW * 4, s);
   }
   if (z.n_incs) {
     k_flatcount<<<(z.n_incs + 255) / 256, 256, 0, s>>>(z.n_incs, b.exp_off, b.ex_dep_cnt, b.flat_off);
@@ -781,6 +781,13 @@ int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s
     count_launch();
   }
   p.end();
+  if (g.nT) {
+    // tile tables: each clock version and snapshot is a table (new tiles counted apart)
+    p.begin("g_propagate", double(z.n_rows) * g.RW * 4 + double(z.n_cs) * 2 * g.RW * 4);
+    const int rc = phaseG_wide(b, g, z, s);
+    p.end();
+    return rc;
+  }
   uint32_t grid, threads;
   size_t smem = 0;
   if (z.cta_barriers) {

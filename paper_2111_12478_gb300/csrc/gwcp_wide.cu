@@ -1,0 +1,633 @@
+// Wide clocks (W > 1024 agents, up to 8192): clock propagation and race check over
+// copy-on-write clock tiles.
+//
+// A clock of width W is cut into nT = ceil(W / 256) tiles of 256 u32 entries. Tiles live
+// in one pool and are immutable once written; a clock is a table of nT tile ids (id 0 is
+// the all-zero tile). A warp walks one agent as in the register-resident walker, but
+// lane T holds the ids of tile T of P_t and H_t instead of the entries themselves. A join
+// P_t |= X (Algorithms 1-2) compares ids tile by tile: an equal or zero tile costs
+// nothing, a differing one is merged by the whole warp (8 entries per lane) and the
+// result keeps an input's id when it equals that input, else it is written as a new
+// tile. Clocks shared after a barrier or an acquire therefore share their tiles, and a
+// clock version (the row the check reads) is a 128-byte table. A release snapshot is
+// two tables; the increment H_t[t] = N_t after it copies the one tile holding t.
+//
+// Publication: a writer fences after writing new tiles and before storing a table that
+// refers to them; tables are written once over SENTINEL words, so a reader accepts a
+// table once none of its nT words is SENTINEL. All waits are bounded (GWCP_ERR_TIMEOUT).
+// Pool exhaustion sets GWCP_ERR_OOM; the walker then keeps its old tile (the host grows
+// the pool and runs the analysis again).
+//
+// The check for wide clocks enumerates partners per access instead of holding a W-wide
+// table: accesses sorted by location are re-sorted stably by (location, class, agent);
+// for access b every (class, agent) group of its location whose class conflicts with b
+// is searched for its latest access before b, and an agent is tested once, against its
+// latest conflicting non-exempt access a*: race iff N(a*) > C_b[v] (the paper's check).
+#include <algorithm>
+
+#include "gwcp_internal.cuh"
+
+namespace gwcp {
+
+namespace {
+
+constexpr uint32_t kSpinLimitW = 1u << 23;
+constexpr uint32_t SENT = 0xFFFFFFFFu;
+enum : uint32_t { P_ACQ = 0, P_REL = 1, P_BAR = 2, P_INCS = 3 };
+enum : uint32_t { BAR_SINGLE = 0, BAR_CTA = 1, BAR_GLOBAL = 2 };
+
+struct WideArgs {
+  Geo g;
+  DevStatus* st;
+  const uint32_t *sy_start, *incs_off, *rowbase;
+  const uint4* plan;
+  const uint4* recmeta;
+  const uint32_t *pool, *flat;
+  uint32_t *rows, *psnap, *hsnap, *cursor;
+  uint32_t* tiles;
+  unsigned long long* tile_ctr;
+  unsigned long long tile_cap;
+  uint32_t n_locks;
+};
+
+__device__ __forceinline__ uint4 max4(uint4 x, uint4 y) {
+  return make_uint4(max(x.x, y.x), max(x.y, y.y), max(x.z, y.z), max(x.w, y.w));
+}
+__device__ __forceinline__ bool eq4(uint4 x, uint4 y) { return x.x == y.x && x.y == y.y && x.z == y.z && x.w == y.w; }
+
+__device__ __forceinline__ const uint4* tile_src(const WideArgs& a, uint32_t id) {
+  return reinterpret_cast<const uint4*>(a.tiles + size_t(id) * kTileW) + (threadIdx.x & 31) * 2;
+}
+__device__ __forceinline__ uint4* tile_dst(const WideArgs& a, uint32_t id) {
+  return reinterpret_cast<uint4*>(a.tiles + size_t(id) * kTileW) + (threadIdx.x & 31) * 2;
+}
+
+// a fresh tile id (warp-uniform); 0 when the pool is exhausted (GWCP_ERR_OOM set)
+__device__ __forceinline__ uint32_t alloc_tile(const WideArgs& a) {
+  unsigned long long id = 0;
+  if ((threadIdx.x & 31) == 0) {
+    id = atomicAdd(a.tile_ctr, 1ull);
+    if (id >= a.tile_cap) {
+      atomicCAS(&a.st->code, 0, GWCP_ERR_OOM);
+      id = 0;
+    }
+  }
+  return uint32_t(__shfl_sync(0xffffffffu, id, 0));
+}
+
+// my |= src, tile by tile (lane T < nT holds the ids of tile T)
+__device__ void merge_table(const WideArgs& a, uint32_t& my, uint32_t src, bool& dirty) {
+  const int lane = threadIdx.x & 31;
+  bool need = lane < int(a.g.nT) && src != 0 && src != my;
+  if (need && my == 0) {
+    my = src;
+    need = false;
+  }
+  uint32_t m = __ballot_sync(0xffffffffu, need);
+  while (m) {
+    const int T = __ffs(m) - 1;
+    m &= m - 1;
+    const uint32_t ia = __shfl_sync(0xffffffffu, my, T), ib = __shfl_sync(0xffffffffu, src, T);
+    const uint4* pa = tile_src(a, ia);
+    const uint4* pb = tile_src(a, ib);
+    const uint4 x0 = __ldcg(pa), x1 = __ldcg(pa + 1), y0 = __ldcg(pb), y1 = __ldcg(pb + 1);
+    const uint4 r0 = max4(x0, y0), r1 = max4(x1, y1);
+    uint32_t nid;
+    if (__all_sync(0xffffffffu, eq4(r0, x0) && eq4(r1, x1))) {
+      nid = ia;
+    } else if (__all_sync(0xffffffffu, eq4(r0, y0) && eq4(r1, y1))) {
+      nid = ib;
+    } else {
+      nid = alloc_tile(a);
+      if (nid) {
+        uint4* d = tile_dst(a, nid);
+        d[0] = r0;
+        d[1] = r1;
+        dirty = true;
+      } else {
+        nid = ia;
+      }
+    }
+    if (lane == T) my = nid;
+  }
+}
+
+// copy of tile `id` with entry e set to val; returns the new id (warp-uniform)
+__device__ uint32_t cow_set(const WideArgs& a, uint32_t id, uint32_t e, uint32_t val, bool& dirty) {
+  const int lane = threadIdx.x & 31;
+  const uint4* p = tile_src(a, id);
+  uint4 x0 = __ldcg(p), x1 = __ldcg(p + 1);
+  if (lane == int(e >> 3)) {
+    uint32_t* w = (e & 4) ? &x1.x : &x0.x;
+    const uint32_t c = e & 3;
+    if (c == 0) w[0] = val;
+    if (c == 1) w[1] = val;
+    if (c == 2) w[2] = val;
+    if (c == 3) w[3] = val;
+  }
+  const uint32_t nid = alloc_tile(a);
+  if (!nid) return id;
+  uint4* d = tile_dst(a, nid);
+  d[0] = x0;
+  d[1] = x1;
+  dirty = true;
+  return nid;
+}
+
+// entry t of the table held by the warp := val (copy of the tile holding t)
+__device__ __forceinline__ void set_entry_w(const WideArgs& a, uint32_t& my, uint32_t t, uint32_t val, bool& dirty) {
+  const uint32_t T = t / kTileW;
+  const uint32_t id = __shfl_sync(0xffffffffu, my, T);
+  const uint32_t nid = cow_set(a, id, t % kTileW, val, dirty);
+  if ((threadIdx.x & 31) == int(T)) my = nid;
+}
+
+// a published table: wait (bounded) until none of its nT words is SENTINEL
+__device__ uint32_t read_table(const WideArgs& a, const uint32_t* tab, bool& abort) {
+  const int lane = threadIdx.x & 31;
+  const bool act = lane < int(a.g.nT);
+  uint32_t v = act ? __ldcg(tab + lane) : 0;
+  if (__all_sync(0xffffffffu, v != SENT)) return v;
+  uint32_t it = 0;
+  while (!abort) {
+    __nanosleep(64);
+    v = act ? __ldcg(tab + lane) : 0;
+    if (__all_sync(0xffffffffu, v != SENT)) return v;
+    if (++it > kSpinLimitW) {
+      if (lane == 0) atomicCAS(&a.st->code, 0, GWCP_ERR_TIMEOUT);
+      abort = true;
+    }
+  }
+  return v == SENT ? 0u : v;
+}
+
+__device__ __forceinline__ void publish(const WideArgs& a, uint32_t* tab, uint32_t id, bool& dirty) {
+  if (dirty) __threadfence();  // the tiles this warp wrote are visible before the table is
+  dirty = false;
+  if ((threadIdx.x & 31) < int(a.g.nT)) __stcg(tab + (threadIdx.x & 31), id);
+}
+
+__device__ __forceinline__ uint32_t entry_of(const WideArgs& a, uint32_t my, uint32_t t) {
+  // entry t of the warp's table, 0 for t >= W; every lane may ask for a different t.
+  // All lanes take part in the shuffle.
+  const bool ok = t < a.g.W;
+  const uint32_t id = __shfl_sync(0xffffffffu, my, ok ? int(t / kTileW) : 0);
+  return ok ? __ldcg(a.tiles + size_t(id) * kTileW + t % kTileW) : 0u;
+}
+
+// Join of one tile over a CTA's members (lane m holds member m's id for the tile):
+// the result keeps a member's id when only one distinct tile is present and no epoch
+// override falls in it; otherwise the maximum (with the overrides C_m[u_m] = N_m) is
+// written as a new tile, or replaced by an input it equals.
+__device__ uint32_t join_members(const WideArgs& a, uint32_t idm, uint32_t nm, uint32_t apb, uint32_t first,
+                                 uint32_t T, bool overrides, bool& dirty) {
+  const int lane = threadIdx.x & 31;
+  const bool act = uint32_t(lane) < apb && idm != 0;
+  const uint32_t same = __match_any_sync(0xffffffffu, act ? idm : 0xFFFFFFFFu);
+  const uint32_t leaders = __ballot_sync(0xffffffffu, act && (__ffs(same) - 1) == lane);
+  // members whose own entry lies in tile T
+  const uint32_t lo = T * kTileW, hi = lo + kTileW;
+  const bool own_here = overrides && uint32_t(lane) < apb && first + lane >= lo && first + lane < hi;
+  const uint32_t ovm = __ballot_sync(0xffffffffu, own_here);
+  if (!ovm && __popc(leaders) <= 1) return leaders ? __shfl_sync(0xffffffffu, idm, __ffs(leaders) - 1) : 0u;
+  uint4 r0 = make_uint4(0, 0, 0, 0), r1 = r0;
+  for (uint32_t m = leaders; m; m &= m - 1) {
+    const uint32_t id = __shfl_sync(0xffffffffu, idm, __ffs(m) - 1);
+    const uint4* p = tile_src(a, id);
+    r0 = max4(r0, __ldcg(p));
+    r1 = max4(r1, __ldcg(p + 1));
+  }
+  for (uint32_t m = ovm; m; m &= m - 1) {
+    const int mm = __ffs(m) - 1;
+    const uint32_t e = first + mm - lo, val = __shfl_sync(0xffffffffu, nm, mm);
+    if (lane == int(e >> 3)) {
+      uint32_t* w = (e & 4) ? &r1.x : &r0.x;
+      const uint32_t c = e & 3;
+      if (c == 0) w[0] = max(w[0], val);
+      if (c == 1) w[1] = max(w[1], val);
+      if (c == 2) w[2] = max(w[2], val);
+      if (c == 3) w[3] = max(w[3], val);
+    }
+  }
+  for (uint32_t m = leaders; m; m &= m - 1) {  // an input that equals the result keeps its id
+    const uint32_t id = __shfl_sync(0xffffffffu, idm, __ffs(m) - 1);
+    const uint4* p = tile_src(a, id);
+    if (__all_sync(0xffffffffu, eq4(r0, __ldcg(p)) && eq4(r1, __ldcg(p + 1)))) return id;
+  }
+  const uint32_t nid = alloc_tile(a);
+  if (!nid) return leaders ? __shfl_sync(0xffffffffu, idm, __ffs(leaders) - 1) : 0u;
+  uint4* d = tile_dst(a, nid);
+  d[0] = r0;
+  d[1] = r1;
+  dirty = true;
+  return nid;
+}
+
+// One warp per agent, one CTA per block of the traced program (agents_per_block <= 32).
+// MINB = CTAs of 1024 threads that must share an SM for all blocks to be co-resident.
+template <int MINB>
+__global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
+  extern __shared__ uint32_t sm[];
+  const Geo& g = a.g;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t apb = g.apb;
+  const uint32_t first = blockIdx.x * apb;
+  const uint32_t u = first + warp;
+  uint32_t* tabs = sm;                  // [apb][2][32] member tables
+  uint32_t* nbuf = sm + apb * 64;       // [apb] member epochs
+  uint32_t* J = nbuf + 32;              // [2][32] joined tables
+  __shared__ int start_code;
+  if (threadIdx.x == 0) start_code = *(volatile int*)&a.st->code;
+  __syncthreads();
+  if (start_code) return;
+  const bool act = lane < int(g.nT);
+  bool dirty = false, abort = false;
+  uint32_t pid = 0, hid = 0;
+  set_entry_w(a, hid, u, 1u, dirty);  // H_t = bottom{t := 1}
+  uint32_t N = 1;
+  unsigned long long joins = 0, visits = 0;
+  if (act) a.rows[size_t(a.rowbase[u]) * kTabW + lane] = 0;
+  const uint32_t k0 = a.sy_start[u], k1 = a.sy_start[u + 1];
+  const uint32_t pb = k0 + a.incs_off[k0], pe = k1 + a.incs_off[k1];
+  uint32_t* const cursor_row = a.cursor + size_t(u) * a.n_locks;
+  uint4 na = make_uint4(0, 0, 0, 0), nb = na;
+  if (pb < pe) {
+    na = a.plan[2 * size_t(pb)];
+    nb = a.plan[2 * size_t(pb) + 1];
+  }
+  for (uint32_t p = pb; p < pe; ++p) {
+    const uint4 ea = na, eb = nb;
+    if (p + 1 < pe) {  // the next entry's loads overlap this one
+      na = a.plan[2 * size_t(p + 1)];
+      nb = a.plan[2 * size_t(p + 1) + 1];
+    }
+    const uint32_t t = ea.x & 0xFF, row = ea.y;
+    if (t == P_ACQ || t == P_INCS) {
+      // acquire: P_t |= P_<l,s'>, H_t |= H_<l,s'>; in-section access: P_t |= L^w (| L^r)
+      const uint32_t off = ea.z, w = ea.w;
+      const uint32_t* list = t == P_ACQ ? a.pool : a.flat;
+      for (uint32_t q = 0; q < w; ++q) {
+        uint32_t x;
+        if (w <= 4)
+          x = q == 0 ? eb.x : q == 1 ? eb.y : q == 2 ? eb.z : eb.w;
+        else
+          x = __ldcg(list + off + q);
+        if (t == P_ACQ) {
+          const uint32_t sp = read_table(a, a.psnap + size_t(x) * kTabW, abort);
+          const uint32_t sh = read_table(a, a.hsnap + size_t(x) * kTabW, abort);
+          merge_table(a, pid, sp, dirty);
+          merge_table(a, hid, sh, dirty);
+          joins += 2;
+        } else {
+          merge_table(a, pid, read_table(a, a.hsnap + size_t(x) * kTabW, abort), dirty);
+          joins += 1;
+        }
+      }
+    } else if (t == P_REL) {
+      // release: pop other agents' records on this lock while their acquire is ordered
+      // before C_t, joining the released ones whose scope overlaps; then publish
+      const uint32_t c = ea.z, L = ea.w;
+      const uint32_t lo = eb.x, hi = eb.y, s = eb.z, my_idx = eb.w;
+      uint32_t cur = __ldcg(cursor_row + L);
+      bool stop = false;
+      while (!stop && lo + cur < hi) {
+        const uint32_t rec = lo + cur + lane;
+        const uint32_t nbr = min(32u, hi - (lo + cur));
+        uint4 m = make_uint4(NONE, 0, NONE, 0);
+        if (rec < hi) m = __ldg(a.recmeta + rec);
+        const uint32_t mag = m.x == NONE ? NONE : (m.x & 0xFFFF);
+        const uint32_t msid = m.x >> 16;
+        const bool mine = mag == u;
+        const bool joinable = !mine && m.z != NONE && m.z < my_idx && scopes_overlap(msid, s);
+        uint32_t start = 0;
+        uint32_t pv = entry_of(a, pid, mag);
+        while (start < nbr) {
+          const bool in = uint32_t(lane) >= start && uint32_t(lane) < nbr;
+          const uint32_t fail = __ballot_sync(0xffffffffu, in && !mine && m.y > pv);
+          const uint32_t f = fail ? uint32_t(__ffs(fail) - 1) : nbr;
+          const uint32_t popped = __ballot_sync(0xffffffffu, in && uint32_t(lane) < f && joinable);
+          // of one agent's popped records only the latest is joined (its H dominates)
+          const uint32_t same = __match_any_sync(0xffffffffu, ((popped >> lane) & 1u) ? mag : 0xFFFFFFFFu);
+          const uint32_t wave = __ballot_sync(0xffffffffu, ((popped >> lane) & 1u) && (same >> lane) <= 1u);
+          visits += __popc(__ballot_sync(0xffffffffu, in && uint32_t(lane) <= f && !mine));
+          for (uint32_t wm = wave; wm; wm &= wm - 1) {
+            const uint32_t r = lo + cur + (__ffs(wm) - 1);
+            merge_table(a, pid, read_table(a, a.hsnap + size_t(r) * kTabW, abort), dirty);
+            ++joins;
+          }
+          if (f == nbr) {
+            start = nbr;
+          } else if (wave) {
+            start = f;  // P grew: test the failing record again
+            pv = entry_of(a, pid, mag);
+          } else {
+            stop = true;  // P unchanged: the record stays unordered
+            start = f;
+            break;
+          }
+        }
+        cur += start;
+      }
+      if (lane == 0) __stcg(cursor_row + L, cur);
+      publish(a, a.psnap + size_t(c) * kTabW, pid, dirty);
+      publish(a, a.hsnap + size_t(c) * kTabW, hid, dirty);
+      set_entry_w(a, hid, u, N + 1, dirty);  // H_t[t] = N_t after the increment
+      ++N;
+    } else {
+      // barrier: C and H joined over the members
+      const uint32_t mode = eb.x;
+      if (mode == BAR_SINGLE) {
+        set_entry_w(a, pid, u, N, dirty);  // P_t = C_t
+      } else {
+        if (act) {
+          tabs[(warp * 2) * 32 + lane] = pid;
+          tabs[(warp * 2 + 1) * 32 + lane] = hid;
+        }
+        if (lane == 0) nbuf[warp] = N;
+        __syncthreads();
+        const uint32_t nw = blockDim.x >> 5;
+        bool wrote = false;
+        for (uint32_t T = warp; T < g.nT; T += nw) {
+          const bool mem = uint32_t(lane) < apb;
+          const uint32_t cm = mem ? tabs[(lane * 2) * 32 + T] : 0, hm = mem ? tabs[(lane * 2 + 1) * 32 + T] : 0;
+          const uint32_t nm = mem ? nbuf[lane] : 0;
+          const uint32_t jc = join_members(a, cm, nm, apb, first, T, true, wrote);
+          const uint32_t jh = join_members(a, hm, nm, apb, first, T, false, wrote);
+          if (lane == 0) {
+            J[T] = jc;
+            J[32 + T] = jh;
+          }
+        }
+        if (wrote) __threadfence();  // members may publish the joined tiles at once
+        __syncthreads();
+        pid = act ? J[lane] : 0;
+        hid = act ? J[32 + lane] : 0;
+        joins += 2 * nw;
+        // J is rewritten only after the next barrier's first __syncthreads, which every
+        // member reaches after reading it here
+      }
+      set_entry_w(a, hid, u, N + 1, dirty);
+      ++N;
+    }
+    if (act) a.rows[size_t(row) * kTabW + lane] = pid;
+  }
+  if (dirty) __threadfence();
+  if (lane == 0) {
+    atomicAdd(&a.st->joins, joins);
+    atomicAdd(&a.st->loop_visits, visits);
+  }
+}
+
+// ---- check ---------------------------------------------------------------------------
+
+__global__ void k_wc_runflags(const uint64_t* key, uint32_t n, uint32_t* flag) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) flag[p] = (p == 0 || key[p] != key[p - 1]) ? 1u : 0u;
+}
+
+// composite key (run, class, agent) for the stable regrouping; value = key-order position
+__global__ void k_wc_compose(const uint32_t* run_excl, const uint32_t* flag, const uint32_t* idx,
+                             const AccInfo* info, uint32_t n, uint64_t* ck, uint32_t* cv) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const uint32_t run = run_excl[p] + flag[p] - 1;
+  const uint32_t who = info[idx[p]].who;
+  ck[p] = (uint64_t(run) << 15) | (uint64_t(who_class(who)) << 13) | who_agent(who);
+  cv[p] = p;
+}
+
+// group starts over the sorted composite keys, and per (run, class) group counts
+__global__ void k_wc_groupflags(const uint64_t* ck, uint32_t n, uint32_t* gflag) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) gflag[i] = (i == 0 || ck[i] != ck[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_wc_groups(const uint64_t* ck, const uint32_t* gflag, const uint32_t* gexcl, uint32_t n,
+                            uint32_t* grp_lo, uint32_t* grp_agent, uint32_t* rc_cnt) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !gflag[i]) return;
+  const uint32_t gi = gexcl[i];
+  grp_lo[gi] = i;
+  grp_agent[gi] = uint32_t(ck[i] & 0x1FFF);
+  atomicAdd(rc_cnt + (ck[i] >> 13), 1u);  // (run << 2 | class)
+}
+
+struct WideCheckArgs {
+  Geo g;
+  uint32_t n;
+  const uint32_t* idx;       // key order -> trace index
+  const uint32_t* flag;      // run starts
+  const uint32_t* run_excl;  // exclusive scan of flag
+  const uint32_t* gs;        // grouped order -> key-order position
+  const uint32_t* grp_lo;    // [n_groups + 1]
+  const uint32_t* grp_agent;
+  const uint32_t* rc_off;    // [(run << 2 | class) + 1]
+  const AccInfo* info;
+  const uint32_t* rows;
+  const uint32_t* tiles;
+  unsigned long long tile_cap;  // ids at or above it (rows a failed walk left stale) read as zero
+  uint64_t* races;
+  unsigned long long race_cap;
+  DevStatus* st;
+};
+
+// latest key-order position < p in group gi, or NONE
+__device__ __forceinline__ uint32_t pred_in_group(const WideCheckArgs& a, uint32_t gi, uint32_t p) {
+  uint32_t lo = a.grp_lo[gi], hi = a.grp_lo[gi + 1];  // positions gs[lo..hi) ascend
+  if (lo == hi || a.gs[lo] >= p) return NONE;
+  while (hi - lo > 1) {  // invariant: gs[lo] < p, and gs[hi] >= p or hi is the end
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a.gs[mid] < p)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return a.gs[lo];
+}
+
+// group of agent v among the groups [g0, g1) (sorted by agent), or NONE
+__device__ __forceinline__ uint32_t find_agent(const WideCheckArgs& a, uint32_t g0, uint32_t g1, uint32_t v) {
+  while (g0 < g1) {
+    const uint32_t mid = (g0 + g1) >> 1;
+    const uint32_t x = a.grp_agent[mid];
+    if (x == v) return mid;
+    if (x < v)
+      g0 = mid + 1;
+    else
+      g1 = mid;
+  }
+  return NONE;
+}
+
+// classes a later access of class cb conflicts with and is not exempt from (bit q = class
+// q), given whether the partner shares b's block
+__device__ __forceinline__ uint32_t conflict_classes(uint32_t cb, bool same_block) {
+  switch (cb) {
+    case C_READ: return 0b1110;
+    case C_WRITE: return 0b1111;
+    case C_ATOM_CTA: return same_block ? 0b0011 : 0b0111;
+    default: return 0b0011;
+  }
+}
+
+// partner tests of the access at key-order position p; returns how many were made
+__device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p) {
+  const uint32_t b = a.idx[p];
+  const AccInfo ib = a.info[b];
+  const uint32_t u = who_agent(ib.who), cb = who_class(ib.who), bu = who_block(ib.who);
+  const uint32_t run = a.run_excl[p] + a.flag[p] - 1;
+  const uint32_t* rowtab = a.rows + size_t(ib.row) * kTabW;
+  const uint32_t any_mask = conflict_classes(cb, false) | conflict_classes(cb, true);
+  uint32_t tests = 0;
+  for (uint32_t q = 0; q < 4; ++q) {
+    if (!((any_mask >> q) & 1u)) continue;
+    const uint32_t g0 = a.rc_off[(run << 2) | q], g1 = a.rc_off[((run << 2) | q) + 1];
+    for (uint32_t gi = g0; gi < g1; ++gi) {
+      const uint32_t v = a.grp_agent[gi];
+      if (v == u) continue;
+      const uint32_t cm = conflict_classes(cb, v / a.g.apb == bu);
+      if (!((cm >> q) & 1u)) continue;
+      const uint32_t pos = pred_in_group(a, gi, p);
+      if (pos == NONE) continue;
+      // tested once per agent: from the class holding its latest conflicting access
+      bool latest = true;
+      for (uint32_t q2 = 0; q2 < 4 && latest; ++q2) {
+        if (q2 == q || !((cm >> q2) & 1u)) continue;
+        const uint32_t h0 = a.rc_off[(run << 2) | q2], h1 = a.rc_off[((run << 2) | q2) + 1];
+        const uint32_t g2 = find_agent(a, h0, h1, v);
+        if (g2 == NONE) continue;
+        const uint32_t pos2 = pred_in_group(a, g2, p);
+        if (pos2 != NONE && (pos2 > pos || (pos2 == pos && q2 < q))) latest = false;
+      }
+      if (!latest) continue;
+      ++tests;
+      const uint32_t ai = a.idx[pos];
+      const uint32_t na = a.info[ai].epoch;
+      const uint32_t tid = __ldg(rowtab + v / kTileW);
+      const uint32_t cv = tid < a.tile_cap ? __ldg(a.tiles + size_t(tid) * kTileW + v % kTileW) : 0u;
+      if (na > cv) {  // N(a*) > C_b[v]
+        const unsigned long long at = atomicAdd(&a.st->n_races, 1ull);
+        if (at < a.race_cap) a.races[at] = (uint64_t(b) << 32) | ai;
+      }
+    }
+  }
+  return tests;
+}
+
+__global__ void k_wc_check(WideCheckArgs a) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t tests = 0;
+  if (p < a.n) tests = check_one(a, p);
+  tests = __reduce_add_sync(0xffffffffu, tests);
+  if ((threadIdx.x & 31) == 0 && tests) atomicAdd(&a.st->partner_tests, (unsigned long long)tests);
+}
+
+__global__ void k_wc_grp_end(const uint32_t* n_groups, uint32_t n, uint32_t* grp_lo) { grp_lo[*n_groups] = n; }
+
+inline uint32_t nblk(uint64_t n, uint32_t t) { return uint32_t((n + t - 1) / t); }
+
+}  // namespace
+
+// Launch of the wide walker (the plan stream is already built on s).
+int phaseG_wide(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s) {
+  WideArgs a{};
+  a.g = g;
+  a.st = b.st;
+  a.sy_start = b.sy_start;
+  a.incs_off = b.incs_cnt;
+  a.rowbase = b.vcount;
+  a.plan = b.plan;
+  a.recmeta = b.recmeta;
+  a.pool = b.dep_pool;
+  a.flat = b.flat;
+  a.rows = b.rows;
+  a.psnap = b.psnap;
+  a.hsnap = b.hsnap;
+  a.cursor = b.cursor;
+  a.tiles = b.tiles;
+  a.tile_ctr = reinterpret_cast<unsigned long long*>(&b.st->spare[2]);
+  a.tile_cap = z.tile_cap;
+  a.n_locks = z.n_locks;
+  const uint32_t threads = g.apb * 32;
+  const size_t smem = (size_t(g.apb) * 64 + 32 + 64) * 4;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // the variant with the most registers whose CTAs are all co-resident
+  void* kern = nullptr;
+  for (void* k : {reinterpret_cast<void*>(k_prop_wide<1>), reinterpret_cast<void*>(k_prop_wide<2>)}) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, int(threads), smem) != cudaSuccess)
+      return GWCP_ERR_CUDA;
+    if (uint64_t(per_sm) * sms >= g.B) {
+      kern = k;
+      break;
+    }
+  }
+  if (!kern) return GWCP_ERR_UNSUPPORTED;  // walkers must be co-resident
+  void* args[] = {&a};
+  if (cudaLaunchCooperativeKernel(kern, dim3(g.B), dim3(threads), args, smem, s) != cudaSuccess) return GWCP_ERR_CUDA;
+  count_launch();
+  return GWCP_OK;
+}
+
+// Regrouping of the key-sorted accesses by (location, class, agent); runs beside the
+// propagation (it needs AccInfo and the key order, not the clocks).
+void phaseI_wide_group(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t s, Prof& p) {
+  (void)g;
+  const uint32_t n = z.n_acc;
+  if (!n) return;
+  p.begin("i_wide_group", double(n) * (8 + 4 + 16 + 12 * 3 * 5 + 16), s);
+  k_wc_runflags<<<nblk(n, 256), 256, 0, s>>>(b.acc_key, n, b.wc_flag);
+  count_launch();
+  scan_exclusive(b.wc_flag, b.wc_run, n, b.wc_run + n, tmp, s);
+  k_wc_compose<<<nblk(n, 256), 256, 0, s>>>(b.wc_run, b.wc_flag, b.acc_idx, b.acc_info, n, b.wc_key, b.wc_val);
+  count_launch();
+  // runs < n <= 2^30: key bits 15 .. 15 + ceil(log2 n)
+  uint32_t rb = 1;
+  while ((1ull << rb) < n) ++rb;
+  const uint64_t mask = (((1ull << rb) - 1) << 15) | 0x7FFFull;
+  if (radix_sort_pairs(b.wc_key, b.wc_val, b.wc_key2, b.wc_val2, n, mask, tmp, s)) {
+    std::swap(b.wc_key, b.wc_key2);
+    std::swap(b.wc_val, b.wc_val2);
+  }
+  k_wc_groupflags<<<nblk(n, 256), 256, 0, s>>>(b.wc_key, n, b.wc_gflag);
+  count_launch();
+  scan_exclusive(b.wc_gflag, b.wc_gexcl, n, b.wc_gexcl + n, tmp, s);
+  cudaMemsetAsync(b.wc_rc, 0, (size_t(n) * 4 + 2) * 4, s);
+  k_wc_groups<<<nblk(n, 256), 256, 0, s>>>(b.wc_key, b.wc_gflag, b.wc_gexcl, n, b.wc_grp_lo, b.wc_grp_agent,
+                                          b.wc_rc);
+  count_launch();
+  k_wc_grp_end<<<1, 1, 0, s>>>(b.wc_gexcl + n, n, b.wc_grp_lo);  // grp_lo[n_groups] = n
+  count_launch();
+  scan_exclusive(b.wc_rc, b.wc_rc, size_t(n) * 4 + 1, nullptr, tmp, s);
+  p.end();
+}
+
+void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
+  const uint32_t n = z.n_acc;
+  if (!n) return;
+  WideCheckArgs a{};
+  a.g = g;
+  a.n = n;
+  a.idx = b.acc_idx;
+  a.flag = b.wc_flag;
+  a.run_excl = b.wc_run;
+  a.gs = b.wc_val;
+  a.grp_lo = b.wc_grp_lo;
+  a.grp_agent = b.wc_grp_agent;
+  a.rc_off = b.wc_rc;
+  a.info = b.acc_info;
+  a.rows = b.rows;
+  a.tiles = b.tiles;
+  a.tile_cap = z.tile_cap;
+  a.races = b.races;
+  a.race_cap = z.race_cap;
+  a.st = b.st;
+  p.begin("i_check", double(n) * (4 + 16 + 4 + 4 + 4 + 8));
+  k_wc_check<<<nblk(n, 256), 256, 0, s>>>(a);
+  count_launch();
+  p.end();
+}
+
+}  // namespace gwcp

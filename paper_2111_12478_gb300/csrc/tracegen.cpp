@@ -133,6 +133,7 @@ struct GenParams {
   double nest_prob;
   double shared_frac;
   double p_syncwarp;
+  uint32_t plant_min_rank;  // planted accesses use address ranks >= this (0: any rank)
 };
 
 int gwcp_tracegen_run(const GenParams* p, void* out_events, uint64_t* n_written) {
@@ -210,6 +211,7 @@ int gwcp_tracegen_run(const GenParams* p, void* out_events, uint64_t* n_written)
   auto planted = [&](uint32_t t, bool exact) {
     const uint32_t b = block_of(t);
     uint64_t r = zipf(rng);
+    if (r < p->plant_min_rank && p->plant_min_rank < NR) r = p->plant_min_rank + rng.below(NR - p->plant_min_rank);
     uint32_t kind = exact ? 0 : uint32_t(rng.below(5));
     if (exact) {
       // a read by another agent directly before the planted write: nothing can order

@@ -269,10 +269,13 @@ class _GenParams(ctypes.Structure):
         ("nest_prob", ctypes.c_double),
         ("shared_frac", ctypes.c_double),
         ("p_syncwarp", ctypes.c_double),
+        ("plant_min_rank", ctypes.c_uint32),
     ]
 
 
-# The workloads the benchmark and the parity tests use, by name. Sizes follow the
+# The workloads the benchmark and the parity tests use, by name. In the 8192-warp trace
+# the planted accesses avoid the 65536 hottest address ranks: a write planted on a read-
+# mostly address read by all 8192 warps would race with every later unordered read. Sizes follow the
 # trace shapes the analysis targets: a 64-thread single-block trace at thread
 # granularity, a 64-warp 8-block trace, a 8192-warp 256-block trace.
 WORKLOADS = {
@@ -291,7 +294,7 @@ WORKLOADS = {
                                  dev_lock_frac=0.3, p_read=0.66, p_write=0.32, p_atomic=0.003,
                                  p_acqrel=0.004, p_fence=0.002, p_barrier=0.001, atomic_dev_frac=0.3,
                                  plant_frac=0.001, n_plant_exact=0, cs_len_mean=3.0, nest_prob=0.1,
-                                 shared_frac=0.1, p_syncwarp=0.0),
+                                 shared_frac=0.1, p_syncwarp=0.0, plant_min_rank=65536),
 }
 
 

@@ -106,6 +106,41 @@ def test_wide_clocks(ctx, W, apb, gran):
     same(ctx, ev, geo)
 
 
+# ---- clocks wider than 1024 agents: tables of copy-on-write tiles -------------------------
+
+@pytest.mark.parametrize("W,apb", [(1088, 32), (1280, 16), (2048, 32)])
+def test_tiled_random(ctx, W, apb):
+    # 1088 agents: a ragged last tile; 1280/16: five tiles, a block of 16 per CTA
+    for fam in ("mixed", "uniform_bar", "dev_locks", "barriers", "nosync"):
+        for seed in range(2):
+            ev, geo = TG.random_small(seed, fam, n_events=5000, num_agents=W, agents_per_block=apb,
+                                      granularity=WARP_GRAN, n_locks=4, n_keys=8)
+            same(ctx, ev, geo)
+
+
+def test_tiled_clock_rows(ctx):
+    ev, geo = TG.random_small(3, "mixed", n_events=4000, num_agents=1280, agents_per_block=16,
+                              granularity=WARP_GRAN, n_locks=4, n_keys=6)
+    rng = np.random.default_rng(0)
+    cand = [i for i in range(len(ev)) if ev["op"][i] in (READ, WRITE, ATOMIC, ACQ, REL)]
+    idx = sorted(rng.choice(cand, size=300, replace=False).tolist())
+    r = O.run(ev, *geo.astuple(), clock_events=idx)
+    gpu_races(ctx, ev, geo)
+    for i in idx:
+        assert np.array_equal(ctx.debug_clock(i, 0, geo.num_agents), r.clocks_c[i]), i
+        if ev["op"][i] == REL:
+            assert np.array_equal(ctx.debug_clock(i, 1, geo.num_agents), r.clocks_h[i]), i
+
+
+@pytest.mark.parametrize("blocks,n,seed", [(64, 300_000, 1), (256, 150_000, 2), (256, 1_000_000, 3)])
+def test_tiled_workload(ctx, blocks, n, seed):
+    # the 8192-warp workload's shape (scoped sync 1%, Zipf(1.05)) on few addresses
+    ev, geo, _ = TG.generate(seed, n_events=n, workload="256blk_8192warp_200M", num_blocks=blocks, n_ranks=2000,
+                             plant_min_rank=64)
+    got = same(ctx, ev, geo)
+    assert len(got) > 0
+
+
 def test_invalid_traces_first_bad_index(ctx):
     from paper_2111_12478_gb300 import gwcp
 
