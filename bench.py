@@ -120,6 +120,126 @@ def traffic_for(phase):
     return None
 
 
+def bench_batched(args, local, torch, gwcp, tracegen, np):
+    """The batched workload (512 independent traces, 10k-5M events, 64-4096 warps; inputs
+    resident on the device): the plain path (one context, one trace after another) against
+    the pool (lanes autotuned on every 8th trace). Wall-clock seconds with the device
+    synchronised on both sides; the pool's race sets must equal the plain path's."""
+    specs = tracegen.many_specs(SEED, **tracegen.BATCH_WORKLOAD)
+    traces = tracegen.generate_many(specs, threads=os.cpu_count() or 8)
+    n_total = int(sum(len(ev) for ev, _ in traces))
+    dev = [torch.from_numpy(ev.view(np.uint8)).to(f"cuda:{local}") for ev, _ in traces]
+    geos = [geo.astuple() for _, geo in traces]
+    ctx = gwcp.Context(local)
+
+    def plain():
+        out = []
+        for d, g in zip(dev, geos):
+            ctx.load_trace(d, *g)
+            ctx.compute_order()
+            out.append(ctx.report_races())
+        return out
+
+    plain()  # sizes the context's buffers
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ref = plain()
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    ctx.close()
+    pool = gwcp.Pool(local, lanes=args.lanes)
+    items = list(zip(dev, geos))
+    best, tune = pool.autotune(items[::8])
+    caps = [len(r) for r in ref]
+    pool.run_batch(items, caps)  # warm-up: lanes size their buffers
+    times, got = [], None
+    for _ in range(args.batch_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        got = pool.run_batch(items, caps)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    identical = all(rc == 0 and np.array_equal(r, w) for (r, rc, _), w in zip(got, ref))
+    pool.close()
+    # the oracle on the short, narrow traces of the batch
+    exact = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle
+
+        idx = [i for i, (ev, g) in enumerate(traces) if len(ev) <= 60_000 and g.num_agents <= 1024][:12]
+        exact = all(np.array_equal(oracle.run(traces[i][0], *geos[i]).races, ref[i]) for i in idx)
+        exact = {"traces_checked": len(idx), "identical": bool(exact)}
+    t_b = statistics.median(times)
+    return {"workload": "512 traces, 10k-5M events (log-uniform), 64-4096 warps, 64-warp 10M-event op mix",
+            "traces": len(traces), "events": n_total, "lanes": best, "autotune_s": tune,
+            "value": n_total / t_b, "unit": "events/s", "s_per_batch": t_b, "batches_timed": len(times),
+            "plain": {"value": n_total / t_plain, "s": t_plain, "path": "one context, traces in sequence"},
+            "speedup_vs_plain": t_plain / t_b, "race_sets_identical_to_plain": identical,
+            "oracle_sample": exact, "n_races": int(sum(len(r) for r in ref)),
+            "inputs": "device-resident", "timing": "wall clock, device synchronised on both sides"}
+
+
+def bench_served(args, local, torch, gwcp, tracegen, np, lanes):
+    """The served workload: requests arriving as a Poisson process at 200/s, 10k-20M
+    events each (prefixes of one 20M-event trace per width class, in pinned host memory,
+    copied to the device by the pool), races copied back to host memory. The same arrival
+    schedule runs on the pool's lanes and on a single lane (the plain path, one trace at a
+    time); latency = completion - arrival on the pool's clock."""
+    cfg = tracegen.SERVE_WORKLOAD
+    base = tracegen.generate_many(tracegen.serve_base_specs(SEED, cfg["n_max"]), threads=os.cpu_count() or 8)
+    pinned = [torch.from_numpy(ev.view(np.uint8)).pin_memory() for ev, _ in base]
+    geos = [g.astuple() for _, g in base]
+    arr, wid, lens = tracegen.serve_requests(SEED, args.serve_requests, cfg["rate"], cfg["n_min"], cfg["n_max"],
+                                            len(base))
+    pool = gwcp.Pool(local, lanes=max(lanes, 1))
+
+    def schedule(active):
+        pool.set_active_lanes(active)
+        # warm the lanes on a few of the longest requests, then serve the schedule
+        big = np.argsort(-lens)[: active]
+        for i in big:
+            pool.wait(pool.submit(pinned[wid[i]][: int(lens[i]) * 16], geos[wid[i]], 0))
+        tickets = [None] * len(arr)
+        start = pool.now() + 0.02
+
+        def submit_all():
+            for i in range(len(arr)):
+                dt = start + arr[i] - pool.now()
+                if dt > 0:
+                    time.sleep(dt)
+                n = int(lens[i])
+                tickets[i] = pool.submit(pinned[wid[i]][: n * 16], geos[wid[i]], 3 * n + 1024)
+
+        th = threading.Thread(target=submit_all)
+        th.start()
+        infos = []
+        for i in range(len(arr)):
+            while tickets[i] is None:
+                time.sleep(0.0005)
+            races, info = pool.wait(tickets[i])
+            infos.append((info.rc, info.n_races, info.t_submit, info.t_done))
+        codes = {}
+        for rc, *_ in infos:
+            codes[rc] = codes.get(rc, 0) + 1
+        th.join()
+        lat = np.array([d - s for _, _, s, d in infos])
+        span = max(d for *_, d in infos) - min(s for _, _, s, _ in infos)
+        ok = sum(1 for rc, *_ in infos if rc == 0)
+        return {"lanes": active, "value": float(lens.sum()) / span, "unit": "events/s",
+                "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                "mean_latency_s": float(lat.mean()), "span_s": span, "requests_ok": ok,
+                "result_codes": {str(k): v for k, v in codes.items()},
+                "n_races": int(sum(n for _, n, _, _ in infos))}
+
+    served = schedule(max(lanes, 1))
+    plain = schedule(1)
+    pool.close()
+    return {"workload": f"Poisson {cfg['rate']:.0f} req/s, 10k-20M events (log-uniform), 64-4096 warps",
+            "requests": len(arr), "offered_events_per_s": float(lens.sum()) / float(arr[-1]),
+            **served, "plain": plain, "speedup_vs_plain": served["value"] / plain["value"],
+            "inputs": "pinned host memory; H2D copy and race D2H inside each request"}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, on the host cores, on a bounded
     prefix of the same workload per step (rank 0 only)."""
@@ -162,6 +282,11 @@ def main():
     ap.add_argument("--events", type=int, default=0, help="analyse only this many events of the workload "
                     "(profiling runs); 0 = the full workload")
     ap.add_argument("--workload", default=WORKLOAD, help="a trace shape of tracegen.WORKLOADS")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched (512-trace) measurement")
+    ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson arrivals) measurement")
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--lanes", type=int, default=32, help="lanes of the batched/served pool")
     ap.add_argument("--cpu-events", type=int, default=0, help="events of the trace the oracle runs on for the "
                     "CPU baseline and the exactness check (a prefix); 0 = the whole trace up to 1024 agents, "
                     "300000 events beyond")
@@ -319,11 +444,20 @@ def main():
             "race_set_bit_exact": exact, "n_races": int(n_races),
             "gpu_launches": int(launches), "clocks": clk,
         }
+    ctx.close()
+    ctx_e2e.close()
+    del dev, pinned
+    if not args.no_batched:
+        b = bench_batched(args, local, torch, gwcp, tracegen, np)
+        if result is not None:
+            result["batched"] = b
+    if not args.no_served:
+        v = bench_served(args, local, torch, gwcp, tracegen, np, b["lanes"] if not args.no_batched else 16)
+        if result is not None:
+            result["served"] = v
     if dist:
         dist.barrier()
         dist.destroy_process_group()
-    ctx.close()
-    ctx_e2e.close()
     if result is not None:
         print(json.dumps(result), flush=True)
 

@@ -90,9 +90,14 @@ typedef struct {
 } gwcp_race;
 
 typedef struct {
-  uint64_t race_capacity; /* races kept on the device; 0 = max(2^20, n) */
+  uint64_t race_capacity; /* races kept on the device; 0 = automatic: max(2^20, n), grown
+                             (the check runs again) when a trace has more races */
   uint32_t profile;       /* 1 = time each kernel with CUDA events (gwcp_profile_get) */
-  uint32_t reserved[5];
+  uint32_t blocking_sync; /* 1 = host waits sleep on a blocking-sync event instead of
+                             spinning (for many contexts driven by many host threads) */
+  uint32_t timeline;      /* 1 = the check records when each of its chunks ends and how many
+                             races it found (gwcp_check_timeline) */
+  uint32_t reserved[3];
 } gwcp_options;
 
 typedef struct gwcp_ctx gwcp_ctx; /* opaque; owns all device memory it allocates */
@@ -132,8 +137,8 @@ int gwcp_compute_order(gwcp_ctx* ctx, void* cuda_stream);
 
 /* Waits for the analysis on cuda_stream and copies up to `cap` races into host memory
  * `out` (may be NULL when cap is 0). *n_races receives the total number of races.
- * Returns GWCP_ERR_CAPACITY if cap < total, or if the context's race_capacity was too
- * small (then *n_races is the count required; raise race_capacity and recompute). */
+ * Returns GWCP_ERR_CAPACITY if cap < total, or if a fixed race_capacity was too small
+ * (then *n_races is the count required; raise race_capacity and recompute). */
 int gwcp_report_races(gwcp_ctx* ctx, gwcp_race* out, uint64_t cap, uint64_t* n_races, void* cuda_stream);
 
 /* Test hook. Copies the clock of event `event_idx` into out_W (num_agents entries):
@@ -182,6 +187,138 @@ int gwcp_counters(const gwcp_ctx* ctx, uint64_t* out8);
  * on it and must be serialised by the caller. */
 int gwcp_analyze_noalloc(const gwcp_event* ev_dev, uint64_t n, const gwcp_geometry* geo, gwcp_race* races_dev,
                          uint64_t races_cap, uint64_t* n_races, uint64_t* first_bad_index, void* cuda_stream);
+
+/* ---- address ranker --------------------------------------------------------------
+ * Not in the paper. A small network scores each location from features of its accesses so
+ * that the per-location check visits likely-racy locations first; every location is still
+ * checked and the race set does not change. Network: 16 features -> 64 -> 64 -> 1, bfloat16
+ * weights and activations with float accumulation; parameters are one float vector of
+ * GWCP_RANK_PARAMS values: W1[64][16], b1[64], W2[64][64], b2[64], w3[64], b3.
+ * Features of a location (float[16]; its accesses in trace order): log1p of the access,
+ * read, write and atomic counts; log1p of the number of distinct agents and blocks (both
+ * mod 64); block- and device-scoped atomic fractions; fraction inside a critical section;
+ * shared-memory flag; acquire/release/barrier events per trace position over the span
+ * from first to last access; log1p(span); share of the first access's agent; agent
+ * switches and agent switches with a write or atomic per consecutive pair; fraction of
+ * writes and atomics inside a critical section. */
+#define GWCP_RANK_PARAMS 5313
+#define GWCP_RANK_FEATURES 16
+
+/* Makes the next gwcp_compute_order of ctx check locations in descending score order
+ * (traces of up to 1024 agents; wider traces are checked in location order). theta: host
+ * array of GWCP_RANK_PARAMS floats, copied; NULL turns the ranker off. */
+int gwcp_set_ranker(gwcp_ctx* ctx, const float* theta);
+
+/* After a successful gwcp_compute_order: the features of every accessed location, in the
+ * order the check visited them (ascending location key when no ranker is set), into device
+ * arrays feat (cap x GWCP_RANK_FEATURES floats) and keys (cap location keys: the address,
+ * or (1 << 63) | (block << 40) | address for shared memory). *n_loc receives the number of
+ * locations; GWCP_ERR_CAPACITY when cap < *n_loc. Synchronous on cuda_stream. */
+int gwcp_location_features(gwcp_ctx* ctx, float* feat, uint64_t* keys, uint64_t cap, uint64_t* n_loc,
+                           void* cuda_stream);
+
+/* Scores of n feature rows (device arrays; theta on the device). Asynchronous. */
+int gwcp_rank_scores(const float* theta, const float* feat, uint64_t n, float* scores, void* cuda_stream);
+
+/* Gradient of the mean weighted logistic loss over n rows (labels 0 or 1; positives weighted
+ * by pos_weight) with respect to theta, into grad (GWCP_RANK_PARAMS floats) and the loss
+ * into *loss (device pointers). The bfloat16 roundings count as the identity. Asynchronous. */
+int gwcp_rank_grad(const float* theta, const float* feat, const float* labels, uint64_t n, float pos_weight,
+                   float* grad, float* loss, void* cuda_stream);
+
+typedef struct {
+  uint32_t epochs, batch; /* passes over the rows; rows per step */
+  float lr, pos_weight;   /* Adam step size (beta 0.9 / 0.999, eps 1e-8); weight of label 1 */
+  uint32_t reserved[4];
+} gwcp_train_options;
+
+/* Trains theta (device, updated in place) with Adam on mini-batches of consecutive rows
+ * (shuffle the rows beforehand); epoch_loss (host, may be NULL) receives the mean batch
+ * loss of each epoch. Allocates its optimizer state for the call. Synchronous. */
+int gwcp_rank_train(float* theta, const float* feat, const float* labels, uint64_t n, const gwcp_train_options* o,
+                    float* epoch_loss, void* cuda_stream);
+
+/* With options.timeline: the check's start (globaltimer ns) and, per chunk of the sorted
+ * access stream in check order, the globaltimer when it ended and the races it found.
+ * Traces of up to 1024 agents. GWCP_ERR_CAPACITY when cap < *n_chunks. Synchronous. */
+int gwcp_check_timeline(gwcp_ctx* ctx, uint64_t* start_ns, uint64_t* chunk_end_ns, uint32_t* chunk_races,
+                        uint64_t cap, uint64_t* n_chunks);
+
+/* ---- batched and served analysis: a pool of lanes ----------------------------------
+ * The paper analyses one trace at a time. A pool runs many independent traces at once on
+ * one GPU: each lane is a context (as gwcp_create) with its own CUDA stream, driven by a
+ * host thread of the pool, and runs the same analysis as gwcp_load_trace +
+ * gwcp_compute_order + gwcp_report_races; lanes overlap on the device, so short traces
+ * and traces whose propagation occupies few SMs share the GPU. Requests are admitted in
+ * submission order when a lane is free and the device memory the pool would then hold
+ * (every lane's cached buffers plus the new request's estimate) stays within the pool's
+ * budget; idle lanes release their buffers when the head request does not fit. A
+ * request's race set is identical to the single-context result for the same trace. */
+typedef struct {
+  const gwcp_event* ev; /* n events, host memory or (ev_is_device = 1) device memory */
+  uint64_t n;
+  gwcp_geometry geo;
+  int32_t ev_is_device;
+  uint32_t reserved; /* must be 0 */
+} gwcp_trace_desc;
+
+typedef struct {
+  uint32_t lanes;         /* worker lanes; 0 = 16. Active lanes start equal to this */
+  uint32_t reserved0;     /* must be 0 */
+  uint64_t mem_budget;    /* device bytes the pool may hold; 0 = 85% of free memory at creation */
+  uint64_t race_capacity; /* per lane, as gwcp_options.race_capacity */
+  uint32_t reserved[4];   /* must be 0 */
+} gwcp_pool_options;
+
+typedef struct {
+  int32_t rc;               /* the request's result code (GWCP_OK, or as gwcp_compute_order /
+                               gwcp_report_races would return) */
+  uint32_t lane;            /* lane that ran it */
+  uint64_t n_races;         /* total races (also when the caller's cap was smaller) */
+  uint64_t first_bad_index; /* after GWCP_ERR_INVALID_TRACE */
+  double t_submit, t_admit, t_done; /* seconds on the pool's steady clock (gwcp_pool_now) */
+} gwcp_request_info;
+
+typedef struct gwcp_pool gwcp_pool; /* opaque; owns its lanes, threads and device memory */
+
+/* Creates a pool on `device`; opt may be NULL (defaults). */
+int gwcp_pool_create(gwcp_pool** out, int device, const gwcp_pool_options* opt);
+
+/* Queues one trace. The pool keeps the pointers: `t->ev` must stay valid and unchanged,
+ * and `out` (host memory, `cap` races, may be NULL when cap is 0) writable, until the
+ * request has been waited for. *ticket identifies the request. Never blocks on the GPU. */
+int gwcp_pool_submit(gwcp_pool* p, const gwcp_trace_desc* t, gwcp_race* out, uint64_t cap, uint64_t* ticket);
+
+/* Result of a request. block = 1 waits for it; block = 0 returns 1 if it is still queued
+ * or running. On completion returns 0 and fills *info (may be NULL); the ticket is then
+ * released. GWCP_ERR_ARGS for an unknown ticket. The request's own code is info->rc. */
+int gwcp_pool_wait(gwcp_pool* p, uint64_t ticket, int block, gwcp_request_info* info);
+
+/* Analyses n traces and waits for all: submits them longest first (so long traces do
+ * not end up alone at the tail), then fills n_races[i] and rc[i] (either may be NULL)
+ * and writes up to cap[i] races into out[i] (out may be NULL when every cap is 0).
+ * Returns 0, or the first nonzero rc[i]. */
+int gwcp_pool_run_batch(gwcp_pool* p, const gwcp_trace_desc* t, uint32_t n, gwcp_race* const* out,
+                        const uint64_t* cap, uint64_t* n_races, int32_t* rc);
+
+/* Number of lanes that take requests (1..lanes given at creation). */
+int gwcp_pool_set_active_lanes(gwcp_pool* p, uint32_t active);
+
+/* Autotuner: runs the n traces as one batch with each candidate number of active lanes
+ * (1, 2, 4, 8, 12, 16, 24, 32, up to the pool's lanes), keeps the fastest, and returns it
+ * in *best (seconds per candidate in secs[], up to 8 entries, may be NULL). Races are
+ * counted, not copied. */
+int gwcp_pool_autotune(gwcp_pool* p, const gwcp_trace_desc* t, uint32_t n, uint32_t* best, double* secs);
+
+/* Seconds on the pool's steady clock (the clock of gwcp_request_info). */
+double gwcp_pool_now(const gwcp_pool* p);
+
+/* Device bytes the pool's lanes hold now. */
+uint64_t gwcp_pool_device_bytes(gwcp_pool* p);
+
+/* Waits for every queued request, stops the threads, frees everything. Requests not yet
+ * waited for are dropped. */
+void gwcp_pool_destroy(gwcp_pool* p);
 
 /* Number of kernels this library has launched in this process, on any context. */
 uint64_t gwcp_launch_count(void);

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT, "libgwcp.so")
 SOURCES = ["gwcp_prims.cu", "gwcp_prep.cu", "gwcp_propagate.cu", "gwcp_check.cu", "gwcp_api.cu",
-           "gwcp_noalloc.cu", "gwcp_wide.cu"]
+           "gwcp_noalloc.cu", "gwcp_wide.cu", "gwcp_pool.cu", "gwcp_rank.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -1,6 +1,7 @@
 // C ABI of libgwcp (include/gwcp.h): context, trace loading, the analysis pipeline,
 // race reporting, test hooks.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -60,6 +61,9 @@ struct gwcp_ctx {
   uint64_t tile_cap_hint = 0;  // wide clocks: pool size that the last run needed
   cudaStream_t side = nullptr;  // runs the access grouping beside the propagation
   cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t sync_ev = nullptr;  // options.blocking_sync: host waits sleep on this event
+  std::vector<float> rank_theta;  // gwcp_set_ranker: the MLP's parameters (empty = off)
+  uint32_t n_chunks_timeline = 0; // chunks of the last check's timeline
   std::vector<float> prof_ms;
   std::vector<double> prof_bytes;
   std::vector<const char*> prof_names;
@@ -94,11 +98,19 @@ int cuda_rc() {
   return e == cudaSuccess ? GWCP_OK : GWCP_ERR_CUDA;
 }
 
+// waits for stream s: spinning (default) or, with options.blocking_sync, sleeping on an
+// event so that many host threads can wait at once without occupying cores
+cudaError_t wait_stream(gwcp_ctx* c, cudaStream_t s) {
+  if (!c->sync_ev) return cudaStreamSynchronize(s);
+  cudaError_t e = cudaEventRecord(c->sync_ev, s);
+  return e != cudaSuccess ? e : cudaEventSynchronize(c->sync_ev);
+}
+
 int read_status(gwcp_ctx* c, cudaStream_t s, const uint32_t* const* extra, int n_extra) {
   cudaMemcpyAsync(c->st_host, c->b.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
   for (int i = 0; i < n_extra; ++i)
     cudaMemcpyAsync(c->cnt_host + i, extra[i], sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return GWCP_ERR_CUDA;
+  if (wait_stream(c, s) != cudaSuccess) return GWCP_ERR_CUDA;
   return cuda_rc();
 }
 
@@ -310,10 +322,57 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   // on a side stream, with their own scratch, while the propagation runs on s
   uint32_t* side_tmp = get<uint32_t>(
       c, "side_tmp", std::max(radix_tmp_need(size_t(z.n_acc) + 1), scan_tmp_need(size_t(z.n_acc) * 4 + 2)) + 64, &oom);
+  const bool ranked = !c->rank_theta.empty() && !g.nT && z.n_acc;
+  RankIn rin{};
+  uint32_t *rk_tmp = nullptr, *rk_nloc = nullptr, *rk_val = nullptr, *rk_val2 = nullptr;
+  float *rk_feat = nullptr, *rk_score = nullptr, *rk_theta = nullptr;
+  uint64_t *rk_lockey = nullptr, *rk_key = nullptr, *rk_key2 = nullptr;
+  size_t rk_bits_words = size_t(z.N) / 32 + 2;
+  if (ranked) {
+    rk_tmp = get<uint32_t>(c, "rk_tmp", rank_tmp_words(z.n_acc), &oom);
+    rin.bits = get<uint32_t>(c, "rk_bits", rk_bits_words, &oom);
+    rk_feat = get<float>(c, "rk_feat", size_t(z.n_acc) * kRankFeatures, &oom);
+    rk_lockey = get<uint64_t>(c, "rk_lockey", z.n_acc, &oom);
+    rk_score = get<float>(c, "rk_score", z.n_acc, &oom);
+    rk_nloc = get<uint32_t>(c, "rk_nloc", 1, &oom);
+    rk_theta = get<float>(c, "rk_theta", kRankParams, &oom);
+    rk_key = get<uint64_t>(c, "rk_key", z.n_acc, &oom);
+    rk_key2 = get<uint64_t>(c, "rk_key2", z.n_acc, &oom);
+    rk_val = get<uint32_t>(c, "rk_val", z.n_acc, &oom);
+    rk_val2 = get<uint32_t>(c, "rk_val2", z.n_acc, &oom);
+  }
+  if (c->opt.timeline && !g.nT) {
+    b.chunk_ns = get<unsigned long long>(c, "chunk_ns", size_t(z.n_chunks) + 1, &oom);
+    b.chunk_races = get<uint32_t>(c, "chunk_races", size_t(z.n_chunks) + 1, &oom);
+  } else {
+    b.chunk_ns = nullptr;
+    b.chunk_races = nullptr;
+  }
   if (oom) return GWCP_ERR_OOM;
   cudaEventRecord(c->fork, s);
   cudaStreamWaitEvent(c->side, c->fork, 0);
   phaseH_sort(b, g, z, key_mask, side_tmp, c->side, c->prof);
+  if (ranked) {
+    // the ranker's order of the check: location runs by descending score
+    c->prof.begin("h_rank", double(z.n_acc) * (12 + 16 + 12 * 2 * 6 + 12), c->side);
+    cudaMemcpyAsync(rk_theta, c->rank_theta.data(), kRankParams * 4, cudaMemcpyHostToDevice, c->side);
+    rin.key = b.acc_key;
+    rin.idx = b.acc_idx;
+    rin.info = b.acc_info;
+    rin.n_acc = z.n_acc;
+    rin.incs_idx = b.incs_idx;
+    rin.n_incs = z.n_incs;
+    rin.acqrel = b.acqrel;
+    rin.n_acqrel = z.n_acqrel;
+    rin.bar = b.bar;
+    rin.n_bar = z.n_bar;
+    rank_features(rin, rk_tmp, rk_bits_words, rk_feat, rk_lockey, rk_nloc, side_tmp, c->side);
+    rank_scores(rk_theta, rk_feat, rk_nloc, z.n_acc, rk_score, c->side);
+    rank_order(rin, rk_tmp, rk_score, rk_key, rk_val, rk_key2, rk_val2, b.acc_key2, b.acc_idx2, side_tmp, c->side);
+    std::swap(b.acc_key, b.acc_key2);
+    std::swap(b.acc_idx, b.acc_idx2);
+    c->prof.end();
+  }
   if (g.nT)
     phaseI_wide_group(b, g, z, side_tmp, c->side, c->prof);
   else
@@ -326,10 +385,12 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   int prc = phaseG_propagate(b, g, z, s, c->prof);
   cudaStreamWaitEvent(s, c->join, 0);
   if (prc) return prc;
+  if (b.chunk_ns) stamp_now(&b.st->spare[5], s);  // the check's start, for the timeline
   if (g.nT)
     phaseI_wide_check(b, g, z, s, c->prof);
   else
     phaseI_check(b, g, z, s, c->prof);
+  c->n_chunks_timeline = b.chunk_ns ? z.n_chunks : 0;
   {
     int rc = read_status(c, s, nullptr, 0);
     if (rc) return rc;
@@ -342,6 +403,27 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   }
   if (code) return code;
   c->n_races = c->st_host->n_races;
+  if (c->n_races > z.race_cap && c->opt.race_capacity == 0) {
+    // automatic capacity: the race buffer was too small (a location read by many agents
+    // and written once races with each of them); grow it and run the check again, which
+    // writes nothing but the races and two counters
+    z.race_cap = c->n_races + c->n_races / 8;
+    b.races = get<uint64_t>(c, "races", z.race_cap, &oom);
+    b.races2 = get<uint64_t>(c, "races2", z.race_cap, &oom);
+    b.scan_tmp = get<uint32_t>(c, "scan_tmp", std::max(need2, radix_tmp_need(z.race_cap + 1) + 64), &oom);
+    if (oom) return GWCP_ERR_OOM;
+    const unsigned long long tests = c->st_host->partner_tests;
+    cudaMemsetAsync(&b.st->n_races, 0, sizeof(unsigned long long), s);
+    if (g.nT)
+      phaseI_wide_check(b, g, z, s, c->prof);
+    else
+      phaseI_check(b, g, z, s, c->prof);
+    int rc = read_status(c, s, nullptr, 0);
+    if (rc) return rc;
+    if (c->st_host->code) return c->st_host->code;
+    c->n_races = c->st_host->n_races;
+    c->st_host->partner_tests = tests;
+  }
   c->races_second = phaseI_sort_races(b, z, c->n_races, s, c->prof);
   c->counters[0] = z.n_acc;
   c->counters[1] = z.n_sync;
@@ -355,6 +437,30 @@ int run(gwcp_ctx* c, cudaStream_t s) {
 }
 
 }  // namespace
+
+namespace gwcp {
+// device bytes the context holds (its cached buffers and its copy of the trace)
+size_t ctx_device_bytes(const gwcp_ctx* c) {
+  size_t t = c->ev_own_cap;
+  for (auto& kv : c->allocs) t += kv.second.second;
+  return t;
+}
+// false when the last compute found more races than the device race buffer holds
+bool ctx_races_complete(const gwcp_ctx* c) { return c->n_races <= c->z.race_cap; }
+// releases the cached buffers (the next compute allocates them again); the caller makes
+// sure no work of this context is in flight
+void ctx_trim(gwcp_ctx* c) {
+  cudaSetDevice(c->device);
+  for (auto& kv : c->allocs)
+    if (kv.second.first) cudaFree(kv.second.first);
+  c->allocs.clear();
+  if (c->ev_own) cudaFree(c->ev_own);
+  c->ev_own = nullptr;
+  c->ev_own_cap = 0;
+  c->has_trace = false;
+  c->computed = false;
+}
+}  // namespace gwcp
 
 extern "C" {
 
@@ -374,7 +480,9 @@ int gwcp_create(gwcp_ctx** out, int device, const gwcp_options* opt) {
       cudaMallocHost(&c->cnt_host, 16 * sizeof(uint32_t)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
+      (c->opt.blocking_sync &&
+       cudaEventCreateWithFlags(&c->sync_ev, cudaEventDisableTiming | cudaEventBlockingSync) != cudaSuccess)) {
     gwcp_destroy(c);
     return GWCP_ERR_OOM;
   }
@@ -463,22 +571,22 @@ int gwcp_report_races(gwcp_ctx* c, gwcp_race* out, uint64_t cap, uint64_t* n_rac
   if (!c->computed) return GWCP_ERR_STATE;
   cudaSetDevice(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return GWCP_ERR_CUDA;
+  if (wait_stream(c, s) != cudaSuccess) return GWCP_ERR_CUDA;
   *n_races = 0;
   if (c->compute_rc) return c->compute_rc;
   *n_races = c->n_races;
   if (c->n_races > c->z.race_cap) return GWCP_ERR_CAPACITY;
   const uint64_t m = std::min<uint64_t>(cap, c->n_races);
   if (m) {
-    std::vector<uint64_t> tmp(m);
-    const uint64_t* src = c->races_second ? c->b.races2 : c->b.races;
-    if (cudaMemcpyAsync(tmp.data(), src, m * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+    // the sorted (later << 32 | earlier) words become gwcp_race records on the device; one
+    // copy brings them to the caller
+    bool oom = false;
+    gwcp_race* dev = get<gwcp_race>(c, "races_out", m, &oom);
+    if (oom) return GWCP_ERR_OOM;
+    races_to_records(c->races_second ? c->b.races2 : c->b.races, m, dev, s);
+    if (cudaMemcpyAsync(out, dev, m * sizeof(gwcp_race), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        wait_stream(c, s) != cudaSuccess)
       return GWCP_ERR_CUDA;
-    for (uint64_t i = 0; i < m; ++i) {
-      out[i].later = tmp[i] >> 32;
-      out[i].earlier = tmp[i] & 0xFFFFFFFFu;
-    }
   }
   // profile of this compute
   c->prof_ms.clear();
@@ -562,6 +670,125 @@ int gwcp_debug_clock(gwcp_ctx* c, uint64_t idx, int which, uint32_t* out) {
   return cuda_rc();
 }
 
+int gwcp_set_ranker(gwcp_ctx* c, const float* theta) {
+  if (!c) return GWCP_ERR_ARGS;
+  if (!theta) {
+    c->rank_theta.clear();
+    return GWCP_OK;
+  }
+  c->rank_theta.assign(theta, theta + kRankParams);
+  return GWCP_OK;
+}
+
+int gwcp_location_features(gwcp_ctx* c, float* feat, uint64_t* keys, uint64_t cap, uint64_t* n_loc, void* stream) {
+  if (!c || !n_loc || (cap && (!feat || !keys))) return GWCP_ERR_ARGS;
+  if (!c->computed || c->compute_rc) return GWCP_ERR_STATE;
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  *n_loc = 0;
+  const Sizes& z = c->z;
+  if (c->n == 0 || z.n_acc == 0) return GWCP_OK;
+  bool oom = false;
+  RankIn in{};
+  const size_t bits_words = size_t(z.N) / 32 + 2;
+  uint32_t* tmp = get<uint32_t>(c, "rk_tmp", rank_tmp_words(z.n_acc), &oom);
+  in.bits = get<uint32_t>(c, "rk_bits", bits_words, &oom);
+  float* f = get<float>(c, "rk_feat", size_t(z.n_acc) * kRankFeatures, &oom);
+  uint64_t* k = get<uint64_t>(c, "rk_lockey", z.n_acc, &oom);
+  uint32_t* nl = get<uint32_t>(c, "rk_nloc", 1, &oom);
+  uint32_t* stmp = get<uint32_t>(c, "side_tmp", scan_tmp_need(size_t(z.n_acc) + 1) + 64, &oom);
+  if (oom) return GWCP_ERR_OOM;
+  const Bufs& b = c->b;
+  in.key = b.acc_key;
+  in.idx = b.acc_idx;
+  in.info = b.acc_info;
+  in.n_acc = z.n_acc;
+  in.incs_idx = b.incs_idx;
+  in.n_incs = z.n_incs;
+  in.acqrel = b.acqrel;
+  in.n_acqrel = z.n_acqrel;
+  in.bar = b.bar;
+  in.n_bar = z.n_bar;
+  rank_features(in, tmp, bits_words, f, k, nl, stmp, s);
+  uint32_t n = 0;
+  if (cudaMemcpyAsync(&n, nl, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess || wait_stream(c, s) != cudaSuccess)
+    return GWCP_ERR_CUDA;
+  *n_loc = n;
+  const uint64_t m = std::min<uint64_t>(cap, n);
+  if (m && (cudaMemcpyAsync(feat, f, m * kRankFeatures * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(keys, k, m * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            wait_stream(c, s) != cudaSuccess))
+    return GWCP_ERR_CUDA;
+  return cap < n ? GWCP_ERR_CAPACITY : cuda_rc();
+}
+
+int gwcp_rank_scores(const float* theta, const float* feat, uint64_t n, float* scores, void* stream) {
+  if ((n && (!theta || !feat || !scores)) || n > kMaxEvents) return GWCP_ERR_ARGS;
+  if (!n) return GWCP_OK;
+  rank_scores(theta, feat, nullptr, uint32_t(n), scores, static_cast<cudaStream_t>(stream));
+  return cuda_rc();
+}
+
+int gwcp_rank_grad(const float* theta, const float* feat, const float* labels, uint64_t n, float pos_weight,
+                   float* grad, float* loss, void* stream) {
+  if (!theta || !grad || !loss || (n && (!feat || !labels)) || n > kMaxEvents) return GWCP_ERR_ARGS;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaMemsetAsync(grad, 0, kRankParams * 4, s);
+  cudaMemsetAsync(loss, 0, 4, s);
+  if (!n) return cuda_rc();
+  return rank_grad(theta, feat, labels, 0, uint32_t(n), pos_weight, 1.0f / float(n), grad, loss, s);
+}
+
+int gwcp_rank_train(float* theta, const float* feat, const float* labels, uint64_t n, const gwcp_train_options* o,
+                    float* epoch_loss, void* stream) {
+  if (!theta || !o || !o->epochs || !o->batch || (n && (!feat || !labels)) || n > kMaxEvents) return GWCP_ERR_ARGS;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* buf = nullptr;  // m, v, grad, per-epoch loss
+  const size_t words = 3 * size_t(kRankParams) + o->epochs;
+  if (cudaMalloc(&buf, words * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return GWCP_ERR_OOM;
+  }
+  float *m = buf, *v = buf + kRankParams, *g = buf + 2 * kRankParams, *ls = buf + 3 * kRankParams;
+  cudaMemsetAsync(buf, 0, words * 4, s);
+  int rc = GWCP_OK;
+  uint64_t t = 0;
+  const uint32_t nb = uint32_t((n + o->batch - 1) / o->batch);
+  for (uint32_t e = 0; e < o->epochs && !rc; ++e) {
+    for (uint32_t q = 0; q < nb && !rc; ++q) {
+      const uint32_t lo = q * o->batch, hi = uint32_t(std::min<uint64_t>(n, uint64_t(lo) + o->batch));
+      rc = rank_grad(theta, feat, labels, lo, hi, o->pos_weight, 1.0f / float(hi - lo) / float(nb), g, ls + e, s);
+      ++t;
+      const float c1 = float(1.0 / (1.0 - std::pow(0.9, double(t))));
+      const float c2 = float(1.0 / (1.0 - std::pow(0.999, double(t))));
+      rank_adam(theta, m, v, g, o->lr, c1, c2, s);
+    }
+  }
+  if (!rc && epoch_loss &&
+      (cudaMemcpyAsync(epoch_loss, ls, size_t(o->epochs) * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess))
+    rc = GWCP_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = GWCP_ERR_CUDA;
+  cudaFree(buf);
+  return rc ? rc : cuda_rc();
+}
+
+int gwcp_check_timeline(gwcp_ctx* c, uint64_t* start_ns, uint64_t* chunk_end_ns, uint32_t* chunk_races, uint64_t cap,
+                        uint64_t* n_chunks) {
+  if (!c || !n_chunks || !start_ns || (cap && (!chunk_end_ns || !chunk_races))) return GWCP_ERR_ARGS;
+  if (!c->computed || c->compute_rc) return GWCP_ERR_STATE;
+  cudaSetDevice(c->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) return GWCP_ERR_CUDA;
+  *n_chunks = c->n_chunks_timeline;
+  if (!c->n_chunks_timeline) return c->opt.timeline ? GWCP_OK : GWCP_ERR_STATE;
+  cudaMemcpy(start_ns, &c->b.st->spare[5], 8, cudaMemcpyDeviceToHost);
+  const uint64_t m = std::min<uint64_t>(cap, c->n_chunks_timeline);
+  if (m) {
+    cudaMemcpy(chunk_end_ns, c->b.chunk_ns, m * 8, cudaMemcpyDeviceToHost);
+    cudaMemcpy(chunk_races, c->b.chunk_races, m * 4, cudaMemcpyDeviceToHost);
+  }
+  return cap < c->n_chunks_timeline ? GWCP_ERR_CAPACITY : cuda_rc();
+}
+
 uint64_t gwcp_first_bad_index(const gwcp_ctx* c) { return c ? c->bad_index : ~0ull; }
 
 uint64_t gwcp_launch_count(void) { return gwcp::launch_count(); }
@@ -591,6 +818,7 @@ void gwcp_destroy(gwcp_ctx* c) {
   for (auto e : c->prof.pool) cudaEventDestroy(e);
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->join) cudaEventDestroy(c->join);
+  if (c->sync_ev) cudaEventDestroy(c->sync_ev);
   if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }

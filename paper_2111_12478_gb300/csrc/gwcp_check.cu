@@ -33,6 +33,8 @@ struct ChunkArgs {
   uint64_t race_cap;
   DevStatus* st;
   Geo g;
+  unsigned long long* chunk_ns;  // optional timeline: globaltimer at each chunk's end
+  uint32_t* chunk_races;         // and the races it found
 };
 
 __device__ __forceinline__ bool chunk_continues(const ChunkArgs& a, uint32_t c) {
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(CHK_WARPS * 32) k_check(ChunkArgs a) {
 #pragma unroll
   for (int j = 0; j < K; ++j) myblk[j] = (lane * K + j) / g.apb;
   uint64_t prev_key = a.key[lo];  // the chunk's first location continues the carried state
-  uint32_t tests = 0;
+  uint32_t tests = 0, found = 0;
   for (uint32_t b0 = lo; b0 < hi; b0 += 32) {
     const uint32_t p = b0 + lane;
     uint64_t k = ~0ull;
@@ -260,6 +262,7 @@ __global__ void __launch_bounds__(CHK_WARPS * 32) k_check(ChunkArgs a) {
         bal[j] = __ballot_sync(0xffffffffu, race[j]);
         cnt += __popc(bal[j]);
       }
+      found += cnt;
       if (cnt) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(&a.st->n_races, (unsigned long long)cnt);
@@ -278,6 +281,12 @@ __global__ void __launch_bounds__(CHK_WARPS * 32) k_check(ChunkArgs a) {
   }
   tests = __reduce_add_sync(0xffffffffu, tests);
   if (lane == 0 && tests) atomicAdd(&a.st->partner_tests, (unsigned long long)tests);
+  if (a.chunk_ns && lane == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    a.chunk_ns[c] = t;
+    a.chunk_races[c] = found;
+  }
 }
 
 inline uint32_t blocks(uint64_t n, uint32_t t) { return uint32_t((n + t - 1) / t); }
@@ -336,6 +345,8 @@ static ChunkArgs chunk_args(const Bufs& b, const Geo& g, const Sizes& z) {
   a.race_cap = z.race_cap;
   a.st = b.st;
   a.g = g;
+  a.chunk_ns = b.chunk_ns;
+  a.chunk_races = b.chunk_races;
   return a;
 }
 
@@ -367,6 +378,19 @@ void phaseI_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, P
     case 16: run_check<16>(a, s, p, per); break;
     case 32: run_check<32>(a, s, p, per); break;
   }
+}
+
+namespace {
+__global__ void k_race_records(const uint64_t* w, uint64_t n, gwcp_race* out) {
+  const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = gwcp_race{w[i] & 0xFFFFFFFFull, w[i] >> 32};
+}
+}  // namespace
+
+void races_to_records(const uint64_t* words, uint64_t n, gwcp_race* out, cudaStream_t s) {
+  if (!n) return;
+  k_race_records<<<unsigned((n + 255) / 256), 256, 0, s>>>(words, n, out);
+  count_launch();
 }
 
 bool phaseI_sort_races(const Bufs& b, const Sizes& z, uint64_t n_races, cudaStream_t s, Prof& p) {

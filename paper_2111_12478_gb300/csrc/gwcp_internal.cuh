@@ -172,6 +172,8 @@ struct Bufs {
   uint32_t* wc_grp_lo = nullptr;     // [n_groups + 1]
   uint32_t* wc_grp_agent = nullptr;  // [n_groups]
   uint32_t* wc_rc = nullptr;     // [4 * n_acc + 2] first group of each (run, class)
+  unsigned long long* chunk_ns = nullptr;  // [n_chunks] check timeline (options.timeline)
+  uint32_t* chunk_races = nullptr;         // [n_chunks]
   uint64_t* races = nullptr;    // [race_cap] (later << 32) | earlier
   uint64_t* races2 = nullptr;
   // scan scratch
@@ -333,6 +335,38 @@ void phaseH_sort(Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, uint3
 void phaseI_carry(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 void phaseI_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 bool phaseI_sort_races(const Bufs& b, const Sizes& z, uint64_t n_races, cudaStream_t s, Prof& p);
+// address ranker (gwcp_rank.cu): features of the locations of a sorted access stream, the
+// MLP's scores, and the ranked order of the stream (location runs by descending score)
+constexpr int kRankParams = 5313, kRankFeatures = 16;
+struct RankIn {
+  const uint64_t* key;   // [n_acc] sorted so that each location's accesses are one run, in trace order
+  const uint32_t* idx;   // [n_acc]
+  const AccInfo* info;
+  uint32_t n_acc;
+  const uint32_t* incs_idx;  // [n_incs] accesses inside a critical section
+  uint32_t n_incs;
+  uint32_t* bits;            // [N / 32 + 1] scratch bitmap
+  const uint32_t* acqrel;    // [n_acqrel] acquire/release trace indices, ascending
+  uint32_t n_acqrel;
+  const uint32_t* bar;       // [n_bar] barrier trace indices, ascending
+  uint32_t n_bar;
+};
+size_t rank_tmp_words(uint32_t n_acc);
+void rank_features(const RankIn& in, uint32_t* tmp, size_t bits_words, float* feat, uint64_t* loc_key,
+                   uint32_t* n_loc_dev, uint32_t* scan_tmp, cudaStream_t s);
+void rank_scores(const float* theta, const float* feat, const uint32_t* n_dev, uint32_t n_bound, float* score,
+                 cudaStream_t s);
+void rank_order(const RankIn& in, const uint32_t* tmp, const float* score, uint64_t* rkey, uint32_t* rval,
+                uint64_t* rkey2, uint32_t* rval2, uint64_t* key_out, uint32_t* idx_out, uint32_t* sort_tmp,
+                cudaStream_t s);
+int rank_grad(const float* theta, const float* feat, const float* y, uint32_t lo, uint32_t hi, float pos_weight,
+              float inv_b, float* grad, float* loss, cudaStream_t s);
+void rank_adam(float* theta, float* m, float* v, float* grad, float lr, float c1, float c2, cudaStream_t s);
+// sorted race words (later << 32 | earlier) -> gwcp_race records (gwcp_check.cu)
+void races_to_records(const uint64_t* words, uint64_t n, gwcp_race* out, cudaStream_t s);
+// check timeline: per chunk the globaltimer at its end and its race count (optional)
+void stamp_now(unsigned long long* at, cudaStream_t s);
+
 // wide clocks (gwcp_wide.cu): the walker over tile tables (after the plan is built), the
 // regrouping of accesses (beside the propagation) and the per-access partner check
 int phaseG_wide(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s);

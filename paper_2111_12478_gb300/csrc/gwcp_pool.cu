@@ -1,0 +1,435 @@
+// Pool of analysis lanes: batched and served analysis of many independent traces on one
+// GPU (include/gwcp.h, "batched and served analysis").
+//
+// A lane is a context with its own stream and a host thread. The analysis of one trace
+// synchronises its stream a few times to size buffers, and its clock propagation keeps
+// only as many SMs busy as the trace has blocks; lanes let other traces' kernels fill the
+// rest of the GPU meanwhile. Lane threads wait on blocking-sync events, so dozens of
+// lanes do not occupy host cores.
+//
+// Admission (continuous batching): requests wait in one FIFO queue; a free lane takes
+// the head when the device bytes the pool would then hold stay within the budget: the
+// cached buffers of every other lane (a busy lane counts at least its admitted
+// estimate) plus the larger of this lane's cache and the head's estimate. When the head
+// does not fit, idle lanes release their caches; when nothing is running, the head is
+// admitted anyway (it alone exceeds the budget). A request that still runs out of device
+// memory releases its lane's cache, waits until no other lane runs, and is retried once.
+// The estimate is a per-event byte count per clock-width class, raised whenever a
+// request grows a lane's cache.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "gwcp_internal.cuh"
+
+namespace gwcp {
+size_t ctx_device_bytes(const gwcp_ctx* c);
+void ctx_trim(gwcp_ctx* c);
+bool ctx_races_complete(const gwcp_ctx* c);
+}  // namespace gwcp
+
+using namespace gwcp;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  gwcp_trace_desc t{};
+  gwcp_race* out = nullptr;
+  uint64_t cap = 0;
+  bool count_only = false;  // autotuning: races are counted, not copied
+  uint64_t est = 0;         // device bytes the analysis is expected to need
+  gwcp_request_info info{};
+  bool done = false;
+};
+
+struct Lane {
+  gwcp_ctx* ctx = nullptr;
+  cudaStream_t s = nullptr;
+  std::thread th;
+  bool busy = false;      // running a request, or being trimmed
+  uint64_t bytes = 0;     // device bytes its context held after its last request
+  uint64_t reserve = 0;   // while busy: the admitted estimate
+};
+
+constexpr int kClasses = 16;  // clock-width classes: ceil(log2(W))
+int width_class(uint32_t W) {
+  int c = 0;
+  while ((1u << c) < W && c < kClasses - 1) ++c;
+  return c;
+}
+
+}  // namespace
+
+struct gwcp_pool {
+  int device = 0;
+  gwcp_pool_options opt{};
+  Clock::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, Request> reqs;  // node-based: references stay valid
+  uint64_t next_ticket = 1;
+  std::vector<Lane> lanes;
+  uint32_t active = 0;
+  uint64_t budget = 0;
+  bool stop = false;
+  bool exclusive = false;  // a lane retrying after running out of memory runs alone
+  double bpe[kClasses];    // estimated device bytes per event, by width class
+};
+
+namespace {
+
+double now_s(const gwcp_pool* p) { return std::chrono::duration<double>(Clock::now() - p->t0).count(); }
+
+uint64_t estimate(const gwcp_pool* p, const gwcp_trace_desc& t) {
+  const double b = p->bpe[width_class(t.geo.num_agents)] * double(t.n) + (t.ev_is_device ? 0.0 : 16.0 * t.n);
+  return uint64_t(b) + (uint64_t(64) << 20);
+}
+
+uint64_t held_by_others(const gwcp_pool* p, size_t i) {
+  uint64_t t = 0;
+  for (size_t j = 0; j < p->lanes.size(); ++j)
+    if (j != i) t += p->lanes[j].busy ? std::max(p->lanes[j].bytes, p->lanes[j].reserve) : p->lanes[j].bytes;
+  return t;
+}
+
+bool any_busy(const gwcp_pool* p) {
+  for (auto& l : p->lanes)
+    if (l.busy) return true;
+  return false;
+}
+
+// Releases the caches of idle lanes other than i (called with the lock held; drops it
+// while freeing). Returns true if any were released.
+bool trim_idle(gwcp_pool* p, size_t i, std::unique_lock<std::mutex>& lk) {
+  std::vector<size_t> victims;
+  for (size_t j = 0; j < p->lanes.size(); ++j)
+    if (j != i && !p->lanes[j].busy && p->lanes[j].bytes) {
+      p->lanes[j].busy = true;
+      victims.push_back(j);
+    }
+  if (victims.empty()) return false;
+  lk.unlock();
+  for (size_t j : victims) ctx_trim(p->lanes[j].ctx);
+  lk.lock();
+  for (size_t j : victims) {
+    p->lanes[j].bytes = 0;
+    p->lanes[j].busy = false;
+  }
+  p->cv_work.notify_all();
+  return true;
+}
+
+void run_request(gwcp_pool* p, Lane& L, Request& r) {
+  uint64_t nr = 0;
+  int rc = gwcp_load_trace(L.ctx, r.t.ev, r.t.n, &r.t.geo, r.t.ev_is_device, L.s);
+  if (!rc) rc = gwcp_compute_order(L.ctx, L.s);
+  if (!rc) {
+    rc = gwcp_report_races(L.ctx, r.count_only ? nullptr : r.out, r.count_only ? 0 : r.cap, &nr, L.s);
+    if (r.count_only && rc == GWCP_ERR_CAPACITY && ctx_races_complete(L.ctx)) rc = GWCP_OK;
+  } else if (rc != GWCP_ERR_ARGS && rc != GWCP_ERR_UNSUPPORTED) {
+    uint64_t dummy = 0;
+    gwcp_report_races(L.ctx, nullptr, 0, &dummy, L.s);  // waits for the stream
+  }
+  r.info.rc = rc;
+  r.info.n_races = nr;
+  r.info.first_bad_index = rc == GWCP_ERR_INVALID_TRACE ? gwcp_first_bad_index(L.ctx) : ~0ull;
+}
+
+void lane_main(gwcp_pool* p, size_t i) {
+  cudaSetDevice(p->device);
+  Lane& L = p->lanes[i];
+  std::unique_lock<std::mutex> lk(p->mu);
+  for (;;) {
+    // L.busy is set by another lane's thread while it releases this lane's cache
+    p->cv_work.wait(lk, [&] { return p->stop || (i < p->active && !p->exclusive && !L.busy && !p->queue.empty()); });
+    if (p->stop) break;
+    Request& head = p->reqs.at(p->queue.front());
+    const uint64_t need = std::max(L.bytes, head.est);
+    if (held_by_others(p, i) + need > p->budget) {
+      if (trim_idle(p, i, lk)) continue;
+      if (any_busy(p)) {  // wait for a running request to finish
+        p->cv_work.wait(lk);
+        continue;
+      }
+      // nothing runs and nothing is left to release: the request alone exceeds the budget
+    }
+    const uint64_t ticket = p->queue.front();
+    p->queue.pop_front();
+    Request& r = p->reqs.at(ticket);
+    L.busy = true;
+    L.reserve = need;
+    r.info.lane = uint32_t(i);
+    r.info.t_admit = now_s(p);
+    const uint64_t before = L.bytes;
+    lk.unlock();
+    run_request(p, L, r);
+    if (r.info.rc == GWCP_ERR_OOM) {  // release this lane's cache, run alone, retry once
+      ctx_trim(L.ctx);
+      lk.lock();
+      L.bytes = 0;
+      L.busy = false;
+      p->cv_work.notify_all();
+      p->cv_work.wait(lk, [&] { return !p->exclusive; });
+      p->exclusive = true;  // no lane admits a request until the retry is done
+      p->cv_work.wait(lk, [&] { return !any_busy(p); });
+      L.busy = true;
+      trim_idle(p, i, lk);
+      lk.unlock();
+      run_request(p, L, r);
+      lk.lock();
+      p->exclusive = false;
+      p->cv_work.notify_all();
+      lk.unlock();
+    }
+    const uint64_t after = ctx_device_bytes(L.ctx);
+    lk.lock();
+    if (after > before && r.t.n >= (1u << 18)) {  // a large request grew the cache: calibrate
+      const double fixed = double(uint64_t(64) << 20);
+      double& b = p->bpe[width_class(r.t.geo.num_agents)];
+      b = std::max(b, std::max(0.0, double(after) - fixed) / double(r.t.n) * 1.1);
+    }
+    L.bytes = after;
+    L.busy = false;
+    L.reserve = 0;
+    r.info.t_done = now_s(p);
+    r.done = true;
+    p->cv_done.notify_all();
+    p->cv_work.notify_all();
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int gwcp_pool_create(gwcp_pool** out, int device, const gwcp_pool_options* opt) {
+  if (!out) return GWCP_ERR_ARGS;
+  *out = nullptr;
+  gwcp_pool_options o{};
+  if (opt) o = *opt;
+  if (o.reserved0 || o.reserved[0] || o.reserved[1] || o.reserved[2] || o.reserved[3]) return GWCP_ERR_ARGS;
+  if (o.lanes == 0) o.lanes = 16;
+  if (o.lanes > 256) return GWCP_ERR_ARGS;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return GWCP_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return GWCP_ERR_CUDA;
+  auto* p = new gwcp_pool();
+  p->device = device;
+  p->opt = o;
+  p->t0 = Clock::now();
+  p->active = o.lanes;
+  for (int c = 0; c < kClasses; ++c) {
+    const double wp = double(std::min(1u << c, 1024u));
+    p->bpe[c] = 256.0 + 0.05 * 4.0 * wp;  // raised by observation
+  }
+  if (o.mem_budget) {
+    p->budget = o.mem_budget;
+  } else {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      delete p;
+      return GWCP_ERR_CUDA;
+    }
+    p->budget = uint64_t(double(fr) * 0.85);
+  }
+  p->lanes.resize(o.lanes);
+  gwcp_options co{};
+  co.race_capacity = o.race_capacity;
+  co.blocking_sync = 1;
+  for (auto& L : p->lanes) {
+    if (gwcp_create(&L.ctx, device, &co) != GWCP_OK ||
+        cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking) != cudaSuccess) {
+      for (auto& M : p->lanes) {
+        if (M.ctx) gwcp_destroy(M.ctx);
+        if (M.s) cudaStreamDestroy(M.s);
+      }
+      delete p;
+      return GWCP_ERR_OOM;
+    }
+  }
+  try {
+    for (size_t i = 0; i < p->lanes.size(); ++i) p->lanes[i].th = std::thread(lane_main, p, i);
+  } catch (...) {
+    {
+      std::lock_guard<std::mutex> lk(p->mu);
+      p->stop = true;
+    }
+    p->cv_work.notify_all();
+    for (auto& L : p->lanes)
+      if (L.th.joinable()) L.th.join();
+    for (auto& L : p->lanes) {
+      gwcp_destroy(L.ctx);
+      cudaStreamDestroy(L.s);
+    }
+    delete p;
+    return GWCP_ERR_OOM;
+  }
+  *out = p;
+  return GWCP_OK;
+}
+
+int gwcp_pool_submit(gwcp_pool* p, const gwcp_trace_desc* t, gwcp_race* out, uint64_t cap, uint64_t* ticket) {
+  if (!p || !t || !ticket || (cap && !out) || (!t->ev && t->n) || t->reserved) return GWCP_ERR_ARGS;
+  std::lock_guard<std::mutex> lk(p->mu);
+  const uint64_t id = p->next_ticket++;
+  Request& r = p->reqs[id];
+  r.t = *t;
+  r.out = out;
+  r.cap = cap;
+  r.est = estimate(p, *t);
+  r.info.t_submit = now_s(p);
+  r.info.lane = ~0u;
+  p->queue.push_back(id);
+  *ticket = id;
+  p->cv_work.notify_all();
+  return GWCP_OK;
+}
+
+int gwcp_pool_wait(gwcp_pool* p, uint64_t ticket, int block, gwcp_request_info* info) {
+  if (!p) return GWCP_ERR_ARGS;
+  std::unique_lock<std::mutex> lk(p->mu);
+  auto it = p->reqs.find(ticket);
+  if (it == p->reqs.end()) return GWCP_ERR_ARGS;
+  Request& r = it->second;
+  if (!r.done) {
+    if (!block) return 1;
+    p->cv_done.wait(lk, [&] { return r.done; });
+  }
+  if (info) *info = r.info;
+  p->reqs.erase(it);
+  return GWCP_OK;
+}
+
+int gwcp_pool_run_batch(gwcp_pool* p, const gwcp_trace_desc* t, uint32_t n, gwcp_race* const* out,
+                        const uint64_t* cap, uint64_t* n_races, int32_t* rcs) {
+  if (!p || (n && !t)) return GWCP_ERR_ARGS;
+  std::vector<uint32_t> order(n);
+  for (uint32_t i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return t[a].n > t[b].n; });
+  std::vector<uint64_t> tickets(n, 0);
+  int first = GWCP_OK;
+  for (uint32_t i : order) {
+    const uint64_t c = cap ? cap[i] : 0;
+    int rc = gwcp_pool_submit(p, &t[i], c && out ? out[i] : nullptr, out ? c : 0, &tickets[i]);
+    if (rc) {
+      tickets[i] = 0;
+      if (rcs) rcs[i] = rc;
+      if (n_races) n_races[i] = 0;
+      if (!first) first = rc;
+    }
+  }
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!tickets[i]) continue;
+    gwcp_request_info info{};
+    gwcp_pool_wait(p, tickets[i], 1, &info);
+    if (rcs) rcs[i] = info.rc;
+    if (n_races) n_races[i] = info.n_races;
+    if (info.rc && !first) first = info.rc;
+  }
+  return first;
+}
+
+int gwcp_pool_set_active_lanes(gwcp_pool* p, uint32_t active) {
+  if (!p || active == 0 || active > p->lanes.size()) return GWCP_ERR_ARGS;
+  {
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->active = active;
+  }
+  p->cv_work.notify_all();
+  return GWCP_OK;
+}
+
+int gwcp_pool_autotune(gwcp_pool* p, const gwcp_trace_desc* t, uint32_t n, uint32_t* best, double* secs) {
+  if (!p || !best || (n && !t)) return GWCP_ERR_ARGS;
+  static const uint32_t kCand[8] = {1, 2, 4, 8, 12, 16, 24, 32};
+  std::vector<uint32_t> order(n);
+  for (uint32_t i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return t[a].n > t[b].n; });
+  double best_s = 1e300;
+  uint32_t best_k = uint32_t(p->lanes.size());
+  for (int c = 0; c < 8; ++c) {
+    const uint32_t k = kCand[c];
+    if (k > p->lanes.size()) {
+      if (secs) secs[c] = 0;
+      continue;
+    }
+    gwcp_pool_set_active_lanes(p, k);
+    const double t0 = now_s(p);
+    std::vector<uint64_t> tickets;
+    int rc = GWCP_OK;
+    {
+      std::lock_guard<std::mutex> lk(p->mu);
+      for (uint32_t i : order) {
+        const uint64_t id = p->next_ticket++;
+        Request& r = p->reqs[id];
+        r.t = t[i];
+        r.count_only = true;
+        r.est = estimate(p, t[i]);
+        r.info.t_submit = now_s(p);
+        p->queue.push_back(id);
+        tickets.push_back(id);
+      }
+    }
+    p->cv_work.notify_all();
+    for (uint64_t id : tickets) {
+      gwcp_request_info info{};
+      gwcp_pool_wait(p, id, 1, &info);
+      if (info.rc && !rc) rc = info.rc;
+    }
+    const double dt = now_s(p) - t0;
+    if (secs) secs[c] = dt;
+    if (rc) {
+      gwcp_pool_set_active_lanes(p, best_k);
+      return rc;
+    }
+    if (dt < best_s) {
+      best_s = dt;
+      best_k = k;
+    }
+  }
+  gwcp_pool_set_active_lanes(p, best_k);
+  *best = best_k;
+  return GWCP_OK;
+}
+
+double gwcp_pool_now(const gwcp_pool* p) { return p ? now_s(p) : 0.0; }
+
+uint64_t gwcp_pool_device_bytes(gwcp_pool* p) {
+  if (!p) return 0;
+  std::lock_guard<std::mutex> lk(p->mu);
+  uint64_t t = 0;
+  for (auto& l : p->lanes) t += std::max(l.bytes, l.busy ? l.reserve : 0);
+  return t;
+}
+
+void gwcp_pool_destroy(gwcp_pool* p) {
+  if (!p) return;
+  {
+    std::unique_lock<std::mutex> lk(p->mu);
+    p->cv_done.wait(lk, [&] { return p->queue.empty() && !any_busy(p); });
+    p->stop = true;
+  }
+  p->cv_work.notify_all();
+  for (auto& L : p->lanes)
+    if (L.th.joinable()) L.th.join();
+  cudaSetDevice(p->device);
+  for (auto& L : p->lanes) {
+    if (L.ctx) gwcp_destroy(L.ctx);
+    if (L.s) cudaStreamDestroy(L.s);
+  }
+  delete p;
+}
+
+}  // extern "C"

@@ -20,7 +20,10 @@ ERRORS = {-1: "INVALID_TRACE", -2: "OOM", -3: "CUDA", -4: "CAPACITY", -5: "TIMEO
 ERR_INVALID_TRACE, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_STATE, ERR_ARGS, ERR_UNSUPPORTED = range(-1, -9, -1)
 EXPORTS = ("gwcp_create", "gwcp_load_trace", "gwcp_compute_order", "gwcp_report_races", "gwcp_debug_clock",
            "gwcp_first_bad_index", "gwcp_profile_get", "gwcp_counters", "gwcp_launch_count", "gwcp_destroy",
-           "gwcp_strerror", "gwcp_analyze_noalloc")
+           "gwcp_strerror", "gwcp_analyze_noalloc", "gwcp_pool_create", "gwcp_pool_submit", "gwcp_pool_wait",
+           "gwcp_pool_run_batch", "gwcp_pool_set_active_lanes", "gwcp_pool_autotune", "gwcp_pool_now",
+           "gwcp_pool_device_bytes", "gwcp_pool_destroy", "gwcp_set_ranker", "gwcp_location_features",
+           "gwcp_rank_scores", "gwcp_rank_grad", "gwcp_rank_train", "gwcp_check_timeline")
 
 
 class GwcpError(RuntimeError):
@@ -37,7 +40,31 @@ class Geometry(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("race_capacity", ctypes.c_uint64), ("profile", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 5)]
+                ("blocking_sync", ctypes.c_uint32), ("timeline", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+
+
+class TrainOptions(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_uint32), ("batch", ctypes.c_uint32), ("lr", ctypes.c_float),
+                ("pos_weight", ctypes.c_float), ("reserved", ctypes.c_uint32 * 4)]
+
+
+RANK_PARAMS, RANK_FEATURES = 5313, 16
+
+
+class TraceDesc(ctypes.Structure):
+    _fields_ = [("ev", ctypes.c_void_p), ("n", ctypes.c_uint64), ("geo", Geometry), ("ev_is_device", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class PoolOptions(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_uint32), ("reserved0", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
+                ("race_capacity", ctypes.c_uint64), ("reserved", ctypes.c_uint32 * 4)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("rc", ctypes.c_int32), ("lane", ctypes.c_uint32), ("n_races", ctypes.c_uint64),
+                ("first_bad_index", ctypes.c_uint64), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
 
 
 class Race(ctypes.Structure):
@@ -69,6 +96,33 @@ def load_library():
     L.gwcp_analyze_noalloc.argtypes = [vp, u64, ctypes.POINTER(Geometry), vp, u64, ctypes.POINTER(u64),
                                        ctypes.POINTER(u64), vp]
     L.gwcp_analyze_noalloc.restype = i32
+    L.gwcp_pool_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(PoolOptions)]
+    L.gwcp_pool_submit.argtypes = [vp, ctypes.POINTER(TraceDesc), vp, u64, ctypes.POINTER(u64)]
+    L.gwcp_pool_wait.argtypes = [vp, u64, i32, ctypes.POINTER(RequestInfo)]
+    L.gwcp_pool_run_batch.argtypes = [vp, ctypes.POINTER(TraceDesc), ctypes.c_uint32, ctypes.POINTER(vp),
+                                      ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_int32)]
+    L.gwcp_pool_set_active_lanes.argtypes = [vp, ctypes.c_uint32]
+    L.gwcp_pool_autotune.argtypes = [vp, ctypes.POINTER(TraceDesc), ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32),
+                                     ctypes.POINTER(ctypes.c_double)]
+    L.gwcp_pool_now.argtypes = [vp]
+    L.gwcp_pool_now.restype = ctypes.c_double
+    L.gwcp_pool_device_bytes.argtypes = [vp]
+    L.gwcp_pool_device_bytes.restype = u64
+    L.gwcp_pool_destroy.argtypes = [vp]
+    L.gwcp_pool_destroy.restype = None
+    for name in ("gwcp_pool_create", "gwcp_pool_submit", "gwcp_pool_wait", "gwcp_pool_run_batch",
+                 "gwcp_pool_set_active_lanes", "gwcp_pool_autotune"):
+        getattr(L, name).restype = i32
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.gwcp_set_ranker.argtypes = [vp, vp]
+    L.gwcp_location_features.argtypes = [vp, vp, vp, u64, ctypes.POINTER(u64), vp]
+    L.gwcp_rank_scores.argtypes = [vp, vp, u64, vp, vp]
+    L.gwcp_rank_grad.argtypes = [vp, vp, vp, u64, ctypes.c_float, vp, vp, vp]
+    L.gwcp_rank_train.argtypes = [vp, vp, vp, u64, ctypes.POINTER(TrainOptions), fp, vp]
+    L.gwcp_check_timeline.argtypes = [vp, ctypes.POINTER(u64), vp, vp, u64, ctypes.POINTER(u64)]
+    for name in ("gwcp_set_ranker", "gwcp_location_features", "gwcp_rank_scores", "gwcp_rank_grad",
+                 "gwcp_rank_train", "gwcp_check_timeline"):
+        getattr(L, name).restype = i32
     L.gwcp_launch_count.argtypes = []
     L.gwcp_launch_count.restype = u64
     L.gwcp_destroy.argtypes = [vp]
@@ -102,9 +156,9 @@ def _stream_ptr(stream) -> int | None:
 class Context:
     """One analysis context on one CUDA device (gwcp_ctx)."""
 
-    def __init__(self, device: int = 0, race_capacity: int = 0, profile: bool = False):
+    def __init__(self, device: int = 0, race_capacity: int = 0, profile: bool = False, timeline: bool = False):
         L = load_library()
-        opt = Options(race_capacity, int(profile))
+        opt = Options(race_capacity, int(profile), 0, int(timeline))
         h = ctypes.c_void_p()
         rc = L.gwcp_create(ctypes.byref(h), device, ctypes.byref(opt))
         if rc:
@@ -189,6 +243,52 @@ class Context:
             raise GwcpError(rc, "gwcp_debug_clock")
         return out
 
+    def set_ranker(self, theta):
+        """Checks locations in the ranker's order from the next compute_order on (theta: 5313
+        float32 parameters, or None to turn the ranker off)."""
+        if theta is None:
+            rc = self._L.gwcp_set_ranker(self._h, None)
+        else:
+            t = np.ascontiguousarray(theta, dtype=np.float32)
+            if t.size != RANK_PARAMS:
+                raise ValueError("theta must hold 5313 values")
+            self._theta = t
+            rc = self._L.gwcp_set_ranker(self._h, t.ctypes.data)
+        if rc:
+            raise GwcpError(rc, "gwcp_set_ranker")
+
+    def location_features(self, stream=None):
+        """Features of every accessed location of the last compute, in check order: (features
+        float32 CUDA tensor [n, 16], location keys int64 CUDA tensor [n] holding the u64 keys)."""
+        import torch
+
+        n = ctypes.c_uint64(0)
+        rc = self._L.gwcp_location_features(self._h, None, None, 0, ctypes.byref(n), _stream_ptr(stream))
+        if rc not in (GWCP_OK, ERR_CAPACITY):
+            raise GwcpError(rc, "gwcp_location_features")
+        feat = torch.zeros((max(n.value, 1), RANK_FEATURES), dtype=torch.float32, device="cuda")
+        keys = torch.zeros(max(n.value, 1), dtype=torch.int64, device="cuda")
+        rc = self._L.gwcp_location_features(self._h, feat.data_ptr(), keys.data_ptr(), n.value, ctypes.byref(n),
+                                            _stream_ptr(stream))
+        if rc:
+            raise GwcpError(rc, "gwcp_location_features")
+        return feat[: n.value], keys[: n.value]
+
+    def check_timeline(self):
+        """(start ns, per-chunk end ns uint64 array, per-chunk race counts uint32 array), chunks
+        in check order (needs timeline=True)."""
+        start, n = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        rc = self._L.gwcp_check_timeline(self._h, ctypes.byref(start), None, None, 0, ctypes.byref(n))
+        if rc not in (GWCP_OK, ERR_CAPACITY):
+            raise GwcpError(rc, "gwcp_check_timeline")
+        ends = np.zeros(max(n.value, 1), dtype=np.uint64)
+        races = np.zeros(max(n.value, 1), dtype=np.uint32)
+        rc = self._L.gwcp_check_timeline(self._h, ctypes.byref(start), ends.ctypes.data, races.ctypes.data, n.value,
+                                         ctypes.byref(n))
+        if rc:
+            raise GwcpError(rc, "gwcp_check_timeline")
+        return int(start.value), ends[: n.value], races[: n.value]
+
     def first_bad_index(self) -> int:
         return int(self._L.gwcp_first_bad_index(self._h))
 
@@ -206,6 +306,45 @@ class Context:
         keys = ("accesses", "sync_entries", "critical_sections", "in_section_accesses", "clock_versions",
                 "partner_tests", "loop_visits", "joins")
         return dict(zip(keys, [int(v) for v in a]))
+
+
+def rank_scores(theta, feat, stream=None):
+    """Scores of feature rows (CUDA tensors: theta [5313] float32, feat [n, 16] float32)."""
+    import torch
+
+    out = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
+    rc = load_library().gwcp_rank_scores(theta.data_ptr(), feat.data_ptr(), feat.shape[0], out.data_ptr(),
+                                         _stream_ptr(stream))
+    if rc:
+        raise GwcpError(rc, "gwcp_rank_scores")
+    return out
+
+
+def rank_grad(theta, feat, labels, pos_weight: float, stream=None):
+    """(gradient [5313] float32 CUDA tensor, loss) of the mean weighted logistic loss."""
+    import torch
+
+    g = torch.empty(RANK_PARAMS, dtype=torch.float32, device=feat.device)
+    loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+    rc = load_library().gwcp_rank_grad(theta.data_ptr(), feat.data_ptr(), labels.data_ptr(), feat.shape[0],
+                                       float(pos_weight), g.data_ptr(), loss.data_ptr(), _stream_ptr(stream))
+    if rc:
+        raise GwcpError(rc, "gwcp_rank_grad")
+    torch.cuda.synchronize(feat.device)
+    return g, float(loss.item())
+
+
+def rank_train(theta, feat, labels, epochs: int, batch: int, lr: float, pos_weight: float, stream=None):
+    """Adam training of theta (CUDA tensor, in place) on feature rows and 0/1 labels (CUDA
+    tensors, rows already shuffled); returns the mean batch loss of each epoch."""
+    losses = np.zeros(epochs, dtype=np.float32)
+    o = TrainOptions(epochs, batch, lr, pos_weight)
+    rc = load_library().gwcp_rank_train(theta.data_ptr(), feat.data_ptr(), labels.data_ptr(), feat.shape[0],
+                                        ctypes.byref(o), losses.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        _stream_ptr(stream))
+    if rc:
+        raise GwcpError(rc, "gwcp_rank_train")
+    return losses
 
 
 def analyze_noalloc(ev_dev_ptr: int, n: int, num_agents: int, agents_per_block: int, granularity: int,
@@ -227,3 +366,123 @@ def analyze(events, num_agents, agents_per_block, granularity, device: int = 0, 
         c.load_trace(events, num_agents, agents_per_block, granularity)
         c.compute_order()
         return c.report_races()
+
+
+def _trace_desc(events, geo) -> tuple[TraceDesc, object]:
+    """A gwcp_trace_desc for a host numpy trace or a torch CUDA tensor; returns it with the
+    object that must stay alive while the pool uses it."""
+    num_agents, agents_per_block, granularity = geo
+    g = Geometry(num_agents, agents_per_block, granularity, 0)
+    if isinstance(events, np.ndarray):
+        a = np.ascontiguousarray(events)
+        if a.dtype.itemsize != 16:
+            raise ValueError("events must be 16-byte records")
+        return TraceDesc(a.ctypes.data, len(a), g, 0, 0), a
+    if not events.is_cuda and not events.is_pinned():
+        raise ValueError("tensor must be on the GPU or in pinned host memory")
+    n = events.numel() * events.element_size() // 16
+    return TraceDesc(events.data_ptr(), n, g, 1 if events.is_cuda else 0, 0), events
+
+
+class Pool:
+    """Batched and served analysis (gwcp_pool): lanes of contexts that run independent
+    traces concurrently on one GPU, admitted by device memory."""
+
+    def __init__(self, device: int = 0, lanes: int = 16, mem_budget: int = 0, race_capacity: int = 0):
+        L = load_library()
+        opt = PoolOptions(lanes, 0, mem_budget, race_capacity)
+        h = ctypes.c_void_p()
+        rc = L.gwcp_pool_create(ctypes.byref(h), device, ctypes.byref(opt))
+        if rc:
+            raise GwcpError(rc, "gwcp_pool_create")
+        self._h, self._L = h, L
+        self._live = {}  # ticket -> (descriptor, trace keep-alive, output array)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.gwcp_pool_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def now(self) -> float:
+        return float(self._L.gwcp_pool_now(self._h))
+
+    def device_bytes(self) -> int:
+        return int(self._L.gwcp_pool_device_bytes(self._h))
+
+    def submit(self, events, geo, cap: int) -> int:
+        """Queues one trace (host numpy array, pinned host tensor or CUDA tensor); geo =
+        (num_agents, agents_per_block, granularity). Up to `cap` races are kept."""
+        d, keep = _trace_desc(events, geo)
+        out = np.zeros((max(cap, 1), 2), dtype=np.uint64)
+        t = ctypes.c_uint64(0)
+        rc = self._L.gwcp_pool_submit(self._h, ctypes.byref(d), out.ctypes.data_as(ctypes.c_void_p), cap,
+                                      ctypes.byref(t))
+        if rc:
+            raise GwcpError(rc, "gwcp_pool_submit")
+        self._live[t.value] = (d, keep, out, cap)
+        return int(t.value)
+
+    def wait(self, ticket: int, block: bool = True):
+        """Returns None if not finished (block=False), else (races (k, 2) uint64 array of
+        (earlier, later) truncated to the cap, RequestInfo)."""
+        info = RequestInfo()
+        rc = self._L.gwcp_pool_wait(self._h, ticket, int(block), ctypes.byref(info))
+        if rc == 1:
+            return None
+        if rc:
+            raise GwcpError(rc, "gwcp_pool_wait")
+        _, _, out, cap = self._live.pop(ticket)
+        return out[: min(info.n_races, cap)] if info.rc in (GWCP_OK, ERR_CAPACITY) else out[:0], info
+
+    def run_batch(self, traces, caps):
+        """traces: list of (events, geo); returns a list of (races, rc, n_races)."""
+        n = len(traces)
+        descs = (TraceDesc * n)()
+        keep = []
+        outs = []
+        for i, (ev, geo) in enumerate(traces):
+            d, k = _trace_desc(ev, geo)
+            descs[i] = d
+            keep.append(k)
+            outs.append(np.zeros((max(caps[i], 1), 2), dtype=np.uint64))
+        optr = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
+        cap = (ctypes.c_uint64 * n)(*caps)
+        nr = (ctypes.c_uint64 * n)()
+        rcs = (ctypes.c_int32 * n)()
+        self._L.gwcp_pool_run_batch(self._h, descs, n, optr, cap, nr, rcs)
+        return [(outs[i][: min(nr[i], caps[i])], int(rcs[i]), int(nr[i])) for i in range(n)]
+
+    def set_active_lanes(self, k: int):
+        rc = self._L.gwcp_pool_set_active_lanes(self._h, k)
+        if rc:
+            raise GwcpError(rc, "gwcp_pool_set_active_lanes")
+
+    def autotune(self, traces):
+        """Picks the number of active lanes that runs `traces` fastest; returns (best, {lanes: s})."""
+        n = len(traces)
+        descs = (TraceDesc * n)()
+        keep = []
+        for i, (ev, geo) in enumerate(traces):
+            d, k = _trace_desc(ev, geo)
+            descs[i] = d
+            keep.append(k)
+        best = ctypes.c_uint32(0)
+        secs = (ctypes.c_double * 8)()
+        rc = self._L.gwcp_pool_autotune(self._h, descs, n, ctypes.byref(best), secs)
+        if rc:
+            raise GwcpError(rc, "gwcp_pool_autotune")
+        cand = (1, 2, 4, 8, 12, 16, 24, 32)
+        return int(best.value), {c: float(secs[i]) for i, c in enumerate(cand) if secs[i] > 0}

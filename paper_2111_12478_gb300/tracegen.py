@@ -321,3 +321,79 @@ def generate(seed: int, n_events: int | None = None, workload: str | None = None
     geo = Geometry(int(p.num_blocks) * int(p.agents_per_block), int(p.agents_per_block), int(p.granularity))
     planted = np.nonzero(out["flags"] & FLAG_PLANTED)[0]
     return out, geo, planted
+
+
+# ---- many independent traces: the batched and the served workloads ----------------------
+
+BATCH_WIDTHS = (64, 128, 256, 512, 1024, 2048, 4096)
+
+
+def blocks_for_width(W: int) -> tuple[int, int]:
+    """(num_blocks, agents_per_block) for a W-warp trace: 8 warps (256 threads) per block up to
+    512 warps, then blocks of W/64 warps (at most 32, the widest block the tile-table clocks
+    take), so that no trace has more than 128 blocks."""
+    apb = min(32, max(8, W // 64))
+    return W // apb, apb
+
+
+def many_specs(seed: int, n_traces: int, n_min: int, n_max: int, widths=BATCH_WIDTHS) -> list[dict]:
+    """Per-trace generator parameters: lengths log-uniform over [n_min, n_max], widths drawn
+    uniformly from `widths` (warp granularity), the op/scope mix of the 64-warp 10M-event
+    workload, address ranks Zipf(1.1) over max(1000, n/10) ranks, a distinct seed per trace."""
+    rng = np.random.default_rng(seed)
+    lens = np.exp(rng.uniform(np.log(n_min), np.log(n_max), size=n_traces)).astype(np.int64)
+    ws = rng.choice(np.asarray(widths), size=n_traces)
+    base = WORKLOADS["8blk_64warp_10M"]
+    specs = []
+    for i in range(n_traces):
+        nb, apb = blocks_for_width(int(ws[i]))
+        p = dict(base)
+        p.update(n_events=int(lens[i]), num_blocks=nb, agents_per_block=apb, n_ranks=max(1000, int(lens[i]) // 10),
+                 seed=int(seed) * 100_003 + i)
+        specs.append(p)
+    return specs
+
+
+def generate_many(specs: list[dict], threads: int = 8) -> list[tuple[np.ndarray, Geometry]]:
+    """Runs the C++ generator for every spec (threads in parallel); returns (events, Geometry)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(p):
+        q = dict(p)
+        s = q.pop("seed")
+        ev, geo, _ = generate(s, **q)
+        return ev, geo
+
+    with ThreadPoolExecutor(max(1, threads)) as ex:
+        return list(ex.map(one, specs))
+
+
+# The batched workload: 512 independent traces, 10k-5M events each, 64-4096 warps.
+BATCH_WORKLOAD = dict(n_traces=512, n_min=10_000, n_max=5_000_000)
+# The served workload: traces of 10k-20M events, 64-4096 warps, arriving as a Poisson
+# process at 200 traces/s.
+SERVE_WORKLOAD = dict(rate=200.0, n_min=10_000, n_max=20_000_000)
+
+
+def serve_base_specs(seed: int, n_max: int, widths=BATCH_WIDTHS) -> list[dict]:
+    """One n_max-event trace per width class; a served request of n events is the first n
+    events of its class's trace (a prefix of a well-formed trace is well-formed)."""
+    base = WORKLOADS["8blk_64warp_10M"]
+    specs = []
+    for j, W in enumerate(widths):
+        nb, apb = blocks_for_width(int(W))
+        p = dict(base)
+        p.update(n_events=int(n_max), num_blocks=nb, agents_per_block=apb, n_ranks=max(1000, int(n_max) // 10),
+                 seed=int(seed) * 7_919 + j)
+        specs.append(p)
+    return specs
+
+
+def serve_requests(seed: int, n_requests: int, rate: float, n_min: int, n_max: int, n_widths: int = len(BATCH_WIDTHS)):
+    """Arrival times of a Poisson process of `rate` requests/s (seconds from the start), each
+    request's width class (uniform) and length (log-uniform over [n_min, n_max])."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    widths = rng.integers(0, n_widths, size=n_requests)
+    lens = np.exp(rng.uniform(np.log(n_min), np.log(n_max), size=n_requests)).astype(np.int64)
+    return arrivals, widths, lens

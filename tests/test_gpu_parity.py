@@ -218,6 +218,30 @@ def test_capacity_and_determinism(ctx):
         assert small.race_count() == len(a)
 
 
+def test_more_races_than_events(ctx):
+    # no synchronisation: 1024 agents each read a location, then agents 0 and 1 write it.
+    # The first write races with the 1023 other readers, the second with the 1022 readers
+    # other than agents 0 and 1 and with the first write: 2046 races per 1026 events,
+    # more than the automatic race buffer's first size (max(2^20, n))
+    W, n_loc = 1024, 600
+    per = W + 2
+    ev = np.zeros(n_loc * per, dtype=TG.EVENT_DTYPE)
+    for x in range(n_loc):
+        o = x * per
+        ev["agent"][o:o + W] = np.arange(W)
+        ev["op"][o:o + W] = READ
+        ev["agent"][o + W], ev["agent"][o + W + 1] = 0, 1
+        ev["op"][o + W:o + W + 2] = WRITE
+        ev["addr"][o:o + per] = 64 * (x + 1)
+    geo = TG.Geometry(W, 32, WARP_GRAN)
+    got = gpu_races(ctx, ev, geo)
+    assert len(got) == n_loc * 2046 > max(1 << 20, len(ev))
+    w1 = np.arange(n_loc) * per + W
+    first = got[np.isin(got[:, 1], w1)]
+    assert len(first) == n_loc * 1023 and set(np.unique(first[:, 1]).tolist()) == set(w1.tolist())
+    assert np.array_equal(got, O.run(ev, *geo.astuple()).races)
+
+
 def test_device_input_and_stream(ctx):
     import torch
 

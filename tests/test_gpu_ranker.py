@@ -1,0 +1,147 @@
+"""The address ranker on the GPU, through the C ABI, against the ranker oracle: features of
+every location, the BF16 MLP's scores, its loss gradient and an Adam step; a ranked check
+gives the same race set; and a network trained on oracle labels puts races earlier in
+the check than the location order does."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import ranker as R
+from paper_2111_12478_gb300 import tracegen as TG
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2111_12478_gb300 import gwcp, ranker
+
+    return torch, gwcp, ranker
+
+
+def gpu_features(gwcp, ev, geo):
+    with gwcp.Context(0) as c:
+        c.load_trace(ev, *geo.astuple())
+        c.compute_order()
+        f, k = c.location_features()
+        return f.cpu().numpy(), k.cpu().numpy().view(np.uint64)
+
+
+def traces():
+    out = [TG.random_small(s, fam, n_events=400, num_agents=16, agents_per_block=4, n_locks=3, n_keys=7)
+           for s, fam in enumerate(("mixed", "barriers", "dev_locks", "nosync"))]
+    out.append(TG.generate(3, n_events=60_000, workload="8blk_64warp_10M")[:2])
+    out.append(TG.generate(2, workload="tiny_1blk_64thr_10k")[:2])
+    return out
+
+
+def test_features_match_oracle(env):
+    torch, gwcp, _ = env
+    for ev, geo in traces():
+        f, k = gpu_features(gwcp, ev, geo)
+        kw, fw = R.features(ev, geo.agents_per_block)
+        assert np.array_equal(k, kw)
+        np.testing.assert_allclose(f, fw, rtol=2e-6, atol=2e-6)
+
+
+def _rows(seed, n):
+    rng = np.random.default_rng(seed)
+    x = np.abs(rng.normal(0, 1.5, (n, R.N_FEAT))).astype(np.float32)
+    y = (rng.random(n) < 0.2).astype(np.float32)
+    th = (rng.normal(0, 0.25, R.N_PARAMS)).astype(np.float32)
+    return th, x, y
+
+
+def test_scores_match_oracle(env):
+    torch, gwcp, _ = env
+    th, x, _ = _rows(1, 5000 + 13)  # a ragged last tile of 16 rows
+    got = gwcp.rank_scores(torch.from_numpy(th).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
+    want, _ = R.forward(th, x)
+    err = np.abs(got - want) / (1 + np.abs(want))
+    # float accumulation order differs; a rare flip of one bfloat16 rounding of h1 moves a
+    # score by at most one bfloat16 step of one hidden unit's contribution
+    assert np.quantile(err, 0.99) < 1e-5 and err.max() < 2e-2
+
+
+def test_grad_matches_oracle(env):
+    torch, gwcp, _ = env
+    th, x, y = _rows(2, 3000)
+    g, loss = gwcp.rank_grad(torch.from_numpy(th).cuda(), torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), 4.0)
+    g = g.cpu().numpy().astype(np.float64)
+    gw = R.grad(th, x, y, 4.0)
+    assert abs(loss - R.loss(th, x, y, 4.0)) < 1e-4 * (1 + abs(loss))
+    assert np.linalg.norm(g - gw) <= 2e-3 * np.linalg.norm(gw)
+    assert np.abs(g - gw).max() <= 2e-3 * np.abs(gw).max()
+
+
+def test_adam_steps_match_oracle(env):
+    torch, gwcp, _ = env
+    th, x, y = _rows(3, 2048)
+    t = torch.from_numpy(th.copy()).cuda()
+    gwcp.rank_train(t, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), epochs=2, batch=2048, lr=1e-3,
+                    pos_weight=3.0)
+    want, m, v = th.astype(np.float64), np.zeros(R.N_PARAMS), np.zeros(R.N_PARAMS)
+    for step in (1, 2):
+        want, m, v = R.adam_step(want, m, v, R.grad(want, x, y, 3.0), step, 1e-3)
+    got = t.cpu().numpy()
+    # each step moves a parameter by at most about lr; gradients agree to ~1e-3
+    assert np.abs(got - want).max() < 2e-4
+
+
+def test_ranked_check_same_races(env):
+    torch, gwcp, ranker = env
+    for ev, geo in traces():
+        want = O.run(ev, *geo.astuple()).races
+        with gwcp.Context(0, timeline=True) as c:
+            c.set_ranker(ranker.init_theta(9))
+            c.load_trace(ev, *geo.astuple())
+            c.compute_order()
+            got = c.report_races()
+            start, ends, per = c.check_timeline()
+            assert np.array_equal(got, want)
+            assert int(per.sum()) == len(want) and len(ends) > 0 and (ends >= start).all()
+
+
+def _train_set(gwcp, seeds, n):
+    X, Y = [], []
+    for s in seeds:
+        ev, geo, _ = TG.generate(s, n_events=n, workload="8blk_64warp_10M")
+        f, k = gpu_features(gwcp, ev, geo)
+        races = O.run(ev, *geo.astuple()).races
+        X.append(f)
+        Y.append(R.labels(ev, geo.agents_per_block, races, k).astype(np.float32))
+    return np.concatenate(X), np.concatenate(Y)
+
+
+def test_trained_ranker_surfaces_races_earlier(env):
+    torch, gwcp, ranker = env
+    X, Y = _train_set(gwcp, (41, 42, 43), 300_000)
+    perm = np.random.default_rng(0).permutation(len(X))
+    X, Y = X[perm], Y[perm]
+    pw = float(min(50.0, (len(Y) - Y.sum()) / max(Y.sum(), 1)))
+    th = torch.from_numpy(ranker.init_theta(1)).cuda()
+    losses = gwcp.rank_train(th, torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), epochs=40, batch=2048,
+                             lr=3e-3, pos_weight=pw)
+    assert losses[-1] < 0.7 * losses[0]
+    # held-out trace: the share of its racy locations among the first 10% of the locations
+    # the check visits, in location order and in the trained ranker's order
+    ev, geo, _ = TG.generate(44, n_events=300_000, workload="8blk_64warp_10M")
+    want = O.run(ev, *geo.astuple()).races
+    recall = {}
+    for name, theta in (("location order", None), ("ranked", th.cpu().numpy())):
+        with gwcp.Context(0, timeline=True) as c:
+            c.set_ranker(theta)
+            c.load_trace(ev, *geo.astuple())
+            c.compute_order()
+            assert np.array_equal(c.report_races(), want)
+            _, keys = c.location_features()  # in check order
+            lab = R.labels(ev, geo.agents_per_block, want, keys.cpu().numpy().view(np.uint64))
+            k = max(1, len(lab) // 10)
+            recall[name] = float(lab[:k].sum() / lab.sum())
+    assert recall["ranked"] >= 0.5 and recall["ranked"] >= recall["location order"] + 0.3, recall
