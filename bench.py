@@ -31,6 +31,13 @@ METRIC = "trace events/sec, race set bit-exact; batched/served vs plain; p50/p99
 SEED = 1
 
 
+T0 = time.perf_counter()
+
+
+def log(msg):
+    print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -240,6 +247,87 @@ def bench_served(args, local, torch, gwcp, tracegen, np, lanes):
             "inputs": "pinned host memory; H2D copy and race D2H inside each request"}
 
 
+def bench_ranker(args, local, torch, gwcp, np, ev, geo, dev):
+    """The trained address ranker on the main workload: the check's timeline (time from its
+    start to the first race and to 50% / 90% / all races) and the share of racy locations
+    among the first 10% of locations checked, in location order and in ranked order. The
+    ranker's features, scores and re-sort run beside the propagation; the race sets of the
+    two orders must be identical."""
+    from paper_2111_12478_gb300 import ranker
+
+    theta = ranker.load_weights()
+    if theta is None:
+        return {"unavailable": "no trained weights (tests/train_ranker.py writes them)"}
+    out, sets = {}, {}
+    for name, t in (("location_order", None), ("ranked", theta)):
+        ctx = gwcp.Context(local, timeline=True, profile=True)
+        ctx.set_ranker(t)
+        ctx.load_trace(dev, *geo.astuple())
+        summ, steps = [], []
+        for rep in range(args.warmup + 5):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.compute_order()
+            n = ctx.race_count()
+            dt = time.perf_counter() - t0
+            if rep >= args.warmup:
+                steps.append(dt)
+                summ.append(ranker.timeline_summary(*ctx.check_timeline()))
+        races = ctx.report_races()
+        _, keys = ctx.location_features()
+        sets[name] = races
+        prof = {k: round(ms, 4) for k, ms, _ in ctx.profile()}
+        ctx.close()
+        med = {k: float(np.median([s_[k] for s_ in summ])) for k in summ[0] if k.endswith("_us")}
+        out[name] = {**med, "races_in_first_10pct_chunks": summ[-1]["races_in_first_10pct_chunks"],
+                     "racy_location_recall_first_10pct": ranker.racy_location_recall(
+                         ev, geo.agents_per_block, races, keys.cpu().numpy().view(np.uint64), 0.1),
+                     "ms_per_step": 1e3 * float(np.median(steps)), "h_rank_ms": prof.get("h_rank"),
+                     "i_check_ms": prof.get("i_check"), "n_races": int(n)}
+    out["race_sets_identical"] = bool(np.array_equal(sets["location_order"], sets["ranked"]))
+    out["note"] = "times in microseconds from the check's start (globaltimer); ranker: BF16 MLP 16-64-64-1"
+    return out
+
+
+def bench_configs(args, local, torch, gwcp, tracegen, np):
+    """The other single-trace workloads, one entry each: events/s of the whole analysis over
+    the device-resident trace (CUDA events on the launching stream; inputs larger than L2
+    for the 200M-event trace, the tiny trace sits in L2) and the race set against the
+    oracle (whole trace, or the races whose later access lies in the first 1M events)."""
+    out = {}
+    for name, warm, steps, prefix in (("tiny_1blk_64thr_10k", 3, 20, 0), ("256blk_8192warp_200M", 1, 2, 1_000_000)):
+        ev, geo, _ = tracegen.generate(SEED, workload=name)
+        dev = torch.from_numpy(ev.view(np.uint8)).to(f"cuda:{local}")
+        s = torch.cuda.Stream(device=local)
+        ctx = gwcp.Context(local)
+        ctx.load_trace(dev, *geo.astuple(), stream=s)
+        for _ in range(warm):
+            ctx.compute_order(stream=s)
+        ms = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            ctx.compute_order(stream=s)
+            e1.record(s)
+            ctx.race_count(stream=s)
+            ms.append(e0.elapsed_time(e1))
+        races = ctx.report_races(stream=s)
+        ctx.close()
+        entry = {"events": int(len(ev)), "agents": geo.num_agents, "value": len(ev) / (statistics.median(ms) / 1e3),
+                 "unit": "events/s", "ms_per_step": statistics.median(ms), "steps": steps, "warmup": warm,
+                 "n_races": int(len(races))}
+        if not args.no_cpu_baseline:
+            from oracle import oracle
+
+            k = prefix or len(ev)
+            want = oracle.run(ev[:k], *geo.astuple()).races
+            entry["race_set_vs_oracle"] = {"events_checked": k, "identical": bool(
+                np.array_equal(want, races[races[:, 1] < k]))}
+        out[name] = entry
+        del dev, ev
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, on the host cores, on a bounded
     prefix of the same workload per step (rank 0 only)."""
@@ -282,6 +370,8 @@ def main():
     ap.add_argument("--events", type=int, default=0, help="analyse only this many events of the workload "
                     "(profiling runs); 0 = the full workload")
     ap.add_argument("--workload", default=WORKLOAD, help="a trace shape of tracegen.WORKLOADS")
+    ap.add_argument("--no-ranker", action="store_true", help="skip the ranked-check measurement")
+    ap.add_argument("--no-configs", action="store_true", help="skip the tiny and 8192-warp workloads")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (512-trace) measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson arrivals) measurement")
     ap.add_argument("--batch-steps", type=int, default=3)
@@ -316,9 +406,8 @@ def main():
         dist.barrier()
     from paper_2111_12478_gb300 import gwcp, tracegen
 
-    ev, geo, planted = tracegen.generate(SEED + rank, workload=args.workload)
-    if args.events:
-        ev = ev[: args.events]  # a prefix of a well-formed trace is well-formed
+    # --events: a shorter trace of the same workload shape (profiling runs)
+    ev, geo, planted = tracegen.generate(SEED + rank, workload=args.workload, n_events=args.events or None)
     n_ev = len(ev)
     stream = torch.cuda.Stream(device=local)
     dev = torch.from_numpy(ev.view(np.uint8).copy()).to(f"cuda:{local}")
@@ -444,17 +533,26 @@ def main():
             "race_set_bit_exact": exact, "n_races": int(n_races),
             "gpu_launches": int(launches), "clocks": clk,
         }
+    log(f"main section done ({time.perf_counter() - T0:.1f} s)")
+    if rank == 0 and not args.no_ranker:
+        result["ranker"] = bench_ranker(args, local, torch, gwcp, np, ev, geo, dev)
+        log(f"ranker section done ({time.perf_counter() - T0:.1f} s)")
     ctx.close()
     ctx_e2e.close()
     del dev, pinned
+    if rank == 0 and not args.no_configs:
+        result["configs"] = bench_configs(args, local, torch, gwcp, tracegen, np)
+        log(f"configs section done ({time.perf_counter() - T0:.1f} s)")
     if not args.no_batched:
         b = bench_batched(args, local, torch, gwcp, tracegen, np)
         if result is not None:
             result["batched"] = b
+        log(f"batched section done ({time.perf_counter() - T0:.1f} s)")
     if not args.no_served:
         v = bench_served(args, local, torch, gwcp, tracegen, np, b["lanes"] if not args.no_batched else 16)
         if result is not None:
             result["served"] = v
+        log(f"served section done ({time.perf_counter() - T0:.1f} s)")
     if dist:
         dist.barrier()
         dist.destroy_process_group()

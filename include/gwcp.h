@@ -97,7 +97,11 @@ typedef struct {
                              spinning (for many contexts driven by many host threads) */
   uint32_t timeline;      /* 1 = the check records when each of its chunks ends and how many
                              races it found (gwcp_check_timeline) */
-  uint32_t reserved[3];
+  uint32_t hb_only;       /* 1 = the paper's happens-before baseline: accesses are checked
+                             against H_t (scoped happens-before of Algorithm 1's H clocks)
+                             instead of C_t; C_t <= H_t, so it reports a subset of the
+                             GWCP races (the predictable races are the difference) */
+  uint32_t reserved[2];
 } gwcp_options;
 
 typedef struct gwcp_ctx gwcp_ctx; /* opaque; owns all device memory it allocates */
@@ -146,6 +150,18 @@ int gwcp_report_races(gwcp_ctx* ctx, gwcp_race* out, uint64_t cap, uint64_t* n_r
  * joins; for a release: the clock it published, before its increment); which = 1: H_t
  * published by a release (GWCP_ERR_UNSUPPORTED for other events). Synchronous. */
 int gwcp_debug_clock(gwcp_ctx* ctx, uint64_t event_idx, int which, uint32_t* out_W);
+
+/* How clocks are held (the representation only; results are identical):
+ * GWCP_CLOCKS_DENSE: every clock a row of W words, held in registers by the walker
+ *   (num_agents <= 1024; wider traces still use tiles);
+ * GWCP_CLOCKS_TILES: clocks as tables of copy-on-write 256-entry tiles (warp granularity,
+ *   agents_per_block <= 32, num_agents <= 8192);
+ * GWCP_CLOCKS_AUTO (default): tiles from 512 agents on where the trace allows them, else
+ *   dense (the two cross near 512 agents on GB300).
+ * Applies from the next gwcp_load_trace, which returns GWCP_ERR_UNSUPPORTED when the trace
+ * does not allow the requested representation. */
+enum { GWCP_CLOCKS_AUTO = 0, GWCP_CLOCKS_DENSE = 1, GWCP_CLOCKS_TILES = 2 };
+int gwcp_set_clock_mode(gwcp_ctx* ctx, uint32_t mode);
 
 /* Index of the first event that violates W1-W4 after GWCP_ERR_INVALID_TRACE. */
 uint64_t gwcp_first_bad_index(const gwcp_ctx* ctx);
@@ -304,11 +320,18 @@ int gwcp_pool_run_batch(gwcp_pool* p, const gwcp_trace_desc* t, uint32_t n, gwcp
 /* Number of lanes that take requests (1..lanes given at creation). */
 int gwcp_pool_set_active_lanes(gwcp_pool* p, uint32_t active);
 
-/* Autotuner: runs the n traces as one batch with each candidate number of active lanes
- * (1, 2, 4, 8, 12, 16, 24, 32, up to the pool's lanes), keeps the fastest, and returns it
- * in *best (seconds per candidate in secs[], up to 8 entries, may be NULL). Races are
- * counted, not copied. */
+/* Autotuner. First, for every clock-width class (ceil(log2(num_agents))) among the n
+ * traces whose traces all allow both clock representations (gwcp_set_clock_mode), times
+ * them one after another with dense and with tile clocks and keeps the faster for that
+ * class (gwcp_pool_clock_modes). Then runs the n traces as one batch with each candidate
+ * number of active lanes (1, 2, 4, 8, 12, 16, 24, 32, up to the pool's lanes), keeps the
+ * fastest and returns it in *best (seconds per candidate in secs[], up to 8 entries, may
+ * be NULL). Races are counted, not copied. */
 int gwcp_pool_autotune(gwcp_pool* p, const gwcp_trace_desc* t, uint32_t n, uint32_t* best, double* secs);
+
+/* The clock mode the pool uses per width class c = ceil(log2(num_agents)), c < 16
+ * (GWCP_CLOCKS_AUTO where the autotuner has not chosen). */
+int gwcp_pool_clock_modes(const gwcp_pool* p, uint32_t* modes16);
 
 /* Seconds on the pool's steady clock (the clock of gwcp_request_info). */
 double gwcp_pool_now(const gwcp_pool* p);

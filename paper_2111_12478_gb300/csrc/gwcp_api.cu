@@ -63,6 +63,7 @@ struct gwcp_ctx {
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t sync_ev = nullptr;  // options.blocking_sync: host waits sleep on this event
   std::vector<float> rank_theta;  // gwcp_set_ranker: the MLP's parameters (empty = off)
+  uint32_t clock_mode = GWCP_CLOCKS_AUTO;  // gwcp_set_clock_mode
   uint32_t n_chunks_timeline = 0; // chunks of the last check's timeline
   std::vector<float> prof_ms;
   std::vector<double> prof_bytes;
@@ -121,6 +122,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   bool oom = false;
   z = Sizes{};
   z.N = c->n;
+  z.hb_only = c->opt.hb_only != 0;
   z.TA = g.Wp <= 256 ? 2048 : 8192;
   while (uint64_t(g.W) * ((z.N + z.TA - 1) / z.TA) > (1ull << 26)) z.TA <<= 1;  // bounded agent histogram
   z.ntA = uint32_t((z.N + z.TA - 1) / z.TA);
@@ -498,9 +500,13 @@ int gwcp_load_trace(gwcp_ctx* c, const gwcp_event* ev, uint64_t n, const gwcp_ge
     return GWCP_ERR_ARGS;
   // clocks of more than kMaxAgents entries are tile tables: warp granularity, and a block
   // of agents fits one CTA of walkers
-  if (geo->num_agents > kMaxAgents &&
-      (geo->num_agents > kMaxAgentsWide || geo->granularity != GWCP_GRAN_WARP || geo->agents_per_block > 32))
-    return GWCP_ERR_UNSUPPORTED;
+  const bool tiles_ok =
+      geo->num_agents <= kMaxAgentsWide && geo->granularity == GWCP_GRAN_WARP && geo->agents_per_block <= 32;
+  if (geo->num_agents > kMaxAgents && !tiles_ok) return GWCP_ERR_UNSUPPORTED;
+  if (c->clock_mode == GWCP_CLOCKS_TILES && !tiles_ok) return GWCP_ERR_UNSUPPORTED;
+  // automatic: tiles from kTilesFromAgents agents on (measured faster from there on GB300)
+  const bool tiles = geo->num_agents > kMaxAgents || c->clock_mode == GWCP_CLOCKS_TILES ||
+                     (c->clock_mode == GWCP_CLOCKS_AUTO && tiles_ok && geo->num_agents >= kTilesFromAgents);
   cudaSetDevice(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Geo g{};
@@ -514,7 +520,7 @@ int gwcp_load_trace(gwcp_ctx* c, const gwcp_event* ev, uint64_t n, const gwcp_ge
   g.Wp = 32 * k;
   g.nT = 0;
   g.RW = g.Wp;
-  if (g.W > kMaxAgents) {
+  if (tiles) {
     g.nT = (g.W + kTileW - 1) / kTileW;
     g.Wp = g.nT * kTileW;
     g.K = g.Wp / 32;
@@ -668,6 +674,12 @@ int gwcp_debug_clock(gwcp_ctx* c, uint64_t idx, int which, uint32_t* out) {
   row[e.agent] = own;
   std::memcpy(out, row.data(), g.W * 4);
   return cuda_rc();
+}
+
+int gwcp_set_clock_mode(gwcp_ctx* c, uint32_t mode) {
+  if (!c || mode > GWCP_CLOCKS_TILES) return GWCP_ERR_ARGS;
+  c->clock_mode = mode;
+  return GWCP_OK;
 }
 
 int gwcp_set_ranker(gwcp_ctx* c, const float* theta) {

@@ -17,6 +17,7 @@ constexpr uint32_t kMaxAgents = 1024;      // clocks held in registers
 constexpr uint32_t kMaxAgentsWide = 8192;  // clocks as tables of copy-on-write tiles
 constexpr uint32_t kTileW = 256;           // entries per clock tile
 constexpr uint32_t kTabW = 32;             // words per published tile table (nT <= 32)
+constexpr uint32_t kTilesFromAgents = 512;  // automatic clock mode: tiles from this width on
 constexpr uint32_t kMaxEvents = (1u << 30) - 1;
 // distinct scope ids one lock may be used with: 64, or 320 when the trace has more than
 // 63 blocks (a block-scoped lock may be used in every block)
@@ -299,6 +300,7 @@ struct Sizes {
   uint64_t race_cap = 0;
   uint64_t tile_cap = 0;      // wide clocks: tiles in the pool
   bool cta_barriers = false;  // every block fits one CTA of walkers
+  bool hb_only = false;       // versions hold H_t: the check then tests scoped happens-before
 };
 
 // profiling hook: records an event pair around each launch when enabled

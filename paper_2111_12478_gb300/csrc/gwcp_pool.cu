@@ -83,6 +83,7 @@ struct gwcp_pool {
   bool stop = false;
   bool exclusive = false;  // a lane retrying after running out of memory runs alone
   double bpe[kClasses];    // estimated device bytes per event, by width class
+  uint32_t clock_mode[kClasses];  // clock representation per width class (autotuned)
 };
 
 namespace {
@@ -130,6 +131,7 @@ bool trim_idle(gwcp_pool* p, size_t i, std::unique_lock<std::mutex>& lk) {
 
 void run_request(gwcp_pool* p, Lane& L, Request& r) {
   uint64_t nr = 0;
+  gwcp_set_clock_mode(L.ctx, p->clock_mode[width_class(r.t.geo.num_agents)]);
   int rc = gwcp_load_trace(L.ctx, r.t.ev, r.t.n, &r.t.geo, r.t.ev_is_device, L.s);
   if (!rc) rc = gwcp_compute_order(L.ctx, L.s);
   if (!rc) {
@@ -233,6 +235,7 @@ int gwcp_pool_create(gwcp_pool** out, int device, const gwcp_pool_options* opt) 
   for (int c = 0; c < kClasses; ++c) {
     const double wp = double(std::min(1u << c, 1024u));
     p->bpe[c] = 256.0 + 0.05 * 4.0 * wp;  // raised by observation
+    p->clock_mode[c] = GWCP_CLOCKS_AUTO;
   }
   if (o.mem_budget) {
     p->budget = o.mem_budget;
@@ -351,9 +354,61 @@ int gwcp_pool_set_active_lanes(gwcp_pool* p, uint32_t active) {
   return GWCP_OK;
 }
 
+namespace {
+// seconds to analyse traces one after another on ctx with a clock mode (races counted)
+double time_mode(gwcp_ctx* ctx, cudaStream_t s, const gwcp_trace_desc* t, const std::vector<uint32_t>& which,
+                 uint32_t mode, int* rc) {
+  gwcp_set_clock_mode(ctx, mode);
+  const auto t0 = Clock::now();
+  for (uint32_t i : which) {
+    uint64_t nr = 0;
+    int r = gwcp_load_trace(ctx, t[i].ev, t[i].n, &t[i].geo, t[i].ev_is_device, s);
+    if (!r) r = gwcp_compute_order(ctx, s);
+    if (!r) r = gwcp_report_races(ctx, nullptr, 0, &nr, s);
+    if (r && r != GWCP_ERR_CAPACITY && !*rc) *rc = r;
+  }
+  cudaStreamSynchronize(s);
+  return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+}  // namespace
+
+int gwcp_pool_clock_modes(const gwcp_pool* p, uint32_t* modes16) {
+  if (!p || !modes16) return GWCP_ERR_ARGS;
+  for (int c = 0; c < kClasses; ++c) modes16[c] = p->clock_mode[c];
+  return GWCP_OK;
+}
+
 int gwcp_pool_autotune(gwcp_pool* p, const gwcp_trace_desc* t, uint32_t n, uint32_t* best, double* secs) {
   if (!p || !best || (n && !t)) return GWCP_ERR_ARGS;
   static const uint32_t kCand[8] = {1, 2, 4, 8, 12, 16, 24, 32};
+  {  // clock representation per width class, timed on a context of this thread
+    std::vector<std::vector<uint32_t>> by(kClasses);
+    std::vector<bool> both(kClasses, true);
+    for (uint32_t i = 0; i < n; ++i) {
+      const int c = width_class(t[i].geo.num_agents);
+      by[c].push_back(i);
+      if (t[i].geo.granularity != GWCP_GRAN_WARP || t[i].geo.agents_per_block > 32 || t[i].geo.num_agents > 1024)
+        both[c] = false;
+    }
+    gwcp_options co{};
+    gwcp_ctx* ctx = nullptr;
+    cudaStream_t s = nullptr;
+    if (gwcp_create(&ctx, p->device, &co) != GWCP_OK || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking))
+      return GWCP_ERR_OOM;
+    int rc = GWCP_OK;
+    for (int c = 0; c < kClasses && !rc; ++c) {
+      if (by[c].empty() || !both[c]) continue;
+      time_mode(ctx, s, t, by[c], GWCP_CLOCKS_DENSE, &rc);  // warm: buffers sized
+      const double td = time_mode(ctx, s, t, by[c], GWCP_CLOCKS_DENSE, &rc);
+      time_mode(ctx, s, t, by[c], GWCP_CLOCKS_TILES, &rc);
+      const double tt = time_mode(ctx, s, t, by[c], GWCP_CLOCKS_TILES, &rc);
+      std::lock_guard<std::mutex> lk(p->mu);
+      p->clock_mode[c] = tt < td ? GWCP_CLOCKS_TILES : GWCP_CLOCKS_DENSE;
+    }
+    gwcp_destroy(ctx);
+    cudaStreamDestroy(s);
+    if (rc) return rc;
+  }
   std::vector<uint32_t> order(n);
   for (uint32_t i = 0; i < n; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return t[a].n > t[b].n; });

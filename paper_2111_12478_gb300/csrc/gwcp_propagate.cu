@@ -38,6 +38,7 @@ struct PropArgs {
   const uint32_t* flat;
   uint4* plan;
   uint4* recmeta;
+  uint32_t hb_only;  // publish H_t instead of P_t as the clock versions the check reads
   uint32_t* rows;
   uint32_t *psnap, *hsnap, *done, *cursor;
   uint32_t *bar_j, *bar_cnt;
@@ -279,7 +280,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_propagate(PropArgs a) {
   bool abort = false;
   uint64_t joins = 0, visits = 0;
   uint32_t nbar = 0;
-  store_row<K>(a.rows + size_t(a.rowbase[u]) * Wc, P);
+  if (a.hb_only)
+    store_row<K>(a.rows + size_t(a.rowbase[u]) * Wc, H);
+  else
+    store_row<K>(a.rows + size_t(a.rowbase[u]) * Wc, P);
   const uint32_t k0 = a.sy_start[u], k1 = a.sy_start[u + 1];
   const uint32_t pb = k0 + a.incs_off[k0], pe = k1 + a.incs_off[k1];
   uint32_t* const cursor_row = a.cursor + size_t(u) * a.n_locks;
@@ -572,7 +576,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_propagate(PropArgs a) {
       set_entry<K>(H, u, N + 1);
       ++N;
     }
-    store_row<K>(a.rows + size_t(row) * Wc, P);
+    if (a.hb_only)
+      store_row<K>(a.rows + size_t(row) * Wc, H);
+    else
+      store_row<K>(a.rows + size_t(row) * Wc, P);
     if (i == 31) {  // next batch
       base += 32;
       ea = ea2;
@@ -756,6 +763,7 @@ int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s
   a.flat = b.flat;
   a.plan = b.plan;
   a.recmeta = b.recmeta;
+  a.hb_only = z.hb_only;
   // plan: per-agent stream of clock-changing steps with their static data resolved
   p.begin("g_plan", double(z.n_sync + z.n_incs) * 64 + double(z.n_cs) * 2 * g.RW * 4);
   if (z.n_cs) {

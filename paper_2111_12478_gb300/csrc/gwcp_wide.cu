@@ -48,6 +48,7 @@ struct WideArgs {
   unsigned long long* tile_ctr;
   unsigned long long tile_cap;
   uint32_t n_locks;
+  uint32_t hb_only;  // publish H_t instead of P_t as the clock versions
 };
 
 __device__ __forceinline__ uint4 max4(uint4 x, uint4 y) {
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
   set_entry_w(a, hid, u, 1u, dirty);  // H_t = bottom{t := 1}
   uint32_t N = 1;
   unsigned long long joins = 0, visits = 0;
-  if (act) a.rows[size_t(a.rowbase[u]) * kTabW + lane] = 0;
+  if (act) a.rows[size_t(a.rowbase[u]) * kTabW + lane] = a.hb_only ? hid : 0u;
   const uint32_t k0 = a.sy_start[u], k1 = a.sy_start[u + 1];
   const uint32_t pb = k0 + a.incs_off[k0], pe = k1 + a.incs_off[k1];
   uint32_t* const cursor_row = a.cursor + size_t(u) * a.n_locks;
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
       set_entry_w(a, hid, u, N + 1, dirty);
       ++N;
     }
-    if (act) a.rows[size_t(row) * kTabW + lane] = pid;
+    if (act) a.rows[size_t(row) * kTabW + lane] = a.hb_only ? hid : pid;
   }
   if (dirty) __threadfence();
   if (lane == 0) {
@@ -470,8 +471,23 @@ __device__ __forceinline__ uint32_t conflict_classes(uint32_t cb, bool same_bloc
   }
 }
 
+// Races found by a block are staged in shared memory and appended with one global atomic
+// per block; a block that finds more than kRaceStage spills the rest with one atomic each.
+constexpr uint32_t kRaceStage = 2048;
+constexpr uint32_t kCheckThreads = 256;
+
+__device__ __forceinline__ void emit_race(const WideCheckArgs& a, uint64_t v, uint32_t* s_cnt, uint64_t* s_buf) {
+  const uint32_t slot = atomicAdd(s_cnt, 1u);
+  if (slot < kRaceStage) {
+    s_buf[slot] = v;
+    return;
+  }
+  const unsigned long long at = atomicAdd(&a.st->n_races, 1ull);
+  if (at < a.race_cap) a.races[at] = v;
+}
+
 // partner tests of the access at key-order position p; returns how many were made
-__device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p) {
+__device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cnt, uint64_t* s_buf) {
   const uint32_t b = a.idx[p];
   const AccInfo ib = a.info[b];
   const uint32_t u = who_agent(ib.who), cb = who_class(ib.who), bu = who_block(ib.who);
@@ -505,21 +521,29 @@ __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p) {
       const uint32_t na = a.info[ai].epoch;
       const uint32_t tid = __ldg(rowtab + v / kTileW);
       const uint32_t cv = tid < a.tile_cap ? __ldg(a.tiles + size_t(tid) * kTileW + v % kTileW) : 0u;
-      if (na > cv) {  // N(a*) > C_b[v]
-        const unsigned long long at = atomicAdd(&a.st->n_races, 1ull);
-        if (at < a.race_cap) a.races[at] = (uint64_t(b) << 32) | ai;
-      }
+      if (na > cv) emit_race(a, (uint64_t(b) << 32) | ai, s_cnt, s_buf);  // N(a*) > C_b[v]
     }
   }
   return tests;
 }
 
-__global__ void k_wc_check(WideCheckArgs a) {
+__global__ void __launch_bounds__(kCheckThreads) k_wc_check(WideCheckArgs a) {
+  __shared__ uint32_t s_cnt;
+  __shared__ unsigned long long s_base;
+  __shared__ uint64_t s_buf[kRaceStage];
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t tests = 0;
-  if (p < a.n) tests = check_one(a, p);
+  if (p < a.n) tests = check_one(a, p, &s_cnt, s_buf);
   tests = __reduce_add_sync(0xffffffffu, tests);
   if ((threadIdx.x & 31) == 0 && tests) atomicAdd(&a.st->partner_tests, (unsigned long long)tests);
+  __syncthreads();
+  const uint32_t n = min(s_cnt, kRaceStage);
+  if (threadIdx.x == 0) s_base = n ? atomicAdd(&a.st->n_races, (unsigned long long)n) : 0ull;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+    if (s_base + i < a.race_cap) a.races[s_base + i] = s_buf[i];
 }
 
 __global__ void k_wc_grp_end(const uint32_t* n_groups, uint32_t n, uint32_t* grp_lo) { grp_lo[*n_groups] = n; }
@@ -548,6 +572,7 @@ int phaseG_wide(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s) {
   a.tile_ctr = reinterpret_cast<unsigned long long*>(&b.st->spare[2]);
   a.tile_cap = z.tile_cap;
   a.n_locks = z.n_locks;
+  a.hb_only = z.hb_only;
   const uint32_t threads = g.apb * 32;
   const size_t smem = (size_t(g.apb) * 64 + 32 + 64) * 4;
   int dev = 0, sms = 0;
@@ -625,7 +650,7 @@ void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t
   a.race_cap = z.race_cap;
   a.st = b.st;
   p.begin("i_check", double(n) * (4 + 16 + 4 + 4 + 4 + 8));
-  k_wc_check<<<nblk(n, 256), 256, 0, s>>>(a);
+  k_wc_check<<<nblk(n, kCheckThreads), kCheckThreads, 0, s>>>(a);
   count_launch();
   p.end();
 }

@@ -23,7 +23,9 @@ EXPORTS = ("gwcp_create", "gwcp_load_trace", "gwcp_compute_order", "gwcp_report_
            "gwcp_strerror", "gwcp_analyze_noalloc", "gwcp_pool_create", "gwcp_pool_submit", "gwcp_pool_wait",
            "gwcp_pool_run_batch", "gwcp_pool_set_active_lanes", "gwcp_pool_autotune", "gwcp_pool_now",
            "gwcp_pool_device_bytes", "gwcp_pool_destroy", "gwcp_set_ranker", "gwcp_location_features",
-           "gwcp_rank_scores", "gwcp_rank_grad", "gwcp_rank_train", "gwcp_check_timeline")
+           "gwcp_rank_scores", "gwcp_rank_grad", "gwcp_rank_train", "gwcp_check_timeline", "gwcp_set_clock_mode",
+           "gwcp_pool_clock_modes")
+CLOCKS_AUTO, CLOCKS_DENSE, CLOCKS_TILES = 0, 1, 2
 
 
 class GwcpError(RuntimeError):
@@ -40,7 +42,8 @@ class Geometry(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("race_capacity", ctypes.c_uint64), ("profile", ctypes.c_uint32),
-                ("blocking_sync", ctypes.c_uint32), ("timeline", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("blocking_sync", ctypes.c_uint32), ("timeline", ctypes.c_uint32), ("hb_only", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 class TrainOptions(ctypes.Structure):
@@ -115,6 +118,10 @@ def load_library():
         getattr(L, name).restype = i32
     fp = ctypes.POINTER(ctypes.c_float)
     L.gwcp_set_ranker.argtypes = [vp, vp]
+    L.gwcp_pool_clock_modes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
+    L.gwcp_pool_clock_modes.restype = i32
+    L.gwcp_set_clock_mode.argtypes = [vp, ctypes.c_uint32]
+    L.gwcp_set_clock_mode.restype = i32
     L.gwcp_location_features.argtypes = [vp, vp, vp, u64, ctypes.POINTER(u64), vp]
     L.gwcp_rank_scores.argtypes = [vp, vp, u64, vp, vp]
     L.gwcp_rank_grad.argtypes = [vp, vp, vp, u64, ctypes.c_float, vp, vp, vp]
@@ -156,9 +163,10 @@ def _stream_ptr(stream) -> int | None:
 class Context:
     """One analysis context on one CUDA device (gwcp_ctx)."""
 
-    def __init__(self, device: int = 0, race_capacity: int = 0, profile: bool = False, timeline: bool = False):
+    def __init__(self, device: int = 0, race_capacity: int = 0, profile: bool = False, timeline: bool = False,
+                 hb_only: bool = False):
         L = load_library()
-        opt = Options(race_capacity, int(profile), 0, int(timeline))
+        opt = Options(race_capacity, int(profile), 0, int(timeline), int(hb_only))
         h = ctypes.c_void_p()
         rc = L.gwcp_create(ctypes.byref(h), device, ctypes.byref(opt))
         if rc:
@@ -242,6 +250,12 @@ class Context:
         if rc:
             raise GwcpError(rc, "gwcp_debug_clock")
         return out
+
+    def set_clock_mode(self, mode: int):
+        """CLOCKS_AUTO, CLOCKS_DENSE or CLOCKS_TILES from the next load_trace on."""
+        rc = self._L.gwcp_set_clock_mode(self._h, mode)
+        if rc:
+            raise GwcpError(rc, "gwcp_set_clock_mode")
 
     def set_ranker(self, theta):
         """Checks locations in the ranker's order from the next compute_order on (theta: 5313
@@ -486,3 +500,9 @@ class Pool:
             raise GwcpError(rc, "gwcp_pool_autotune")
         cand = (1, 2, 4, 8, 12, 16, 24, 32)
         return int(best.value), {c: float(secs[i]) for i, c in enumerate(cand) if secs[i] > 0}
+
+    def clock_modes(self) -> dict:
+        """Chosen clock mode per width class {ceil(log2(W)): mode} (modes other than AUTO)."""
+        m = (ctypes.c_uint32 * 16)()
+        self._L.gwcp_pool_clock_modes(self._h, m)
+        return {c: int(m[c]) for c in range(16) if m[c]}

@@ -98,12 +98,17 @@ def test_edge_cases(ctx):
     same(ctx, ev, geo2)                                         # one agent per block
 
 
-@pytest.mark.parametrize("W,apb,gran", [(1024, 32, WARP_GRAN), (256, 16, WARP_GRAN), (96, 96, THREAD),
-                                        (128, 64, THREAD)])
+@pytest.mark.parametrize("W,apb,gran", [(1024, 32, WARP_GRAN), (512, 16, WARP_GRAN), (256, 16, WARP_GRAN),
+                                        (96, 96, THREAD), (128, 64, THREAD)])
 def test_wide_clocks(ctx, W, apb, gran):
+    # register-resident (dense) clocks at every width they take
+    from paper_2111_12478_gb300 import gwcp
+
     ev, geo = TG.random_small(7, "mixed", n_events=3000, num_agents=W, agents_per_block=apb, granularity=gran,
                               n_locks=6, n_keys=12)
-    same(ctx, ev, geo)
+    with gwcp.Context(0) as c:
+        c.set_clock_mode(gwcp.CLOCKS_DENSE)
+        same(c, ev, geo)
 
 
 # ---- clocks wider than 1024 agents: tables of copy-on-write tiles -------------------------
@@ -116,6 +121,31 @@ def test_tiled_random(ctx, W, apb):
             ev, geo = TG.random_small(seed, fam, n_events=5000, num_agents=W, agents_per_block=apb,
                                       granularity=WARP_GRAN, n_locks=4, n_keys=8)
             same(ctx, ev, geo)
+
+
+@pytest.mark.parametrize("W,apb", [(64, 8), (256, 32), (512, 16), (1024, 32)])
+def test_tiles_at_dense_widths(W, apb):
+    # the tile-table clocks at widths the register clocks also take: same races as the oracle
+    pytest.importorskip("torch")
+    from paper_2111_12478_gb300 import gwcp
+
+    with gwcp.Context(0) as c:
+        c.set_clock_mode(gwcp.CLOCKS_TILES)
+        cases = [TG.random_small(seed, fam, n_events=3000, num_agents=W, agents_per_block=apb, granularity=WARP_GRAN,
+                                 n_locks=4, n_keys=8)
+                 for fam in ("mixed", "uniform_bar", "dev_locks", "barriers", "nosync") for seed in range(2)]
+        nb = W // apb
+        cases.append(TG.generate(5, n_events=100_000, workload="8blk_64warp_10M", num_blocks=nb,
+                                 agents_per_block=apb)[:2])
+        for ev, geo in cases:
+            c.load_trace(ev, *geo.astuple())
+            c.compute_order()
+            assert np.array_equal(c.report_races(), O.run(ev, *geo.astuple()).races)
+        # thread granularity cannot use tiles
+        ev, geo = TG.random_small(0, "mixed", n_events=100, num_agents=8, agents_per_block=4)
+        with pytest.raises(gwcp.GwcpError) as ei:
+            c.load_trace(ev, *geo.astuple())
+        assert ei.value.code == gwcp.ERR_UNSUPPORTED
 
 
 def test_tiled_clock_rows(ctx):
@@ -240,6 +270,32 @@ def test_more_races_than_events(ctx):
     first = got[np.isin(got[:, 1], w1)]
     assert len(first) == n_loc * 1023 and set(np.unique(first[:, 1]).tolist()) == set(w1.tolist())
     assert np.array_equal(got, O.run(ev, *geo.astuple()).races)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_hb_only_variant(mode):
+    # the paper's happens-before baseline (H clocks) on both clock representations: the
+    # oracle's HB-only race set, contained in the GWCP race set (C_t <= H_t: GWCP orders
+    # fewer pairs and predicts the races HB misses)
+    pytest.importorskip("torch")
+    from paper_2111_12478_gb300 import gwcp
+
+    cases = [TG.random_small(seed, fam, n_events=600, num_agents=16, agents_per_block=8, granularity=WARP_GRAN,
+                             n_locks=3, n_keys=6)
+             for fam in TG.FAMILIES for seed in range(3)]
+    cases.append(TG.generate(6, n_events=150_000, workload="8blk_64warp_10M")[:2])
+    n_more = 0
+    with gwcp.Context(0, hb_only=True) as h, gwcp.Context(0) as w:
+        h.set_clock_mode(mode)
+        for ev, geo in cases:
+            h.load_trace(ev, *geo.astuple())
+            h.compute_order()
+            hb = h.report_races()
+            assert np.array_equal(hb, O.run(ev, *geo.astuple(), hb_only=True).races)
+            gw = gpu_races(w, ev, geo)
+            assert {tuple(r) for r in hb.tolist()} <= {tuple(r) for r in gw.tolist()}
+            n_more += len(gw) - len(hb)
+    assert n_more > 0  # GWCP predicts races that HB misses
 
 
 def test_device_input_and_stream(ctx):

@@ -143,8 +143,15 @@ def test_invalid_trace_in_batch(gw, mix):
 
 
 def test_autotune(gw, mix):
-    traces, _ = mix
+    traces, want = mix
     with gw.Pool(0, lanes=8) as P:
         best, secs = P.autotune([(ev, geo.astuple()) for ev, geo in traces])
         assert best in secs and set(secs) == {1, 2, 4, 8}
         assert secs[best] == min(secs.values())
+        # width classes 7..10 (128..1024 warps) hold only traces that take both clock
+        # representations; class 6 also holds thread-granularity traces
+        modes = P.clock_modes()
+        assert {7, 8, 9, 10} <= set(modes) <= {6, 7, 8, 9, 10} and set(modes.values()) <= {1, 2}
+        got = P.run_batch([(ev, geo.astuple()) for ev, geo in traces], [len(w) for w in want])
+        for (races, rc, n), w in zip(got, want):
+            assert rc == 0 and np.array_equal(races, w)
