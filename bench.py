@@ -109,7 +109,7 @@ def source_hash(names):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"g_propagate": ["gwcp_propagate.cu"], "i_check": ["gwcp_check.cu"], "h_sort": ["gwcp_prims.cu"],
+KERNEL_SOURCES = {"g_propagate": ["gwcp_propagate.cu"], "i_check": ["gwcp_wide.cu"], "h_sort": ["gwcp_prims.cu"],
                   "a_scatter": ["gwcp_prep.cu"], "a_count": ["gwcp_prep.cu"], "d_gaps": ["gwcp_prep.cu"]}
 
 

@@ -64,6 +64,7 @@ struct gwcp_ctx {
   cudaEvent_t sync_ev = nullptr;  // options.blocking_sync: host waits sleep on this event
   std::vector<float> rank_theta;  // gwcp_set_ranker: the MLP's parameters (empty = off)
   uint32_t clock_mode = GWCP_CLOCKS_AUTO;  // gwcp_set_clock_mode
+  uint32_t check_mode = GWCP_CHECK_AUTO;   // gwcp_set_check_mode
   uint32_t n_chunks_timeline = 0; // chunks of the last check's timeline
   std::vector<float> prof_ms;
   std::vector<double> prof_bytes;
@@ -123,6 +124,8 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   z = Sizes{};
   z.N = c->n;
   z.hb_only = c->opt.hb_only != 0;
+  z.sparse_check = g.nT || c->check_mode == GWCP_CHECK_SPARSE ||
+                   (c->check_mode == GWCP_CHECK_AUTO && g.W >= kSparseCheckFromAgents);
   z.TA = g.Wp <= 256 ? 2048 : 8192;
   while (uint64_t(g.W) * ((z.N + z.TA - 1) / z.TA) > (1ull << 26)) z.TA <<= 1;  // bounded agent histogram
   z.ntA = uint32_t((z.N + z.TA - 1) / z.TA);
@@ -286,7 +289,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   const bool global_bars = !z.cta_barriers || g.gran == GWCP_GRAN_THREAD;
   b.bar_j = get<uint32_t>(c, "bar_j", global_bars ? size_t(z.n_bar) * 2 * g.Wp : 1, &oom);
   b.bar_cnt = get<uint32_t>(c, "bar_cnt", global_bars ? z.n_bar : 1, &oom);
-  if (g.nT) {
+  if (z.sparse_check) {
     const size_t na = size_t(z.n_acc) + 1;
     b.wc_flag = get<uint32_t>(c, "wc_flag", na, &oom);
     b.wc_run = get<uint32_t>(c, "wc_run", na, &oom);
@@ -324,7 +327,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   // on a side stream, with their own scratch, while the propagation runs on s
   uint32_t* side_tmp = get<uint32_t>(
       c, "side_tmp", std::max(radix_tmp_need(size_t(z.n_acc) + 1), scan_tmp_need(size_t(z.n_acc) * 4 + 2)) + 64, &oom);
-  const bool ranked = !c->rank_theta.empty() && !g.nT && z.n_acc;
+  const bool ranked = !c->rank_theta.empty() && z.n_acc;
   RankIn rin{};
   uint32_t *rk_tmp = nullptr, *rk_nloc = nullptr, *rk_val = nullptr, *rk_val2 = nullptr;
   float *rk_feat = nullptr, *rk_score = nullptr, *rk_theta = nullptr;
@@ -343,9 +346,10 @@ int run(gwcp_ctx* c, cudaStream_t s) {
     rk_val = get<uint32_t>(c, "rk_val", z.n_acc, &oom);
     rk_val2 = get<uint32_t>(c, "rk_val2", z.n_acc, &oom);
   }
-  if (c->opt.timeline && !g.nT) {
-    b.chunk_ns = get<unsigned long long>(c, "chunk_ns", size_t(z.n_chunks) + 1, &oom);
-    b.chunk_races = get<uint32_t>(c, "chunk_races", size_t(z.n_chunks) + 1, &oom);
+  z.n_timeline = z.sparse_check ? sparse_check_blocks(z.n_acc) : z.n_chunks;
+  if (c->opt.timeline) {
+    b.chunk_ns = get<unsigned long long>(c, "chunk_ns", size_t(z.n_timeline) + 1, &oom);
+    b.chunk_races = get<uint32_t>(c, "chunk_races", size_t(z.n_timeline) + 1, &oom);
   } else {
     b.chunk_ns = nullptr;
     b.chunk_races = nullptr;
@@ -375,7 +379,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
     std::swap(b.acc_idx, b.acc_idx2);
     c->prof.end();
   }
-  if (g.nT)
+  if (z.sparse_check)
     phaseI_wide_group(b, g, z, side_tmp, c->side, c->prof);
   else
     phaseI_carry(b, g, z, c->side, c->prof);
@@ -388,11 +392,11 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   cudaStreamWaitEvent(s, c->join, 0);
   if (prc) return prc;
   if (b.chunk_ns) stamp_now(&b.st->spare[5], s);  // the check's start, for the timeline
-  if (g.nT)
+  if (z.sparse_check)
     phaseI_wide_check(b, g, z, s, c->prof);
   else
     phaseI_check(b, g, z, s, c->prof);
-  c->n_chunks_timeline = b.chunk_ns ? z.n_chunks : 0;
+  c->n_chunks_timeline = b.chunk_ns ? z.n_timeline : 0;
   {
     int rc = read_status(c, s, nullptr, 0);
     if (rc) return rc;
@@ -416,7 +420,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
     if (oom) return GWCP_ERR_OOM;
     const unsigned long long tests = c->st_host->partner_tests;
     cudaMemsetAsync(&b.st->n_races, 0, sizeof(unsigned long long), s);
-    if (g.nT)
+    if (z.sparse_check)
       phaseI_wide_check(b, g, z, s, c->prof);
     else
       phaseI_check(b, g, z, s, c->prof);
@@ -674,6 +678,12 @@ int gwcp_debug_clock(gwcp_ctx* c, uint64_t idx, int which, uint32_t* out) {
   row[e.agent] = own;
   std::memcpy(out, row.data(), g.W * 4);
   return cuda_rc();
+}
+
+int gwcp_set_check_mode(gwcp_ctx* c, uint32_t mode) {
+  if (!c || mode > GWCP_CHECK_SPARSE) return GWCP_ERR_ARGS;
+  c->check_mode = mode;
+  return GWCP_OK;
 }
 
 int gwcp_set_clock_mode(gwcp_ctx* c, uint32_t mode) {

@@ -18,6 +18,7 @@ constexpr uint32_t kMaxAgentsWide = 8192;  // clocks as tables of copy-on-write 
 constexpr uint32_t kTileW = 256;           // entries per clock tile
 constexpr uint32_t kTabW = 32;             // words per published tile table (nT <= 32)
 constexpr uint32_t kTilesFromAgents = 512;  // automatic clock mode: tiles from this width on
+constexpr uint32_t kSparseCheckFromAgents = 1;  // automatic check mode: partner groups (measured faster)
 constexpr uint32_t kMaxEvents = (1u << 30) - 1;
 // distinct scope ids one lock may be used with: 64, or 320 when the trace has more than
 // 63 blocks (a block-scoped lock may be used in every block)
@@ -301,6 +302,8 @@ struct Sizes {
   uint64_t tile_cap = 0;      // wide clocks: tiles in the pool
   bool cta_barriers = false;  // every block fits one CTA of walkers
   bool hb_only = false;       // versions hold H_t: the check then tests scoped happens-before
+  bool sparse_check = false;  // partner-group check (always with tile clocks)
+  uint32_t n_timeline = 0;    // check timeline entries (chunks or check blocks)
 };
 
 // profiling hook: records an event pair around each launch when enabled
@@ -374,5 +377,6 @@ void stamp_now(unsigned long long* at, cudaStream_t s);
 int phaseG_wide(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s);
 void phaseI_wide_group(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t s, Prof& p);
 void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
+uint32_t sparse_check_blocks(uint32_t n_acc);  // timeline entries of the partner-group check
 
 }  // namespace gwcp

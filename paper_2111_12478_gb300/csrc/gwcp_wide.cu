@@ -430,6 +430,9 @@ struct WideCheckArgs {
   uint64_t* races;
   unsigned long long race_cap;
   DevStatus* st;
+  uint32_t dense_wp;             // 0: clocks are tile tables; else dense rows of this many words
+  unsigned long long* chunk_ns;  // optional timeline: globaltimer at each block's end
+  uint32_t* chunk_races;         // and the races it found
 };
 
 // latest key-order position < p in group gi, or NONE
@@ -492,7 +495,7 @@ __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cn
   const AccInfo ib = a.info[b];
   const uint32_t u = who_agent(ib.who), cb = who_class(ib.who), bu = who_block(ib.who);
   const uint32_t run = a.run_excl[p] + a.flag[p] - 1;
-  const uint32_t* rowtab = a.rows + size_t(ib.row) * kTabW;
+  const uint32_t* rowtab = a.rows + size_t(ib.row) * (a.dense_wp ? a.dense_wp : kTabW);
   const uint32_t any_mask = conflict_classes(cb, false) | conflict_classes(cb, true);
   uint32_t tests = 0;
   for (uint32_t q = 0; q < 4; ++q) {
@@ -519,8 +522,13 @@ __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cn
       ++tests;
       const uint32_t ai = a.idx[pos];
       const uint32_t na = a.info[ai].epoch;
-      const uint32_t tid = __ldg(rowtab + v / kTileW);
-      const uint32_t cv = tid < a.tile_cap ? __ldg(a.tiles + size_t(tid) * kTileW + v % kTileW) : 0u;
+      uint32_t cv;
+      if (a.dense_wp) {
+        cv = __ldg(rowtab + v);
+      } else {
+        const uint32_t tid = __ldg(rowtab + v / kTileW);
+        cv = tid < a.tile_cap ? __ldg(a.tiles + size_t(tid) * kTileW + v % kTileW) : 0u;
+      }
       if (na > cv) emit_race(a, (uint64_t(b) << 32) | ai, s_cnt, s_buf);  // N(a*) > C_b[v]
     }
   }
@@ -544,6 +552,12 @@ __global__ void __launch_bounds__(kCheckThreads) k_wc_check(WideCheckArgs a) {
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
     if (s_base + i < a.race_cap) a.races[s_base + i] = s_buf[i];
+  if (a.chunk_ns && threadIdx.x == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    a.chunk_ns[blockIdx.x] = t;
+    a.chunk_races[blockIdx.x] = s_cnt;
+  }
 }
 
 __global__ void k_wc_grp_end(const uint32_t* n_groups, uint32_t n, uint32_t* grp_lo) { grp_lo[*n_groups] = n; }
@@ -629,6 +643,8 @@ void phaseI_wide_group(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStrea
   p.end();
 }
 
+uint32_t sparse_check_blocks(uint32_t n_acc) { return nblk(n_acc, kCheckThreads); }
+
 void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   const uint32_t n = z.n_acc;
   if (!n) return;
@@ -649,6 +665,9 @@ void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t
   a.races = b.races;
   a.race_cap = z.race_cap;
   a.st = b.st;
+  a.dense_wp = g.nT ? 0u : g.Wp;
+  a.chunk_ns = b.chunk_ns;
+  a.chunk_races = b.chunk_races;
   p.begin("i_check", double(n) * (4 + 16 + 4 + 4 + 4 + 8));
   k_wc_check<<<nblk(n, kCheckThreads), kCheckThreads, 0, s>>>(a);
   count_launch();

@@ -24,8 +24,9 @@ EXPORTS = ("gwcp_create", "gwcp_load_trace", "gwcp_compute_order", "gwcp_report_
            "gwcp_pool_run_batch", "gwcp_pool_set_active_lanes", "gwcp_pool_autotune", "gwcp_pool_now",
            "gwcp_pool_device_bytes", "gwcp_pool_destroy", "gwcp_set_ranker", "gwcp_location_features",
            "gwcp_rank_scores", "gwcp_rank_grad", "gwcp_rank_train", "gwcp_check_timeline", "gwcp_set_clock_mode",
-           "gwcp_pool_clock_modes")
+           "gwcp_pool_clock_modes", "gwcp_set_check_mode")
 CLOCKS_AUTO, CLOCKS_DENSE, CLOCKS_TILES = 0, 1, 2
+CHECK_AUTO, CHECK_CHUNKED, CHECK_SPARSE = 0, 1, 2
 
 
 class GwcpError(RuntimeError):
@@ -120,6 +121,8 @@ def load_library():
     L.gwcp_set_ranker.argtypes = [vp, vp]
     L.gwcp_pool_clock_modes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
     L.gwcp_pool_clock_modes.restype = i32
+    L.gwcp_set_check_mode.argtypes = [vp, ctypes.c_uint32]
+    L.gwcp_set_check_mode.restype = i32
     L.gwcp_set_clock_mode.argtypes = [vp, ctypes.c_uint32]
     L.gwcp_set_clock_mode.restype = i32
     L.gwcp_location_features.argtypes = [vp, vp, vp, u64, ctypes.POINTER(u64), vp]
@@ -256,6 +259,12 @@ class Context:
         rc = self._L.gwcp_set_clock_mode(self._h, mode)
         if rc:
             raise GwcpError(rc, "gwcp_set_clock_mode")
+
+    def set_check_mode(self, mode: int):
+        """CHECK_AUTO, CHECK_CHUNKED or CHECK_SPARSE from the next compute_order on."""
+        rc = self._L.gwcp_set_check_mode(self._h, mode)
+        if rc:
+            raise GwcpError(rc, "gwcp_set_check_mode")
 
     def set_ranker(self, theta):
         """Checks locations in the ranker's order from the next compute_order on (theta: 5313

@@ -273,6 +273,31 @@ def test_more_races_than_events(ctx):
 
 
 @pytest.mark.parametrize("mode", [1, 2])
+def test_check_modes_dense_clocks(mode):
+    # the chunked check and the partner-group check over dense register clocks
+    pytest.importorskip("torch")
+    from paper_2111_12478_gb300 import gwcp, ranker
+
+    with gwcp.Context(0, timeline=True) as c:
+        c.set_clock_mode(gwcp.CLOCKS_DENSE)
+        c.set_check_mode(mode)
+        for W, apb, gran in [(4, 2, THREAD), (64, 64, THREAD), (40, 8, WARP_GRAN), (256, 16, WARP_GRAN)]:
+            for fam in TG.FAMILIES:
+                for seed in range(4):
+                    ev, geo = TG.random_small(seed, fam, n_events=300, num_agents=W, agents_per_block=apb,
+                                              granularity=gran, n_locks=3, n_keys=5)
+                    same(c, ev, geo)
+        for ev, geo in (TG.generate(2, workload="tiny_1blk_64thr_10k")[:2],
+                        TG.generate(8, n_events=200_000, workload="8blk_64warp_10M")[:2]):
+            want = same(c, ev, geo)
+            c.set_ranker(ranker.init_theta(3))  # a ranked order: same races, full timeline
+            got = gpu_races(c, ev, geo)
+            _, _, per = c.check_timeline()
+            c.set_ranker(None)
+            assert np.array_equal(got, want) and int(per.sum()) == len(want)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
 def test_hb_only_variant(mode):
     # the paper's happens-before baseline (H clocks) on both clock representations: the
     # oracle's HB-only race set, contained in the GWCP race set (C_t <= H_t: GWCP orders
