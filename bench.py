@@ -127,6 +127,20 @@ def traffic_for(phase):
     return None
 
 
+def replica_reduce(t_local: float, events_local: int, dist=None, device="cpu"):
+    """Replicas (one independent trace per rank, no collective on the data path): the job's
+    time is the slowest rank's, its work the events of all ranks. Returns (t_max, events)."""
+    if dist is None:
+        return t_local, events_local
+    import torch
+
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    e = torch.tensor([float(events_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(e.item())
+
+
 def bench_batched(args, local, torch, gwcp, tracegen, np):
     """The batched workload (512 independent traces, 10k-5M events, 64-4096 warps; inputs
     resident on the device): the plain path (one context, one trace after another) against
@@ -450,13 +464,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in per_step]
     total_ms = sum(step_ms)
     t_local = total_ms / 1e3
-    if dist:
-        t = torch.tensor([t_local], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    value = n_ev * world * args.steps / t_max
+    t_max, ev_total = replica_reduce(t_local, n_ev * args.steps, dist, device=f"cuda:{local}")
+    value = ev_total / t_max
     ms_per_step = t_max * 1e3 / args.steps
 
     # end to end through the C ABI: pinned host trace -> device, compute, races -> host
@@ -528,6 +537,12 @@ def main():
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                          "traffic": traffic_for(dom), "algorithmic_bytes": dom_bytes, "avg_ms": dom_ms},
+            "roofline_check": ({"bound": "hbm", "kernel": "i_check", "achieved": phases["i_check"][1] / (phases["i_check"][0] / 1e3) / 1e9,
+                                "peak": peak, "unit": "GB/s", "frac": phases["i_check"][1] / (phases["i_check"][0] / 1e3) / 1e9 / peak,
+                                "traffic": traffic_for("i_check"), "algorithmic_bytes": phases["i_check"][1],
+                                "avg_ms": phases["i_check"][0],
+                                "dram_frac": (traffic_for("i_check") / (phases["i_check"][0] / 1e3) / 1e9 / peak
+                                              if traffic_for("i_check") else None)} if "i_check" in phases else None),
             "phases_ms": {k: round(v[0], 4) for k, v in sorted(phases.items(), key=lambda kv: -kv[1][0])},
             "cpu_baseline": cpu,
             "race_set_bit_exact": exact, "n_races": int(n_races),

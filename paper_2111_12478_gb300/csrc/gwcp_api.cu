@@ -62,6 +62,7 @@ struct gwcp_ctx {
   cudaStream_t side = nullptr;  // runs the access grouping beside the propagation
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t sync_ev = nullptr;  // options.blocking_sync: host waits sleep on this event
+  cudaStream_t alloc_s = nullptr;  // stream that buffer (re)allocations are ordered on
   std::vector<float> rank_theta;  // gwcp_set_ranker: the MLP's parameters (empty = off)
   uint32_t clock_mode = GWCP_CLOCKS_AUTO;  // gwcp_set_clock_mode
   uint32_t check_mode = GWCP_CHECK_AUTO;   // gwcp_set_check_mode
@@ -76,16 +77,19 @@ namespace {
 const uint32_t kNoneHost = 0xFFFFFFFFu;
 const int kRerun = 1;  // run() result: the tile pool was grown, run again
 
+// Buffers come from the device's default memory pool, allocated and freed in stream
+// order on the context's current stream (c->alloc_s): growing a buffer neither waits for
+// the device nor blocks other streams, so contexts on other streams keep running.
 template <typename T>
 T* get(gwcp_ctx* c, const char* name, size_t count, bool* oom) {
   const size_t bytes = (count ? count : 1) * sizeof(T);
   auto& a = c->allocs[name];
   if (a.second < bytes) {
-    if (a.first) cudaFree(a.first);
+    if (a.first) cudaFreeAsync(a.first, c->alloc_s);
     a.first = nullptr;
     a.second = 0;
     const size_t want = bytes + bytes / 8;
-    if (cudaMalloc(&a.first, want) != cudaSuccess) {
+    if (cudaMallocAsync(&a.first, want, c->alloc_s) != cudaSuccess) {
       cudaGetLastError();
       *oom = true;
       return nullptr;
@@ -93,6 +97,16 @@ T* get(gwcp_ctx* c, const char* name, size_t count, bool* oom) {
     a.second = want;
   }
   return static_cast<T*>(a.first);
+}
+
+// Makes s the stream that buffer frees and allocations are ordered on; when the caller
+// switched streams, the previous one is drained first so that no stream-ordered free can
+// overtake work still queued there.
+void use_stream(gwcp_ctx* c, cudaStream_t s) {
+  if (c->alloc_s != s) {
+    cudaStreamSynchronize(c->alloc_s);
+    c->alloc_s = s;
+  }
 }
 
 int cuda_rc() {
@@ -117,6 +131,7 @@ int read_status(gwcp_ctx* c, cudaStream_t s, const uint32_t* const* extra, int n
 }
 
 int run(gwcp_ctx* c, cudaStream_t s) {
+  use_stream(c, s);
   Bufs& b = c->b;
   Sizes& z = c->z;
   const Geo& g = c->g;
@@ -355,6 +370,13 @@ int run(gwcp_ctx* c, cudaStream_t s) {
     b.chunk_races = nullptr;
   }
   if (oom) return GWCP_ERR_OOM;
+  phaseF_incs(b, g, z, key_mask, s, c->prof);
+  phaseF_walk(b, g, z, key_mask, s, c->prof);
+  z.n_groups = z.n_exp;  // upper bound; the kernel reads the exact count on the device
+  phaseF_deps(b, g, z, s, c->prof);
+  // the access grouping (and the ranker) need only the decoded accesses: they run on the
+  // side stream while the propagation occupies its few SMs, after the main stream's other
+  // phases so that they do not compete with them
   cudaEventRecord(c->fork, s);
   cudaStreamWaitEvent(c->side, c->fork, 0);
   phaseH_sort(b, g, z, key_mask, side_tmp, c->side, c->prof);
@@ -384,10 +406,6 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   else
     phaseI_carry(b, g, z, c->side, c->prof);
   cudaEventRecord(c->join, c->side);
-  phaseF_incs(b, g, z, key_mask, s, c->prof);
-  phaseF_walk(b, g, z, key_mask, s, c->prof);
-  z.n_groups = z.n_exp;  // upper bound; the kernel reads the exact count on the device
-  phaseF_deps(b, g, z, s, c->prof);
   int prc = phaseG_propagate(b, g, z, s, c->prof);
   cudaStreamWaitEvent(s, c->join, 0);
   if (prc) return prc;
@@ -457,10 +475,14 @@ bool ctx_races_complete(const gwcp_ctx* c) { return c->n_races <= c->z.race_cap;
 // sure no work of this context is in flight
 void ctx_trim(gwcp_ctx* c) {
   cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->alloc_s);
   for (auto& kv : c->allocs)
-    if (kv.second.first) cudaFree(kv.second.first);
+    if (kv.second.first) cudaFreeAsync(kv.second.first, c->alloc_s);
   c->allocs.clear();
-  if (c->ev_own) cudaFree(c->ev_own);
+  if (c->ev_own) cudaFreeAsync(c->ev_own, c->alloc_s);
+  cudaStreamSynchronize(c->alloc_s);
+  cudaMemPool_t mp;  // give the pool's unused reserve back to the device
+  if (cudaDeviceGetDefaultMemPool(&mp, c->device) == cudaSuccess) cudaMemPoolTrimTo(mp, 0);
   c->ev_own = nullptr;
   c->ev_own_cap = 0;
   c->has_trace = false;
@@ -479,6 +501,15 @@ int gwcp_create(gwcp_ctx** out, int device, const gwcp_options* opt) {
     return GWCP_ERR_CUDA;
   }
   if (cudaSetDevice(device) != cudaSuccess) return GWCP_ERR_CUDA;
+  {
+    // freed buffers stay reserved in the device's default pool for the next allocation
+    // instead of going back to the driver at every synchronisation
+    cudaMemPool_t mp;
+    uint64_t keep = ~0ull;
+    if (cudaDeviceGetDefaultMemPool(&mp, device) == cudaSuccess)
+      cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaGetLastError();
+  }
   auto* c = new gwcp_ctx();
   c->device = device;
   if (opt) c->opt = *opt;
@@ -513,6 +544,7 @@ int gwcp_load_trace(gwcp_ctx* c, const gwcp_event* ev, uint64_t n, const gwcp_ge
                      (c->clock_mode == GWCP_CLOCKS_AUTO && tiles_ok && geo->num_agents >= kTilesFromAgents);
   cudaSetDevice(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  use_stream(c, s);
   Geo g{};
   g.W = geo->num_agents;
   g.apb = geo->agents_per_block;
@@ -539,10 +571,10 @@ int gwcp_load_trace(gwcp_ctx* c, const gwcp_event* ev, uint64_t n, const gwcp_ge
   } else {
     const size_t bytes = (n ? n : 1) * sizeof(Event);
     if (c->ev_own_cap < bytes) {
-      if (c->ev_own) cudaFree(c->ev_own);
+      if (c->ev_own) cudaFreeAsync(c->ev_own, s);
       c->ev_own = nullptr;
       c->ev_own_cap = 0;
-      if (cudaMalloc(&c->ev_own, bytes) != cudaSuccess) {
+      if (cudaMallocAsync(&c->ev_own, bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return GWCP_ERR_OOM;
       }
@@ -581,6 +613,7 @@ int gwcp_report_races(gwcp_ctx* c, gwcp_race* out, uint64_t cap, uint64_t* n_rac
   if (!c->computed) return GWCP_ERR_STATE;
   cudaSetDevice(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  use_stream(c, s);
   if (wait_stream(c, s) != cudaSuccess) return GWCP_ERR_CUDA;
   *n_races = 0;
   if (c->compute_rc) return c->compute_rc;
@@ -707,6 +740,7 @@ int gwcp_location_features(gwcp_ctx* c, float* feat, uint64_t* keys, uint64_t ca
   if (!c->computed || c->compute_rc) return GWCP_ERR_STATE;
   cudaSetDevice(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  use_stream(c, s);
   *n_loc = 0;
   const Sizes& z = c->z;
   if (c->n == 0 || z.n_acc == 0) return GWCP_OK;
@@ -832,9 +866,12 @@ int gwcp_counters(const gwcp_ctx* c, uint64_t* out8) {
 void gwcp_destroy(gwcp_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->alloc_s);
+  if (c->side) cudaStreamSynchronize(c->side);
   for (auto& kv : c->allocs)
-    if (kv.second.first) cudaFree(kv.second.first);
-  if (c->ev_own) cudaFree(c->ev_own);
+    if (kv.second.first) cudaFreeAsync(kv.second.first, c->alloc_s);
+  if (c->ev_own) cudaFreeAsync(c->ev_own, c->alloc_s);
+  cudaStreamSynchronize(c->alloc_s);
   if (c->st_host) cudaFreeHost(c->st_host);
   if (c->cnt_host) cudaFreeHost(c->cnt_host);
   for (auto e : c->prof.pool) cudaEventDestroy(e);

@@ -613,7 +613,6 @@ int phaseG_wide(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s) {
 // Regrouping of the key-sorted accesses by (location, class, agent); runs beside the
 // propagation (it needs AccInfo and the key order, not the clocks).
 void phaseI_wide_group(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t s, Prof& p) {
-  (void)g;
   const uint32_t n = z.n_acc;
   if (!n) return;
   p.begin("i_wide_group", double(n) * (8 + 4 + 16 + 12 * 3 * 5 + 16), s);
@@ -622,10 +621,12 @@ void phaseI_wide_group(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStrea
   scan_exclusive(b.wc_flag, b.wc_run, n, b.wc_run + n, tmp, s);
   k_wc_compose<<<nblk(n, 256), 256, 0, s>>>(b.wc_run, b.wc_flag, b.acc_idx, b.acc_info, n, b.wc_key, b.wc_val);
   count_launch();
-  // runs < n <= 2^30: key bits 15 .. 15 + ceil(log2 n)
-  uint32_t rb = 1;
+  // runs < n <= 2^30: key bits 15 .. 15 + ceil(log2 n); class bits 13-14; agent bits below
+  // 13, of which only ceil(log2 W) vary
+  uint32_t rb = 1, ab = 0;
   while ((1ull << rb) < n) ++rb;
-  const uint64_t mask = (((1ull << rb) - 1) << 15) | 0x7FFFull;
+  while ((1u << ab) < g.W) ++ab;
+  const uint64_t mask = (((1ull << rb) - 1) << 15) | (3ull << 13) | ((1ull << ab) - 1);
   if (radix_sort_pairs(b.wc_key, b.wc_val, b.wc_key2, b.wc_val2, n, mask, tmp, s)) {
     std::swap(b.wc_key, b.wc_key2);
     std::swap(b.wc_val, b.wc_val2);
