@@ -48,7 +48,8 @@ def read_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms; summary() keeps the
+    samples taken between mark_start() and mark_end() (the timed region)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -70,9 +71,18 @@ class ClockSampler:
             self.proc = None
         return self
 
+    t_start = None
+    t_end = None
+
+    def mark_start(self):
+        self.t_start = time.perf_counter()
+
+    def mark_end(self):
+        self.t_end = time.perf_counter()
+
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *a):
         if self.proc:
@@ -85,7 +95,9 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
+        for t, ln in self.lines:
+            if self.t_start is not None and (t < self.t_start or (self.t_end is not None and t > self.t_end + 0.2)):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -375,7 +387,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gwcp", choices=["gwcp", "reference"])
     ap.add_argument("--ref-events", type=int, default=1_000_000)
@@ -431,6 +443,7 @@ def main():
     def step():
         ctx.compute_order(stream=stream)
 
+    clocks = ClockSampler(local).__enter__()  # started early: nvidia-smi takes a moment to start
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -442,24 +455,26 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
-        for _ in range(args.steps):
-            s0 = torch.cuda.Event(enable_timing=True)
-            s1 = torch.cuda.Event(enable_timing=True)
-            s0.record(stream)
-            if not per_step:
-                start.record(stream)
-            step()
-            s1.record(stream)
-            n_races = ctx.race_count(stream=stream)  # synchronises; the result read of the step
-            per_step.append((s0, s1))
-            for name, ms, by in ctx.profile():
-                a = prof_acc.setdefault(name, [0.0, 0.0, 0])
-                a[0] += ms
-                a[1] += by
-                a[2] += 1
-        end.record(stream)
-        torch.cuda.synchronize()
+    clocks.mark_start()
+    for _ in range(args.steps):
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        if not per_step:
+            start.record(stream)
+        step()
+        s1.record(stream)
+        n_races = ctx.race_count(stream=stream)  # synchronises; the result read of the step
+        per_step.append((s0, s1))
+        for name, ms, by in ctx.profile():
+            a = prof_acc.setdefault(name, [0.0, 0.0, 0])
+            a[0] += ms
+            a[1] += by
+            a[2] += 1
+    end.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark_end()
+    clocks.__exit__(None, None, None)
     launches = gwcp.launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in per_step]
     total_ms = sum(step_ms)
