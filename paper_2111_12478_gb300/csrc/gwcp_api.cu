@@ -317,6 +317,9 @@ int run(gwcp_ctx* c, cudaStream_t s) {
     b.wc_grp_lo = get<uint32_t>(c, "wc_grp_lo", na, &oom);
     b.wc_grp_agent = get<uint32_t>(c, "wc_grp_agent", na, &oom);
     b.wc_rc = get<uint32_t>(c, "wc_rc", 4 * na + 2, &oom);
+    b.wc_who = get<uint32_t>(c, "wc_who", na, &oom);
+    b.wc_row = get<uint32_t>(c, "wc_row", na, &oom);
+    b.wc_ep = get<uint32_t>(c, "wc_ep", na, &oom);
   } else {
     z.n_chunks = uint32_t(check_chunks(z.n_acc));
     const size_t ng = check_group_count(z.n_acc);

@@ -174,6 +174,9 @@ struct Bufs {
   uint32_t* wc_grp_lo = nullptr;     // [n_groups + 1]
   uint32_t* wc_grp_agent = nullptr;  // [n_groups]
   uint32_t* wc_rc = nullptr;     // [4 * n_acc + 2] first group of each (run, class)
+  uint32_t* wc_who = nullptr;    // [n_acc] record fields in key order: who, version row, epoch
+  uint32_t* wc_row = nullptr;
+  uint32_t* wc_ep = nullptr;
   unsigned long long* chunk_ns = nullptr;  // [n_chunks] check timeline (options.timeline)
   uint32_t* chunk_races = nullptr;         // [n_chunks]
   uint64_t* races = nullptr;    // [race_cap] (later << 32) | earlier

@@ -387,14 +387,21 @@ __global__ void k_wc_runflags(const uint64_t* key, uint32_t n, uint32_t* flag) {
 }
 
 // composite key (run, class, agent) for the stable regrouping; value = key-order position
+// composite keys (run, class, agent) of the key-ordered accesses; also the fields of each
+// access record the check needs, copied into key order (a sequential read for the check
+// instead of a gather by trace index)
 __global__ void k_wc_compose(const uint32_t* run_excl, const uint32_t* flag, const uint32_t* idx,
-                             const AccInfo* info, uint32_t n, uint64_t* ck, uint32_t* cv) {
+                             const AccInfo* info, uint32_t n, uint64_t* ck, uint32_t* cv, uint32_t* s_who,
+                             uint32_t* s_row, uint32_t* s_ep) {
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const uint32_t run = run_excl[p] + flag[p] - 1;
-  const uint32_t who = info[idx[p]].who;
-  ck[p] = (uint64_t(run) << 15) | (uint64_t(who_class(who)) << 13) | who_agent(who);
+  const AccInfo in = info[idx[p]];
+  ck[p] = (uint64_t(run) << 15) | (uint64_t(who_class(in.who)) << 13) | who_agent(in.who);
   cv[p] = p;
+  s_who[p] = in.who;
+  s_row[p] = in.row;
+  s_ep[p] = in.epoch;
 }
 
 // group starts over the sorted composite keys, and per (run, class) group counts
@@ -424,6 +431,7 @@ struct WideCheckArgs {
   const uint32_t* grp_agent;
   const uint32_t* rc_off;    // [(run << 2 | class) + 1]
   const AccInfo* info;
+  const uint32_t *s_who, *s_row, *s_ep;  // record fields in key order
   const uint32_t* rows;
   const uint32_t* tiles;
   unsigned long long tile_cap;  // ids at or above it (rows a failed walk left stale) read as zero
@@ -492,10 +500,10 @@ __device__ __forceinline__ void emit_race(const WideCheckArgs& a, uint64_t v, ui
 // partner tests of the access at key-order position p; returns how many were made
 __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cnt, uint64_t* s_buf) {
   const uint32_t b = a.idx[p];
-  const AccInfo ib = a.info[b];
-  const uint32_t u = who_agent(ib.who), cb = who_class(ib.who), bu = who_block(ib.who);
+  const uint32_t bwho = a.s_who[p];
+  const uint32_t u = who_agent(bwho), cb = who_class(bwho), bu = who_block(bwho);
   const uint32_t run = a.run_excl[p] + a.flag[p] - 1;
-  const uint32_t* rowtab = a.rows + size_t(ib.row) * (a.dense_wp ? a.dense_wp : kTabW);
+  const uint32_t* rowtab = a.rows + size_t(a.s_row[p]) * (a.dense_wp ? a.dense_wp : kTabW);
   const uint32_t any_mask = conflict_classes(cb, false) | conflict_classes(cb, true);
   uint32_t tests = 0;
   for (uint32_t q = 0; q < 4; ++q) {
@@ -521,7 +529,7 @@ __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cn
       if (!latest) continue;
       ++tests;
       const uint32_t ai = a.idx[pos];
-      const uint32_t na = a.info[ai].epoch;
+      const uint32_t na = a.s_ep[pos];
       uint32_t cv;
       if (a.dense_wp) {
         cv = __ldg(rowtab + v);
@@ -619,7 +627,8 @@ void phaseI_wide_group(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStrea
   k_wc_runflags<<<nblk(n, 256), 256, 0, s>>>(b.acc_key, n, b.wc_flag);
   count_launch();
   scan_exclusive(b.wc_flag, b.wc_run, n, b.wc_run + n, tmp, s);
-  k_wc_compose<<<nblk(n, 256), 256, 0, s>>>(b.wc_run, b.wc_flag, b.acc_idx, b.acc_info, n, b.wc_key, b.wc_val);
+  k_wc_compose<<<nblk(n, 256), 256, 0, s>>>(b.wc_run, b.wc_flag, b.acc_idx, b.acc_info, n, b.wc_key, b.wc_val,
+                                            b.wc_who, b.wc_row, b.wc_ep);
   count_launch();
   // runs < n <= 2^30: key bits 15 .. 15 + ceil(log2 n); class bits 13-14; agent bits below
   // 13, of which only ceil(log2 W) vary
@@ -660,6 +669,9 @@ void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t
   a.grp_agent = b.wc_grp_agent;
   a.rc_off = b.wc_rc;
   a.info = b.acc_info;
+  a.s_who = b.wc_who;
+  a.s_row = b.wc_row;
+  a.s_ep = b.wc_ep;
   a.rows = b.rows;
   a.tiles = b.tiles;
   a.tile_cap = z.tile_cap;

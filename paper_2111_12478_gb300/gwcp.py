@@ -225,9 +225,19 @@ class Context:
         if rc:
             raise GwcpError(rc, "gwcp_compute_order")
 
-    def report_races(self, stream=None, cap: int | None = None) -> np.ndarray:
-        """Returns races as a (k, 2) uint64 array of (earlier, later), sorted by (later, earlier)."""
+    def report_races(self, stream=None, cap: int | None = None, out: np.ndarray | None = None) -> np.ndarray:
+        """Returns races as a (k, 2) uint64 array of (earlier, later), sorted by (later, earlier).
+        out: a reusable (cap, 2) uint64 host array to write into (e.g. a view of pinned memory,
+        which makes the device-to-host copy a single DMA); the result is a view of it."""
         n = ctypes.c_uint64(0)
+        if out is not None:
+            if out.dtype != np.uint64 or out.ndim != 2 or out.shape[1] != 2 or not out.flags.c_contiguous:
+                raise ValueError("out must be a C-contiguous (cap, 2) uint64 array")
+            rc = self._L.gwcp_report_races(self._h, out.ctypes.data_as(ctypes.c_void_p), out.shape[0],
+                                           ctypes.byref(n), _stream_ptr(stream))
+            if rc:
+                raise GwcpError(rc, "gwcp_report_races")
+            return out[: n.value]
         if cap is None:
             rc = self._L.gwcp_report_races(self._h, None, 0, ctypes.byref(n), _stream_ptr(stream))
             if rc not in (GWCP_OK, ERR_CAPACITY) or (rc == ERR_CAPACITY and n.value == 0):
