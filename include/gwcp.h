@@ -175,6 +175,14 @@ int gwcp_set_clock_mode(gwcp_ctx* ctx, uint32_t mode);
 enum { GWCP_CHECK_AUTO = 0, GWCP_CHECK_CHUNKED = 1, GWCP_CHECK_SPARSE = 2 };
 int gwcp_set_check_mode(gwcp_ctx* ctx, uint32_t mode);
 
+/* Test hook of failure detection. Every device wait of the analysis (a clock row or
+ * barrier count that another walker has not published yet) is bounded: after its poll
+ * limit it records GWCP_ERR_TIMEOUT and the walker carries on, so the kernel ends and the
+ * context stays usable. This runs that wait in one warp on `device` against a row that
+ * nothing ever completes, with `spin_limit` polls; *status receives the kernel's status
+ * (GWCP_ERR_TIMEOUT). Synchronous; allocates and frees a small buffer. */
+int gwcp_debug_wait_timeout(int device, uint32_t spin_limit, int* status);
+
 /* Index of the first event that violates W1-W4 after GWCP_ERR_INVALID_TRACE. */
 uint64_t gwcp_first_bad_index(const gwcp_ctx* ctx);
 

@@ -848,6 +848,13 @@ int gwcp_check_timeline(gwcp_ctx* c, uint64_t* start_ns, uint64_t* chunk_end_ns,
   return cap < c->n_chunks_timeline ? GWCP_ERR_CAPACITY : cuda_rc();
 }
 
+int gwcp_debug_wait_timeout(int device, uint32_t spin_limit, int* status) {
+  if (!status || spin_limit == 0) return GWCP_ERR_ARGS;
+  if (cudaSetDevice(device) != cudaSuccess) return GWCP_ERR_CUDA;
+  *status = GWCP_OK;
+  return wait_probe(spin_limit, status);
+}
+
 uint64_t gwcp_first_bad_index(const gwcp_ctx* c) { return c ? c->bad_index : ~0ull; }
 
 uint64_t gwcp_launch_count(void) { return gwcp::launch_count(); }

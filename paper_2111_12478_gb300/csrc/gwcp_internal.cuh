@@ -337,6 +337,8 @@ void phaseE_walk(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Pr
 void phaseF_incs(const Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, cudaStream_t s, Prof& p);
 void phaseF_walk(Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, cudaStream_t s, Prof& p);
 int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
+// failure detection test: the walkers' bounded wait on a row nothing completes
+int wait_probe(uint32_t limit, int* code);
 // access grouping; tmp is the sort scratch (it may run beside other work on stream s)
 void phaseH_sort(Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, uint32_t* tmp, cudaStream_t s, Prof& p);
 // per-chunk carries of the check (needs the sorted accesses and AccInfo, not the clocks)

@@ -133,14 +133,16 @@ __device__ __forceinline__ bool row_complete(const uint32_t (&y)[K]) {
   return __all_sync(0xffffffffu, ok);
 }
 
-// re-read from L2 until complete (bounded)
+// re-read from L2 until complete (bounded: after `limit` polls the wait gives up, sets
+// GWCP_ERR_TIMEOUT and the walker carries on)
 template <int K>
-__device__ __noinline__ void wait_row(const uint32_t* row, uint32_t (&y)[K], bool& abort, DevStatus* st) {
+__device__ __noinline__ void wait_row(const uint32_t* row, uint32_t (&y)[K], bool& abort, DevStatus* st,
+                                     uint32_t limit = kSpinLimit) {
   uint32_t it = 0;
   for (;;) {
     load_row<K>(row, y);
     if (row_complete<K>(y) || abort) return;
-    if (++it > kSpinLimit) {
+    if (++it > limit) {
       if ((threadIdx.x & 31) == 0) atomicCAS(&st->code, 0, GWCP_ERR_TIMEOUT);
       abort = true;
       return;
@@ -720,7 +722,34 @@ int launch_k(const PropArgs& a, uint32_t grid, uint32_t threads, size_t smem_xch
   return launch<K, 0, 1024>(a, grid, threads, smem_xchg, s);
 }
 
+// failure-detection test: one warp waits, with the walkers' bounded wait, on a clock row
+// that nothing completes
+__global__ void k_wait_probe(const uint32_t* row, DevStatus* st, uint32_t limit) {
+  uint32_t y[1];
+  bool abort = false;
+  wait_row<1>(row, y, abort, st, limit);
+}
+
 }  // namespace
+
+int wait_probe(uint32_t limit, int* code) {
+  // a 32-word row of SENTINEL words (never completed) and a status record
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, 256 + sizeof(DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    return GWCP_ERR_OOM;
+  }
+  auto* row = static_cast<uint32_t*>(mem);
+  auto* st = reinterpret_cast<DevStatus*>(static_cast<char*>(mem) + 256);
+  cudaMemset(row, 0xFF, 256);
+  cudaMemset(st, 0, sizeof(DevStatus));
+  k_wait_probe<<<1, 32>>>(row, st, limit);
+  count_launch();
+  int rc = cudaDeviceSynchronize() == cudaSuccess ? GWCP_OK : GWCP_ERR_CUDA;
+  if (!rc && cudaMemcpy(code, &st->code, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = GWCP_ERR_CUDA;
+  cudaFree(mem);
+  return rc;
+}
 
 int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   PropArgs a{};

@@ -24,7 +24,7 @@ EXPORTS = ("gwcp_create", "gwcp_load_trace", "gwcp_compute_order", "gwcp_report_
            "gwcp_pool_run_batch", "gwcp_pool_set_active_lanes", "gwcp_pool_autotune", "gwcp_pool_now",
            "gwcp_pool_device_bytes", "gwcp_pool_destroy", "gwcp_set_ranker", "gwcp_location_features",
            "gwcp_rank_scores", "gwcp_rank_grad", "gwcp_rank_train", "gwcp_check_timeline", "gwcp_set_clock_mode",
-           "gwcp_pool_clock_modes", "gwcp_set_check_mode")
+           "gwcp_pool_clock_modes", "gwcp_set_check_mode", "gwcp_debug_wait_timeout")
 CLOCKS_AUTO, CLOCKS_DENSE, CLOCKS_TILES = 0, 1, 2
 CHECK_AUTO, CHECK_CHUNKED, CHECK_SPARSE = 0, 1, 2
 
@@ -121,6 +121,8 @@ def load_library():
     L.gwcp_set_ranker.argtypes = [vp, vp]
     L.gwcp_pool_clock_modes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
     L.gwcp_pool_clock_modes.restype = i32
+    L.gwcp_debug_wait_timeout.argtypes = [i32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int)]
+    L.gwcp_debug_wait_timeout.restype = i32
     L.gwcp_set_check_mode.argtypes = [vp, ctypes.c_uint32]
     L.gwcp_set_check_mode.restype = i32
     L.gwcp_set_clock_mode.argtypes = [vp, ctypes.c_uint32]
@@ -339,6 +341,16 @@ class Context:
         keys = ("accesses", "sync_entries", "critical_sections", "in_section_accesses", "clock_versions",
                 "partner_tests", "loop_visits", "joins")
         return dict(zip(keys, [int(v) for v in a]))
+
+
+def debug_wait_timeout(device: int, spin_limit: int) -> int:
+    """Runs the analysis' bounded device wait on a row nothing completes; returns the kernel's
+    status (ERR_TIMEOUT when the wait gave up as it must)."""
+    st = ctypes.c_int(0)
+    rc = load_library().gwcp_debug_wait_timeout(device, spin_limit, ctypes.byref(st))
+    if rc:
+        raise GwcpError(rc, "gwcp_debug_wait_timeout")
+    return int(st.value)
 
 
 def rank_scores(theta, feat, stream=None):

@@ -323,6 +323,20 @@ def test_hb_only_variant(mode):
     assert n_more > 0  # GWCP predicts races that HB misses
 
 
+def test_bounded_wait_gives_up_and_device_stays_usable(ctx):
+    # failure detection without a fault: the walkers' bounded wait on a clock row that
+    # nothing completes gives up with a timeout status; the next analysis runs normally
+    import time
+
+    from paper_2111_12478_gb300 import gwcp
+
+    t0 = time.perf_counter()
+    assert gwcp.debug_wait_timeout(0, 20_000) == gwcp.ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 10
+    ev, geo, _ = TG.generate(2, workload="tiny_1blk_64thr_10k")
+    same(ctx, ev, geo)
+
+
 def test_device_input_and_stream(ctx):
     import torch
 
