@@ -256,11 +256,15 @@ def bench_served(args, local, torch, gwcp, tracegen, np, lanes):
             codes[rc] = codes.get(rc, 0) + 1
         th.join()
         lat = np.array([d - s for _, _, s, d in infos])
+        # a request's races reach the caller together, when the request completes
+        ttfr = np.array([d - s for _, n, s, d in infos if n > 0])
         span = max(d for *_, d in infos) - min(s for _, _, s, _ in infos)
         ok = sum(1 for rc, *_ in infos if rc == 0)
         return {"lanes": active, "value": float(lens.sum()) / span, "unit": "events/s",
                 "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                 "mean_latency_s": float(lat.mean()), "span_s": span, "requests_ok": ok,
+                "p50_time_to_first_race_s": float(np.percentile(ttfr, 50)) if len(ttfr) else None,
+                "p99_time_to_first_race_s": float(np.percentile(ttfr, 99)) if len(ttfr) else None,
                 "result_codes": {str(k): v for k, v in codes.items()},
                 "n_races": int(sum(n for _, n, _, _ in infos))}
 
@@ -346,9 +350,13 @@ def bench_configs(args, local, torch, gwcp, tracegen, np):
             from oracle import oracle
 
             k = prefix or len(ev)
+            t0 = time.perf_counter()
             want = oracle.run(ev[:k], *geo.astuple()).races
+            dt = time.perf_counter() - t0
             entry["race_set_vs_oracle"] = {"events_checked": k, "identical": bool(
                 np.array_equal(want, races[races[:, 1] < k]))}
+            entry["cpu_oracle"] = {"value": k / dt, "unit": "events/s", "cores": 1,
+                                   "sample": f"first {k} events" if prefix else "whole trace"}
         out[name] = entry
         del dev, ev
     return out
