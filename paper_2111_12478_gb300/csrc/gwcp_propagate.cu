@@ -316,6 +316,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_propagate(PropArgs a) {
         const bool second = p >= base + 32;
         const int src = int((p - base) & 31);
         const uint32_t t2 = __shfl_sync(0xffffffffu, second ? ea2.x : ea.x, src) & 0xFF;
+        if (t2 == P_BAR) {  // a barrier stages nothing: an empty group, header kind 0
+          if (lane == 0) (ring + (p % R) * SLOT)[SLOT - 4] = 0u;
+          cp_async_commit();
+          return;
+        }
         const uint32_t w2 = __shfl_sync(0xffffffffu, second ? ea2.w : ea.w, src);
         const uint32_t x0 = __shfl_sync(0xffffffffu, second ? eb2.x : eb.x, src);
         const uint32_t x1 = __shfl_sync(0xffffffffu, second ? eb2.y : eb.y, src);
