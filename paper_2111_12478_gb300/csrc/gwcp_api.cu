@@ -63,6 +63,8 @@ struct gwcp_ctx {
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t sync_ev = nullptr;  // options.blocking_sync: host waits sleep on this event
   cudaStream_t alloc_s = nullptr;  // stream that buffer (re)allocations are ordered on
+  void* stage_host = nullptr;       // pinned staging for race copies into pageable memory
+  cudaEvent_t stage_ev[2] = {nullptr, nullptr};
   std::vector<float> rank_theta;  // gwcp_set_ranker: the MLP's parameters (empty = off)
   uint32_t clock_mode = GWCP_CLOCKS_AUTO;  // gwcp_set_clock_mode
   uint32_t check_mode = GWCP_CHECK_AUTO;   // gwcp_set_check_mode
@@ -107,6 +109,54 @@ void use_stream(gwcp_ctx* c, cudaStream_t s) {
     cudaStreamSynchronize(c->alloc_s);
     c->alloc_s = s;
   }
+}
+
+cudaError_t wait_stream(gwcp_ctx* c, cudaStream_t s);
+
+constexpr size_t kStageChunk = size_t(8) << 20;  // bytes per staging half
+
+// Device -> host copy of `bytes` into caller memory. Page-locked (or registered) memory
+// takes one DMA. Pageable memory goes through the context's own two pinned halves, chunk
+// by chunk (the next chunk's DMA overlaps the host copy of the previous one), instead of
+// the driver's shared staging path.
+int copy_to_host(gwcp_ctx* c, void* out, const void* dev, size_t bytes, cudaStream_t s) {
+  cudaPointerAttributes at{};
+  const bool pinned = cudaPointerGetAttributes(&at, out) == cudaSuccess &&
+                      (at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  if (pinned || bytes <= 65536) {
+    if (cudaMemcpyAsync(out, dev, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return GWCP_ERR_CUDA;
+    return wait_stream(c, s) == cudaSuccess ? GWCP_OK : GWCP_ERR_CUDA;
+  }
+  if (!c->stage_host) {
+    if (cudaMallocHost(&c->stage_host, 2 * kStageChunk) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->stage_ev[0], cudaEventDisableTiming | cudaEventBlockingSync) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->stage_ev[1], cudaEventDisableTiming | cudaEventBlockingSync) != cudaSuccess) {
+      cudaGetLastError();
+      if (c->stage_host) cudaFreeHost(c->stage_host);
+      c->stage_host = nullptr;
+      if (cudaMemcpyAsync(out, dev, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return GWCP_ERR_CUDA;
+      return wait_stream(c, s) == cudaSuccess ? GWCP_OK : GWCP_ERR_CUDA;
+    }
+  }
+  char* half[2] = {static_cast<char*>(c->stage_host), static_cast<char*>(c->stage_host) + kStageChunk};
+  const size_t n = (bytes + kStageChunk - 1) / kStageChunk;
+  for (size_t k = 0; k <= n; ++k) {
+    if (k < n) {  // DMA of chunk k into half k % 2
+      const size_t len = std::min(kStageChunk, bytes - k * kStageChunk);
+      if (cudaMemcpyAsync(half[k & 1], static_cast<const char*>(dev) + k * kStageChunk, len,
+                          cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaEventRecord(c->stage_ev[k & 1], s) != cudaSuccess)
+        return GWCP_ERR_CUDA;
+    }
+    if (k > 0) {  // host copy of chunk k - 1
+      const size_t j = k - 1;
+      const size_t len = std::min(kStageChunk, bytes - j * kStageChunk);
+      if (cudaEventSynchronize(c->stage_ev[j & 1]) != cudaSuccess) return GWCP_ERR_CUDA;
+      std::memcpy(static_cast<char*>(out) + j * kStageChunk, half[j & 1], len);
+    }
+  }
+  return GWCP_OK;
 }
 
 int cuda_rc() {
@@ -630,9 +680,8 @@ int gwcp_report_races(gwcp_ctx* c, gwcp_race* out, uint64_t cap, uint64_t* n_rac
     gwcp_race* dev = get<gwcp_race>(c, "races_out", m, &oom);
     if (oom) return GWCP_ERR_OOM;
     races_to_records(c->races_second ? c->b.races2 : c->b.races, m, dev, s);
-    if (cudaMemcpyAsync(out, dev, m * sizeof(gwcp_race), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        wait_stream(c, s) != cudaSuccess)
-      return GWCP_ERR_CUDA;
+    int rc = copy_to_host(c, out, dev, m * sizeof(gwcp_race), s);
+    if (rc) return rc;
   }
   // profile of this compute
   c->prof_ms.clear();
@@ -883,6 +932,9 @@ void gwcp_destroy(gwcp_ctx* c) {
   if (c->ev_own) cudaFreeAsync(c->ev_own, c->alloc_s);
   cudaStreamSynchronize(c->alloc_s);
   if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->stage_host) cudaFreeHost(c->stage_host);
+  for (auto e : c->stage_ev)
+    if (e) cudaEventDestroy(e);
   if (c->cnt_host) cudaFreeHost(c->cnt_host);
   for (auto e : c->prof.pool) cudaEventDestroy(e);
   if (c->fork) cudaEventDestroy(c->fork);

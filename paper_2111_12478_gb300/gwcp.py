@@ -492,17 +492,20 @@ class Pool:
         _, _, out, cap = self._live.pop(ticket)
         return out[: min(info.n_races, cap)] if info.rc in (GWCP_OK, ERR_CAPACITY) else out[:0], info
 
-    def run_batch(self, traces, caps):
-        """traces: list of (events, geo); returns a list of (races, rc, n_races)."""
+    def run_batch(self, traces, caps, outs=None):
+        """traces: list of (events, geo); returns a list of (races, rc, n_races). outs: optional
+        reusable (>= cap, 2) uint64 arrays, one per trace, that the races are written into."""
         n = len(traces)
         descs = (TraceDesc * n)()
         keep = []
-        outs = []
+        if outs is None:
+            outs = [np.zeros((max(c, 1), 2), dtype=np.uint64) for c in caps]
         for i, (ev, geo) in enumerate(traces):
             d, k = _trace_desc(ev, geo)
             descs[i] = d
             keep.append(k)
-            outs.append(np.zeros((max(caps[i], 1), 2), dtype=np.uint64))
+            if outs[i].shape[0] < caps[i] or outs[i].dtype != np.uint64 or not outs[i].flags.c_contiguous:
+                raise ValueError("outs[i] must be a C-contiguous (>= cap, 2) uint64 array")
         optr = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
         cap = (ctypes.c_uint64 * n)(*caps)
         nr = (ctypes.c_uint64 * n)()
