@@ -230,6 +230,20 @@ def bench_served(args, local, torch, gwcp, tracegen, np, lanes):
     arr, wid, lens = tracegen.serve_requests(SEED, args.serve_requests, cfg["rate"], cfg["n_min"], cfg["n_max"],
                                             len(base))
     pool = gwcp.Pool(local, lanes=max(lanes, 1))
+    # result arrays are recycled, as a server would: a free list per power-of-two size
+    free, free_lock = {}, threading.Lock()
+
+    def take(rows):
+        k = 1 << max(10, int(rows - 1).bit_length())
+        with free_lock:
+            lst = free.get(k)
+            if lst:
+                return lst.pop()
+        return np.empty((k, 2), dtype=np.uint64)
+
+    def give(a):
+        with free_lock:
+            free.setdefault(a.shape[0], []).append(a)
 
     def schedule(active):
         pool.set_active_lanes(active)
@@ -238,6 +252,7 @@ def bench_served(args, local, torch, gwcp, tracegen, np, lanes):
         for i in big:
             pool.wait(pool.submit(pinned[wid[i]][: int(lens[i]) * 16], geos[wid[i]], 0))
         tickets = [None] * len(arr)
+        bufs = [None] * len(arr)
         start = pool.now() + 0.02
 
         def submit_all():
@@ -246,7 +261,9 @@ def bench_served(args, local, torch, gwcp, tracegen, np, lanes):
                 if dt > 0:
                     time.sleep(dt)
                 n = int(lens[i])
-                tickets[i] = pool.submit(pinned[wid[i]][: n * 16], geos[wid[i]], 3 * n + 1024)
+                buf = take(3 * n + 1024)
+                bufs[i] = buf
+                tickets[i] = pool.submit(pinned[wid[i]][: n * 16], geos[wid[i]], 3 * n + 1024, out=buf)
 
         th = threading.Thread(target=submit_all)
         th.start()
@@ -256,6 +273,8 @@ def bench_served(args, local, torch, gwcp, tracegen, np, lanes):
                 time.sleep(0.0005)
             races, info = pool.wait(tickets[i])
             infos.append((info.rc, info.n_races, info.t_submit, info.t_done))
+            give(bufs[i])
+            bufs[i] = None
         codes = {}
         for rc, *_ in infos:
             codes[rc] = codes.get(rc, 0) + 1

@@ -467,11 +467,15 @@ class Pool:
     def device_bytes(self) -> int:
         return int(self._L.gwcp_pool_device_bytes(self._h))
 
-    def submit(self, events, geo, cap: int) -> int:
+    def submit(self, events, geo, cap: int, out: np.ndarray | None = None) -> int:
         """Queues one trace (host numpy array, pinned host tensor or CUDA tensor); geo =
-        (num_agents, agents_per_block, granularity). Up to `cap` races are kept."""
+        (num_agents, agents_per_block, granularity). Up to `cap` races are kept, in `out`
+        (a reusable C-contiguous (>= cap, 2) uint64 array) when given."""
         d, keep = _trace_desc(events, geo)
-        out = np.zeros((max(cap, 1), 2), dtype=np.uint64)
+        if out is None:
+            out = np.zeros((max(cap, 1), 2), dtype=np.uint64)
+        elif out.dtype != np.uint64 or out.ndim != 2 or out.shape[0] < cap or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous (>= cap, 2) uint64 array")
         t = ctypes.c_uint64(0)
         rc = self._L.gwcp_pool_submit(self._h, ctypes.byref(d), out.ctypes.data_as(ctypes.c_void_p), cap,
                                       ctypes.byref(t))
