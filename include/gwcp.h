@@ -269,7 +269,9 @@ typedef struct {
 
 /* Trains theta (device, updated in place) with Adam on mini-batches of consecutive rows
  * (shuffle the rows beforehand); epoch_loss (host, may be NULL) receives the mean batch
- * loss of each epoch. Allocates its optimizer state for the call. Synchronous. */
+ * loss of each epoch. One epoch's kernel launches are captured once as a CUDA graph and
+ * replayed per epoch (the Adam step count lives on the device). Allocates its optimizer
+ * state for the call. Synchronous. */
 int gwcp_rank_train(float* theta, const float* feat, const float* labels, uint64_t n, const gwcp_train_options* o,
                     float* epoch_loss, void* cuda_stream);
 
@@ -363,7 +365,8 @@ uint64_t gwcp_pool_device_bytes(gwcp_pool* p);
  * waited for are dropped. */
 void gwcp_pool_destroy(gwcp_pool* p);
 
-/* Number of kernels this library has launched in this process, on any context. */
+/* Number of kernels this library has launched in this process, on any context (a kernel
+ * in a replayed CUDA graph counts once, when it was captured). */
 uint64_t gwcp_launch_count(void);
 
 void gwcp_destroy(gwcp_ctx* ctx);

@@ -851,29 +851,46 @@ int gwcp_rank_train(float* theta, const float* feat, const float* labels, uint64
                     float* epoch_loss, void* stream) {
   if (!theta || !o || !o->epochs || !o->batch || (n && (!feat || !labels)) || n > kMaxEvents) return GWCP_ERR_ARGS;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  float* buf = nullptr;  // m, v, grad, per-epoch loss
-  const size_t words = 3 * size_t(kRankParams) + o->epochs;
+  // optimizer state, gradient, loss accumulator, per-epoch losses, counters
+  float* buf = nullptr;
+  const size_t words = 3 * size_t(kRankParams) + 1 + o->epochs + 2;
   if (cudaMalloc(&buf, words * 4) != cudaSuccess) {
     cudaGetLastError();
     return GWCP_ERR_OOM;
   }
-  float *m = buf, *v = buf + kRankParams, *g = buf + 2 * kRankParams, *ls = buf + 3 * kRankParams;
+  float *m = buf, *v = buf + kRankParams, *g = buf + 2 * kRankParams, *acc = buf + 3 * kRankParams;
+  float* losses = acc + 1;
+  auto* ctr = reinterpret_cast<uint32_t*>(losses + o->epochs);
   cudaMemsetAsync(buf, 0, words * 4, s);
   int rc = GWCP_OK;
-  uint64_t t = 0;
-  const uint32_t nb = uint32_t((n + o->batch - 1) / o->batch);
-  for (uint32_t e = 0; e < o->epochs && !rc; ++e) {
-    for (uint32_t q = 0; q < nb && !rc; ++q) {
-      const uint32_t lo = q * o->batch, hi = uint32_t(std::min<uint64_t>(n, uint64_t(lo) + o->batch));
-      rc = rank_grad(theta, feat, labels, lo, hi, o->pos_weight, 1.0f / float(hi - lo) / float(nb), g, ls + e, s);
-      ++t;
-      const float c1 = float(1.0 / (1.0 - std::pow(0.9, double(t))));
-      const float c2 = float(1.0 / (1.0 - std::pow(0.999, double(t))));
-      rank_adam(theta, m, v, g, o->lr, c1, c2, s);
+  if (n) {
+    // one epoch's launches (a gradient and an Adam step per mini-batch) are captured once
+    // as a CUDA graph and replayed for every epoch; without capture they are launched
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int erc = rank_epoch(theta, feat, labels, uint32_t(n), o->batch, o->lr, o->pos_weight, m, v, g, acc,
+                                 losses, ctr, cs);
+      if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || erc ||
+          cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+        exec = nullptr;
     }
+    cudaGetLastError();
+    for (uint32_t e = 0; e < o->epochs && !rc; ++e) {
+      if (exec)
+        rc = cudaGraphLaunch(exec, s) == cudaSuccess ? GWCP_OK : GWCP_ERR_CUDA;
+      else
+        rc = rank_epoch(theta, feat, labels, uint32_t(n), o->batch, o->lr, o->pos_weight, m, v, g, acc, losses,
+                        ctr, s);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
   }
   if (!rc && epoch_loss &&
-      (cudaMemcpyAsync(epoch_loss, ls, size_t(o->epochs) * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess))
+      cudaMemcpyAsync(epoch_loss, losses, size_t(o->epochs) * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     rc = GWCP_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = GWCP_ERR_CUDA;
   cudaFree(buf);

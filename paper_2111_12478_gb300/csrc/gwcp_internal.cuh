@@ -372,6 +372,9 @@ void rank_order(const RankIn& in, const uint32_t* tmp, const float* score, uint6
 int rank_grad(const float* theta, const float* feat, const float* y, uint32_t lo, uint32_t hi, float pos_weight,
               float inv_b, float* grad, float* loss, cudaStream_t s);
 void rank_adam(float* theta, float* m, float* v, float* grad, float lr, float c1, float c2, cudaStream_t s);
+int rank_epoch(float* theta, const float* feat, const float* y, uint32_t n, uint32_t batch, float lr,
+               float pos_weight, float* m, float* v, float* grad, float* loss_acc, float* losses, uint32_t* ctr,
+               cudaStream_t s);
 // sorted race words (later << 32 | earlier) -> gwcp_race records (gwcp_check.cu)
 void races_to_records(const uint64_t* words, uint64_t n, gwcp_race* out, cudaStream_t s);
 // check timeline: per chunk the globaltimer at its end and its race count (optional)

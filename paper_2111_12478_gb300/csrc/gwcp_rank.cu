@@ -407,6 +407,31 @@ __global__ void k_adam(float* theta, float* m, float* v, float* grad, float lr, 
   grad[p] = 0.f;
 }
 
+// Adam with the step count in device memory (one epoch of steps is a replayable graph):
+// step t = *step + 1; bias corrections 1 / (1 - beta^t)
+__global__ void k_adam_dev(float* theta, float* m, float* v, float* grad, float lr, const uint32_t* step) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N_PARAMS) return;
+  const float t = float(*step + 1);
+  const float c1 = 1.f / (1.f - powf(0.9f, t)), c2 = 1.f / (1.f - powf(0.999f, t));
+  const float g = grad[p];
+  const float mm = 0.9f * m[p] + 0.1f * g;
+  const float vv = 0.999f * v[p] + 0.001f * g * g;
+  m[p] = mm;
+  v[p] = vv;
+  theta[p] -= lr * (mm * c1) / (sqrtf(vv * c2) + 1e-8f);
+  grad[p] = 0.f;
+}
+
+__global__ void k_step_inc(uint32_t* step) { ++*step; }
+
+// end of an epoch: its accumulated loss into losses[epoch], then the next epoch
+__global__ void k_epoch_end(float* loss_acc, float* losses, uint32_t* epoch) {
+  losses[*epoch] = *loss_acc;
+  *loss_acc = 0.f;
+  ++*epoch;
+}
+
 // ---- ranked order of the check --------------------------------------------------------
 
 // key = (16 bits of the score, high scores first) << 32 | location ordinal
@@ -514,6 +539,26 @@ int rank_grad(const float* theta, const float* feat, const float* y, uint32_t lo
               float inv_b, float* grad, float* loss, cudaStream_t s) {
   if (hi <= lo) return GWCP_OK;
   k_mlp_grad<<<nblk(hi - lo, 128), 128, 0, s>>>(theta, feat, y, lo, hi, pos_weight, inv_b, grad, loss);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? GWCP_OK : GWCP_ERR_CUDA;
+}
+
+// One epoch of training as launches on stream s: per batch the gradient, Adam and the
+// step count; then the epoch's loss. Counters: ctr[0] Adam steps, ctr[1] epochs.
+int rank_epoch(float* theta, const float* feat, const float* y, uint32_t n, uint32_t batch, float lr,
+               float pos_weight, float* m, float* v, float* grad, float* loss_acc, float* losses, uint32_t* ctr,
+               cudaStream_t s) {
+  const uint32_t nb = (n + batch - 1) / batch;
+  for (uint32_t q = 0; q < nb; ++q) {
+    const uint32_t lo = q * batch, hi = std::min(n, lo + batch);
+    int rc = rank_grad(theta, feat, y, lo, hi, pos_weight, 1.0f / float(hi - lo) / float(nb), grad, loss_acc, s);
+    if (rc) return rc;
+    k_adam_dev<<<nblk(N_PARAMS, 256), 256, 0, s>>>(theta, m, v, grad, lr, ctr);
+    count_launch();
+    k_step_inc<<<1, 1, 0, s>>>(ctr);
+    count_launch();
+  }
+  k_epoch_end<<<1, 1, 0, s>>>(loss_acc, losses, ctr + 1);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? GWCP_OK : GWCP_ERR_CUDA;
 }

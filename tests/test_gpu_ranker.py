@@ -84,8 +84,12 @@ def test_adam_steps_match_oracle(env):
     torch, gwcp, _ = env
     th, x, y = _rows(3, 2048)
     t = torch.from_numpy(th.copy()).cuda()
+    n0 = gwcp.launch_count()
     gwcp.rank_train(t, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), epochs=2, batch=2048, lr=1e-3,
                     pos_weight=3.0)
+    # one epoch (gradient, Adam, step count, epoch end) is captured once and replayed as a
+    # CUDA graph: its four kernels are counted once, not once per epoch
+    assert gwcp.launch_count() - n0 == 4
     want, m, v = th.astype(np.float64), np.zeros(R.N_PARAMS), np.zeros(R.N_PARAMS)
     for step in (1, 2):
         want, m, v = R.adam_step(want, m, v, R.grad(want, x, y, 3.0), step, 1e-3)
