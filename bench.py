@@ -188,6 +188,7 @@ def bench_batched(args, local, torch, gwcp, tracegen, np):
     pool = gwcp.Pool(local, lanes=args.lanes)
     items = list(zip(dev, geos))
     best, tune = pool.autotune(items[::8])
+    pack = pool.settings()[1]
     caps = [len(r) for r in ref]
     pool.run_batch(items, caps, outs)  # warm-up: lanes size their buffers
     times, got = [], None
@@ -209,7 +210,7 @@ def bench_batched(args, local, torch, gwcp, tracegen, np):
         exact = {"traces_checked": len(idx), "identical": bool(exact)}
     t_b = statistics.median(times)
     return {"workload": "512 traces, 10k-5M events (log-uniform), 64-4096 warps, 64-warp 10M-event op mix",
-            "traces": len(traces), "events": n_total, "lanes": best, "autotune_s": tune,
+            "traces": len(traces), "events": n_total, "lanes": best, "autotune_s": tune, "pack_walkers": pack,
             "value": n_total / t_b, "unit": "events/s", "s_per_batch": t_b, "batches_timed": len(times),
             "plain": {"value": n_total / t_plain, "s": t_plain, "path": "one context, traces in sequence"},
             "speedup_vs_plain": t_plain / t_b, "race_sets_identical_to_plain": identical,
@@ -217,7 +218,7 @@ def bench_batched(args, local, torch, gwcp, tracegen, np):
             "inputs": "device-resident", "timing": "wall clock, device synchronised on both sides"}
 
 
-def bench_served(args, local, torch, gwcp, tracegen, np, lanes):
+def bench_served(args, local, torch, gwcp, tracegen, np, lanes, pack=True):
     """The served workload: requests arriving as a Poisson process at 200/s, 10k-20M
     events each (prefixes of one 20M-event trace per width class, in pinned host memory,
     copied to the device by the pool), races copied back to host memory. The same arrival
@@ -229,7 +230,7 @@ def bench_served(args, local, torch, gwcp, tracegen, np, lanes):
     geos = [g.astuple() for _, g in base]
     arr, wid, lens = tracegen.serve_requests(SEED, args.serve_requests, cfg["rate"], cfg["n_min"], cfg["n_max"],
                                             len(base))
-    pool = gwcp.Pool(local, lanes=max(lanes, 1))
+    pool = gwcp.Pool(local, lanes=max(lanes, 1), pack_walkers=pack)
     # result arrays are recycled, as a server would: a free list per power-of-two size
     free, free_lock = {}, threading.Lock()
 
@@ -308,6 +309,7 @@ def bench_served(args, local, torch, gwcp, tracegen, np, lanes):
     arr, wid, lens = arr_full, wid_full, lens_full
     pool.close()
     return {"workload": f"Poisson {cfg['rate']:.0f} req/s, 10k-20M events (log-uniform), 64-4096 warps",
+            "pack_walkers": pack,
             "requests": len(arr), "offered_events_per_s": float(lens.sum()) / float(arr[-1]),
             **served, "plain": plain, "speedup_vs_plain": served["value"] / plain["value"],
             "at_60pct_capacity": sustainable,
@@ -627,7 +629,8 @@ def main():
             result["batched"] = b
         log(f"batched section done ({time.perf_counter() - T0:.1f} s)")
     if not args.no_served:
-        v = bench_served(args, local, torch, gwcp, tracegen, np, b["lanes"] if not args.no_batched else 16)
+        v = bench_served(args, local, torch, gwcp, tracegen, np, b["lanes"] if not args.no_batched else 16,
+                         b["pack_walkers"] if not args.no_batched else True)
         if result is not None:
             result["served"] = v
         log(f"served section done ({time.perf_counter() - T0:.1f} s)")

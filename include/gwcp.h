@@ -101,7 +101,9 @@ typedef struct {
                              against H_t (scoped happens-before of Algorithm 1's H clocks)
                              instead of C_t; C_t <= H_t, so it reports a subset of the
                              GWCP races (the predictable races are the difference) */
-  uint32_t reserved[2];
+  uint32_t pack_walkers;  /* 1 = tile-clock walkers run two CTAs per SM where they fit, which
+                             leaves SMs to other streams (fastest alone: 0) */
+  uint32_t reserved[1];
 } gwcp_options;
 
 typedef struct gwcp_ctx gwcp_ctx; /* opaque; owns all device memory it allocates */
@@ -302,7 +304,7 @@ typedef struct {
 
 typedef struct {
   uint32_t lanes;         /* worker lanes; 0 = 16. Active lanes start equal to this */
-  uint32_t reserved0;     /* must be 0 */
+  uint32_t pack_walkers;  /* as gwcp_options.pack_walkers, for every lane */
   uint64_t mem_budget;    /* device bytes the pool may hold; 0 = 85% of free memory at creation */
   uint64_t race_capacity; /* per lane, as gwcp_options.race_capacity */
   uint32_t reserved[4];   /* must be 0 */
@@ -348,8 +350,14 @@ int gwcp_pool_set_active_lanes(gwcp_pool* p, uint32_t active);
  * class (gwcp_pool_clock_modes). Then runs the n traces as one batch with each candidate
  * number of active lanes (1, 2, 4, 8, 12, 16, 24, 32, up to the pool's lanes), keeps the
  * fastest and returns it in *best (seconds per candidate in secs[], up to 8 entries, may
- * be NULL). Races are counted, not copied. */
+ * be NULL). Last, with that many lanes, runs the batch once more with the other setting
+ * of pack_walkers and keeps whichever was faster (gwcp_pool_settings). Races are counted,
+ * not copied. */
 int gwcp_pool_autotune(gwcp_pool* p, const gwcp_trace_desc* t, uint32_t n, uint32_t* best, double* secs);
+
+/* The pool's current settings: active lanes and whether tile walkers are packed two CTAs
+ * per SM (the autotuner's choices, or the creation options). Either pointer may be NULL. */
+int gwcp_pool_settings(const gwcp_pool* p, uint32_t* active_lanes, uint32_t* pack_walkers);
 
 /* The clock mode the pool uses per width class c = ceil(log2(num_agents)), c < 16
  * (GWCP_CLOCKS_AUTO where the autotuner has not chosen). */

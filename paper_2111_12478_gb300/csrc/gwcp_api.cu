@@ -189,6 +189,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   z = Sizes{};
   z.N = c->n;
   z.hb_only = c->opt.hb_only != 0;
+  z.pack_walkers = c->opt.pack_walkers != 0;
   z.sparse_check = g.nT || c->check_mode == GWCP_CHECK_SPARSE ||
                    (c->check_mode == GWCP_CHECK_AUTO && g.W >= kSparseCheckFromAgents);
   z.TA = g.Wp <= 256 ? 2048 : 8192;
@@ -522,6 +523,7 @@ size_t ctx_device_bytes(const gwcp_ctx* c) {
   for (auto& kv : c->allocs) t += kv.second.second;
   return t;
 }
+void ctx_set_pack_walkers(gwcp_ctx* c, bool pack) { c->opt.pack_walkers = pack ? 1u : 0u; }
 // false when the last compute found more races than the device race buffer holds
 bool ctx_races_complete(const gwcp_ctx* c) { return c->n_races <= c->z.race_cap; }
 // releases the cached buffers (the next compute allocates them again); the caller makes

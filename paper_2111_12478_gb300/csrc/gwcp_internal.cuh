@@ -306,6 +306,7 @@ struct Sizes {
   bool cta_barriers = false;  // every block fits one CTA of walkers
   bool hb_only = false;       // versions hold H_t: the check then tests scoped happens-before
   bool sparse_check = false;  // partner-group check (always with tile clocks)
+  bool pack_walkers = false;  // tile walkers: two CTAs per SM where they fit
   uint32_t n_timeline = 0;    // check timeline entries (chunks or check blocks)
 };
 

@@ -32,6 +32,7 @@ namespace gwcp {
 size_t ctx_device_bytes(const gwcp_ctx* c);
 void ctx_trim(gwcp_ctx* c);
 bool ctx_races_complete(const gwcp_ctx* c);
+void ctx_set_pack_walkers(gwcp_ctx* c, bool pack);
 }  // namespace gwcp
 
 using namespace gwcp;
@@ -84,6 +85,7 @@ struct gwcp_pool {
   bool exclusive = false;  // a lane retrying after running out of memory runs alone
   double bpe[kClasses];    // estimated device bytes per event, by width class
   uint32_t clock_mode[kClasses];  // clock representation per width class (autotuned)
+  bool pack = false;              // tile walkers two CTAs per SM (autotuned)
 };
 
 namespace {
@@ -132,6 +134,7 @@ bool trim_idle(gwcp_pool* p, size_t i, std::unique_lock<std::mutex>& lk) {
 void run_request(gwcp_pool* p, Lane& L, Request& r) {
   uint64_t nr = 0;
   gwcp_set_clock_mode(L.ctx, p->clock_mode[width_class(r.t.geo.num_agents)]);
+  ctx_set_pack_walkers(L.ctx, p->pack);
   int rc = gwcp_load_trace(L.ctx, r.t.ev, r.t.n, &r.t.geo, r.t.ev_is_device, L.s);
   if (!rc) rc = gwcp_compute_order(L.ctx, L.s);
   if (!rc) {
@@ -218,7 +221,7 @@ int gwcp_pool_create(gwcp_pool** out, int device, const gwcp_pool_options* opt) 
   *out = nullptr;
   gwcp_pool_options o{};
   if (opt) o = *opt;
-  if (o.reserved0 || o.reserved[0] || o.reserved[1] || o.reserved[2] || o.reserved[3]) return GWCP_ERR_ARGS;
+  if (o.pack_walkers > 1 || o.reserved[0] || o.reserved[1] || o.reserved[2] || o.reserved[3]) return GWCP_ERR_ARGS;
   if (o.lanes == 0) o.lanes = 16;
   if (o.lanes > 256) return GWCP_ERR_ARGS;
   int ndev = 0;
@@ -232,6 +235,7 @@ int gwcp_pool_create(gwcp_pool** out, int device, const gwcp_pool_options* opt) 
   p->opt = o;
   p->t0 = Clock::now();
   p->active = o.lanes;
+  p->pack = o.pack_walkers != 0;
   for (int c = 0; c < kClasses; ++c) {
     const double wp = double(std::min(1u << c, 1024u));
     p->bpe[c] = 256.0 + 0.05 * 4.0 * wp;  // raised by observation
@@ -251,6 +255,7 @@ int gwcp_pool_create(gwcp_pool** out, int device, const gwcp_pool_options* opt) 
   gwcp_options co{};
   co.race_capacity = o.race_capacity;
   co.blocking_sync = 1;
+  co.pack_walkers = o.pack_walkers ? 1 : 0;
   for (auto& L : p->lanes) {
     if (gwcp_create(&L.ctx, device, &co) != GWCP_OK ||
         cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking) != cudaSuccess) {
@@ -412,18 +417,11 @@ int gwcp_pool_autotune(gwcp_pool* p, const gwcp_trace_desc* t, uint32_t n, uint3
   std::vector<uint32_t> order(n);
   for (uint32_t i = 0; i < n; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return t[a].n > t[b].n; });
-  double best_s = 1e300;
-  uint32_t best_k = uint32_t(p->lanes.size());
-  for (int c = 0; c < 8; ++c) {
-    const uint32_t k = kCand[c];
-    if (k > p->lanes.size()) {
-      if (secs) secs[c] = 0;
-      continue;
-    }
+  // seconds for the traces as one batch with k active lanes (races counted)
+  auto time_batch = [&](uint32_t k, int* rc) {
     gwcp_pool_set_active_lanes(p, k);
     const double t0 = now_s(p);
     std::vector<uint64_t> tickets;
-    int rc = GWCP_OK;
     {
       std::lock_guard<std::mutex> lk(p->mu);
       for (uint32_t i : order) {
@@ -441,21 +439,42 @@ int gwcp_pool_autotune(gwcp_pool* p, const gwcp_trace_desc* t, uint32_t n, uint3
     for (uint64_t id : tickets) {
       gwcp_request_info info{};
       gwcp_pool_wait(p, id, 1, &info);
-      if (info.rc && !rc) rc = info.rc;
+      if (info.rc && !*rc) *rc = info.rc;
     }
-    const double dt = now_s(p) - t0;
+    return now_s(p) - t0;
+  };
+  double best_s = 1e300;
+  uint32_t best_k = uint32_t(p->lanes.size());
+  int rc = GWCP_OK;
+  for (int c = 0; c < 8 && !rc; ++c) {
+    const uint32_t k = kCand[c];
+    if (k > p->lanes.size()) {
+      if (secs) secs[c] = 0;
+      continue;
+    }
+    const double dt = time_batch(k, &rc);
     if (secs) secs[c] = dt;
-    if (rc) {
-      gwcp_pool_set_active_lanes(p, best_k);
-      return rc;
-    }
     if (dt < best_s) {
       best_s = dt;
       best_k = k;
     }
   }
+  if (!rc) {  // tile walkers packed two CTAs per SM, or one: keep the faster
+    const bool first = p->pack;
+    p->pack = !first;
+    const double dt = time_batch(best_k, &rc);
+    if (dt >= best_s) p->pack = first;
+  }
   gwcp_pool_set_active_lanes(p, best_k);
+  if (rc) return rc;
   *best = best_k;
+  return GWCP_OK;
+}
+
+int gwcp_pool_settings(const gwcp_pool* p, uint32_t* active_lanes, uint32_t* pack_walkers) {
+  if (!p) return GWCP_ERR_ARGS;
+  if (active_lanes) *active_lanes = p->active;
+  if (pack_walkers) *pack_walkers = p->pack ? 1u : 0u;
   return GWCP_OK;
 }
 

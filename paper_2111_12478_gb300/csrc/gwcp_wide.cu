@@ -600,9 +600,12 @@ int phaseG_wide(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // the variant with the most registers whose CTAs are all co-resident
+  // the variant with the most registers whose CTAs are all co-resident; packed: two CTAs
+  // per SM first, which leaves SMs to other streams' kernels
   void* kern = nullptr;
-  for (void* k : {reinterpret_cast<void*>(k_prop_wide<1>), reinterpret_cast<void*>(k_prop_wide<2>)}) {
+  void* order[2] = {reinterpret_cast<void*>(k_prop_wide<1>), reinterpret_cast<void*>(k_prop_wide<2>)};
+  if (z.pack_walkers) std::swap(order[0], order[1]);
+  for (void* k : order) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, int(threads), smem) != cudaSuccess)
       return GWCP_ERR_CUDA;

@@ -24,7 +24,7 @@ EXPORTS = ("gwcp_create", "gwcp_load_trace", "gwcp_compute_order", "gwcp_report_
            "gwcp_pool_run_batch", "gwcp_pool_set_active_lanes", "gwcp_pool_autotune", "gwcp_pool_now",
            "gwcp_pool_device_bytes", "gwcp_pool_destroy", "gwcp_set_ranker", "gwcp_location_features",
            "gwcp_rank_scores", "gwcp_rank_grad", "gwcp_rank_train", "gwcp_check_timeline", "gwcp_set_clock_mode",
-           "gwcp_pool_clock_modes", "gwcp_set_check_mode", "gwcp_debug_wait_timeout")
+           "gwcp_pool_clock_modes", "gwcp_set_check_mode", "gwcp_debug_wait_timeout", "gwcp_pool_settings")
 CLOCKS_AUTO, CLOCKS_DENSE, CLOCKS_TILES = 0, 1, 2
 CHECK_AUTO, CHECK_CHUNKED, CHECK_SPARSE = 0, 1, 2
 
@@ -44,7 +44,7 @@ class Geometry(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("race_capacity", ctypes.c_uint64), ("profile", ctypes.c_uint32),
                 ("blocking_sync", ctypes.c_uint32), ("timeline", ctypes.c_uint32), ("hb_only", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("pack_walkers", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
 
 
 class TrainOptions(ctypes.Structure):
@@ -61,7 +61,7 @@ class TraceDesc(ctypes.Structure):
 
 
 class PoolOptions(ctypes.Structure):
-    _fields_ = [("lanes", ctypes.c_uint32), ("reserved0", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
+    _fields_ = [("lanes", ctypes.c_uint32), ("pack_walkers", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
                 ("race_capacity", ctypes.c_uint64), ("reserved", ctypes.c_uint32 * 4)]
 
 
@@ -119,6 +119,8 @@ def load_library():
         getattr(L, name).restype = i32
     fp = ctypes.POINTER(ctypes.c_float)
     L.gwcp_set_ranker.argtypes = [vp, vp]
+    L.gwcp_pool_settings.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]
+    L.gwcp_pool_settings.restype = i32
     L.gwcp_pool_clock_modes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
     L.gwcp_pool_clock_modes.restype = i32
     L.gwcp_debug_wait_timeout.argtypes = [i32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int)]
@@ -433,9 +435,10 @@ class Pool:
     """Batched and served analysis (gwcp_pool): lanes of contexts that run independent
     traces concurrently on one GPU, admitted by device memory."""
 
-    def __init__(self, device: int = 0, lanes: int = 16, mem_budget: int = 0, race_capacity: int = 0):
+    def __init__(self, device: int = 0, lanes: int = 16, mem_budget: int = 0, race_capacity: int = 0,
+                 pack_walkers: bool = True):
         L = load_library()
-        opt = PoolOptions(lanes, 0, mem_budget, race_capacity)
+        opt = PoolOptions(lanes, int(pack_walkers), mem_budget, race_capacity)
         h = ctypes.c_void_p()
         rc = L.gwcp_pool_create(ctypes.byref(h), device, ctypes.byref(opt))
         if rc:
@@ -538,6 +541,12 @@ class Pool:
             raise GwcpError(rc, "gwcp_pool_autotune")
         cand = (1, 2, 4, 8, 12, 16, 24, 32)
         return int(best.value), {c: float(secs[i]) for i, c in enumerate(cand) if secs[i] > 0}
+
+    def settings(self) -> tuple[int, bool]:
+        """(active lanes, tile walkers packed two CTAs per SM)."""
+        a, pk = ctypes.c_uint32(0), ctypes.c_uint32(0)
+        self._L.gwcp_pool_settings(self._h, ctypes.byref(a), ctypes.byref(pk))
+        return int(a.value), bool(pk.value)
 
     def clock_modes(self) -> dict:
         """Chosen clock mode per width class {ceil(log2(W)): mode} (modes other than AUTO)."""

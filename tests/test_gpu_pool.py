@@ -148,6 +148,7 @@ def test_autotune(gw, mix):
         best, secs = P.autotune([(ev, geo.astuple()) for ev, geo in traces])
         assert best in secs and set(secs) == {1, 2, 4, 8}
         assert secs[best] == min(secs.values())
+        assert P.settings()[0] == best  # (active lanes, packed walkers)
         # width classes 7..10 (128..1024 warps) hold only traces that take both clock
         # representations; class 6 also holds thread-granularity traces
         modes = P.clock_modes()
