@@ -8,7 +8,9 @@
 * closed forms (no synchronisation, all accesses under one device lock, barrier
   phases, blocks without device synchronisation);
 * invariants (H_t[t] = N_t, the one-entry epoch test equals the component-wise test,
-  HB-only races are a subset of GWCP races).
+  HB-only races are a subset of GWCP races);
+* FastTrack's detector, written independently, finds the first race on each location at
+  the same access as the oracle's race set.
 """
 import itertools
 
@@ -299,3 +301,42 @@ def test_clock_capture_invariants():
         mine = [i for i in idx if ev["agent"][i] == t and ev["op"][i] in (READ, WRITE, ATOMIC, ACQ, REL)]
         for a, c in itertools.pairwise(mine):
             assert (r.clocks_c[a] <= r.clocks_c[c]).all()
+
+
+def _location(ev, i, apb):
+    shared = int(ev["space"][i]) == 1
+    return (shared, int(ev["agent"][i]) // apb if shared else -1, int(ev["addr"][i]))
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_fasttrack_first_race_per_location(seed):
+    # FastTrack's detector (last write as an epoch, last reads per agent), written here from
+    # its published description and fed the oracle's clocks C_b, reports its first race on
+    # a location at the same access b as the earliest race (a*, b) of the oracle's reading
+    # of the race set on that location: before the first race every earlier conflicting
+    # access is ordered, so the last write (or reads) is unordered iff some earlier one is.
+    # Atomics are made plain writes so that no exemption is involved.
+    fam = TG.FAMILIES[seed % len(TG.FAMILIES)]
+    ev, geo = TG.random_small(seed, fam, n_events=160, num_agents=6, agents_per_block=3, n_locks=2, n_keys=4)
+    ev = ev.copy()
+    ev["op"][ev["op"] == ATOMIC] = WRITE
+    acc = [i for i in range(len(ev)) if ev["op"][i] in (READ, WRITE)]
+    r = O.run(ev, *geo.astuple(), clock_events=acc)
+    apb = geo.agents_per_block
+    W, R, first_ft = {}, {}, {}
+    for b in acc:
+        x, u, C = _location(ev, b, apb), int(ev["agent"][b]), r.clocks_c[b]
+        racy = x in W and W[x][1] != u and W[x][0] > C[W[x][1]]
+        if ev["op"][b] == WRITE:
+            racy |= any(v != u and e > C[v] for v, e in R.get(x, {}).items())
+            W[x] = (int(C[u]), u)
+            R[x] = {}
+        else:
+            R.setdefault(x, {})[u] = int(C[u])
+        if racy and x not in first_ft:
+            first_ft[x] = b
+    first_or = {}
+    for a, b in r.races.tolist():
+        x = _location(ev, b, apb)
+        first_or[x] = min(first_or.get(x, b), b)
+    assert first_ft == first_or
