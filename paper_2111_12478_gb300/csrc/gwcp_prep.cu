@@ -761,7 +761,7 @@ void phaseC_walk(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Pr
 }
 
 void phaseD_gaps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
-  p.begin("d_gaps", double(z.n_acc) * (4 + 16 + 16));
+  p.begin("d_gaps", double(z.n_acc) * (4 + 16 + 16), s);
   const uint64_t gaps = uint64_t(g.W) + z.n_sync;
   k_d_fill<<<blocks(gaps * 32, 256), 256, 0, s>>>(b.ev, g, z.n_sync, b.S, b.seg, b.sy_start, b.sy_spos, b.sy_N,
                                                   b.sy_depth, b.sy_ver, b.incs_cnt, b.vcount, b.acc_info, b.incs_idx,
