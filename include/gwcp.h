@@ -136,13 +136,18 @@ int gwcp_load_trace(gwcp_ctx* ctx, const gwcp_event* ev, uint64_t n, const gwcp_
  * critical-section annotation, clock propagation (Algorithms 1-2), access grouping, the
  * per-location race check and race compaction. Kernels are enqueued on cuda_stream; the
  * call synchronises that stream three times: twice to size its buffers from device-side
- * counts and once at the end for the status. Validation errors, a device-side timeout
- * (GWCP_ERR_TIMEOUT) and exhausted device memory (GWCP_ERR_OOM) are returned here and
- * again by gwcp_report_races. */
+ * counts and once at the end for the status (once more when the automatic race buffer
+ * grows and the check runs again; with tile clocks an exhausted tile pool is grown and
+ * the analysis run again). Buffers are allocated in stream order on cuda_stream from the
+ * device's default memory pool and kept for the next call. Validation errors, a
+ * device-side timeout (GWCP_ERR_TIMEOUT) and exhausted device memory (GWCP_ERR_OOM) are
+ * returned here and again by gwcp_report_races. */
 int gwcp_compute_order(gwcp_ctx* ctx, void* cuda_stream);
 
 /* Waits for the analysis on cuda_stream and copies up to `cap` races into host memory
- * `out` (may be NULL when cap is 0). *n_races receives the total number of races.
+ * `out` (may be NULL when cap is 0): one DMA into page-locked memory, or through the
+ * context's own pinned double buffer into pageable memory. *n_races receives the total
+ * number of races.
  * Returns GWCP_ERR_CAPACITY if cap < total, or if a fixed race_capacity was too small
  * (then *n_races is the count required; raise race_capacity and recompute). */
 int gwcp_report_races(gwcp_ctx* ctx, gwcp_race* out, uint64_t cap, uint64_t* n_races, void* cuda_stream);
