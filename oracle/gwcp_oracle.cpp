@@ -104,6 +104,9 @@ struct OracleOptions {
   int32_t release_scope_ieee;   // A2 alternative
   int32_t atomic_scope_lesser;  // A6 alternative
   int32_t hb_only;              // check against H_t instead of C_t
+  int32_t forced_barrier;       // forced compression at barriers (section "Vector Clock
+                                // Compression", second paragraph of its two ideas)
+  int32_t version_words;        // size every clock version in the block/warp compressed form
 };
 
 struct OracleResult {
@@ -114,6 +117,10 @@ struct OracleResult {
   uint64_t loop_visits = 0;           // release-loop record visits
   uint64_t partner_tests = 0;         // (b, v) pairs with a candidate a*
   uint64_t invariant_violations = 0;  // H_t[t] != N_t or a clock that went down
+  // option version_words: the clock versions (P_t, or H_t with hb_only, at the start and
+  // after each acquire, release, barrier and access made while holding a lock) and the
+  // words they take in the compressed form
+  uint64_t versions = 0, version_words = 0;
   // clocks captured at requested events
   std::vector<uint64_t> clock_events;
   std::vector<uint32_t> clock_c, clock_h;  // row-major [k][W]
@@ -290,6 +297,7 @@ class Analysis {
   }
 
   void run(const Event* ev, uint64_t n, const std::vector<int64_t>& want_clock) {
+    for (uint32_t t = 0; t < g_.W; ++t) version(t);
     for (uint64_t i = 0; i < n; ++i) {
       const Event& e = ev[i];
       switch (e.op) {
@@ -342,11 +350,23 @@ class Analysis {
 
   // Algorithm 1, procedure sync(scope): join the C and H clocks of every thread in
   // scope, give the joins to all of them, then increment (reading A3).
+  // Forced compression (option forced_barrier): after the join, the entries of the
+  // participants are all set to the highest of them, in both joined clocks, and so are
+  // the participants' local times; every participant leaves the barrier at the same
+  // logical time, so each one's clock holds one common value for the whole scope.
   void sync(const std::vector<uint32_t>& scope) {
     VC joined(g_.W, 0), joinedHB(g_.W, 0);
     for (uint32_t t : scope) {
       joinc(joined, C(t));
       joinc(joinedHB, H_[t]);
+    }
+    if (opt_.forced_barrier) {
+      uint32_t top = 0;
+      for (uint32_t t : scope) top = std::max({top, joined[t], joinedHB[t]});
+      for (uint32_t t : scope) {
+        joined[t] = joinedHB[t] = top;
+        N_[t] = top;
+      }
     }
     for (uint32_t t : scope) {
       P_[t] = joined;
@@ -356,6 +376,7 @@ class Analysis {
       N_[t] += 1;
       H_[t][t] += 1;
       check_invariant(t);
+      version(t);
     }
   }
 
@@ -384,6 +405,7 @@ class Analysis {
     rec.acqC = C(t);
     L.records.push_back(std::move(rec));
     held_[t].push_back(Held{l, sid, L.records.size() - 1, {}, {}});
+    version(t);
   }
 
   bool leq(const VC& a, const VC& b) const {
@@ -431,6 +453,7 @@ class Analysis {
     own.relH = H_[t];
     N_[t] += 1;
     H_[t][t] += 1;
+    version(t);
   }
 
   LClocks& lclk(uint64_t l, uint32_t sid, uint64_t x) {
@@ -465,6 +488,7 @@ class Analysis {
       }
     }
     for (Held& h : held_[u]) (write ? h.Wr : h.R).push_back(x);  // A11
+    if (!held_[u].empty()) version(u);
 
     const VC cb = opt_.hb_only ? H_[u] : C(u);
     const uint32_t bu = g_.block(u);
@@ -504,6 +528,38 @@ class Analysis {
       mine.idx = i;
       mine.epoch = N_[u];
     }
+  }
+
+  // Words of clock v in the compressed form of section "Vector Clock Compression": one
+  // word per block (its common value when all its entries are equal); an expanded block
+  // adds one word per warp (a warp is one agent at warp granularity, 32 threads at thread
+  // granularity), and a warp whose entries differ adds its 32 values.
+  uint64_t compressed_words(const VC& v) const {
+    const uint32_t gs = g_.gran == 1 ? 1 : 32;
+    const uint32_t nw = (g_.apb + gs - 1) / gs;
+    uint64_t words = g_.B;
+    for (uint32_t b = 0; b < g_.B; ++b) {
+      const uint32_t* x = v.data() + size_t(b) * g_.apb;
+      bool block_equal = true;
+      uint64_t extra = nw;
+      for (uint32_t w = 0; w < nw; ++w) {
+        const uint32_t lo = w * gs, hi = std::min(lo + gs, g_.apb);
+        bool warp_equal = true;
+        for (uint32_t i = lo; i < hi; ++i) {
+          if (x[i] != x[lo]) warp_equal = false;
+          if (x[i] != x[0]) block_equal = false;
+        }
+        if (!warp_equal) extra += 32;
+      }
+      if (!block_equal) words += extra;
+    }
+    return words;
+  }
+
+  void version(uint32_t t) {
+    if (!opt_.version_words) return;
+    res_->versions++;
+    res_->version_words += compressed_words(opt_.hb_only ? H_[t] : P_[t]);
   }
 
   void capture(size_t k, const Event& e) {
@@ -599,6 +655,10 @@ void oracle_counters(const OracleResult* r, uint64_t* out5) {
   out5[2] = r->loop_visits;
   out5[3] = r->partner_tests;
   out5[4] = r->invariant_violations;
+}
+void oracle_versions(const OracleResult* r, uint64_t* out2) {
+  out2[0] = r->versions;
+  out2[1] = r->version_words;
 }
 // Copies the captured clocks of the k-th requested event; returns 0 if captured.
 int oracle_clock(const OracleResult* r, uint64_t k, uint32_t* c_out, uint32_t* h_out) {

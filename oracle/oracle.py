@@ -30,7 +30,8 @@ class _Geometry(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("all_pairs", ctypes.c_int32), ("release_scope_ieee", ctypes.c_int32),
-                ("atomic_scope_lesser", ctypes.c_int32), ("hb_only", ctypes.c_int32)]
+                ("atomic_scope_lesser", ctypes.c_int32), ("hb_only", ctypes.c_int32),
+                ("forced_barrier", ctypes.c_int32), ("version_words", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -60,6 +61,7 @@ def lib():
         L.oracle_num_races.restype = u64
         L.oracle_copy_races.argtypes = [vp, pu64]
         L.oracle_counters.argtypes = [vp, pu64]
+        L.oracle_versions.argtypes = [vp, pu64]
         L.oracle_clock.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]
         L.oracle_clock.restype = ctypes.c_int
         L.oracle_free.argtypes = [vp]
@@ -97,10 +99,12 @@ def validate(events, num_agents: int, agents_per_block: int, granularity: int) -
 
 
 def run(events, num_agents: int, agents_per_block: int, granularity: int, *, all_pairs=False,
-        release_scope_ieee=False, atomic_scope_lesser=False, hb_only=False, clock_events=None) -> OracleRun:
+        release_scope_ieee=False, atomic_scope_lesser=False, hb_only=False, forced_barrier=False,
+        version_words=False, clock_events=None) -> OracleRun:
     a = _raw(events)
     g = _Geometry(num_agents, agents_per_block, granularity, 0)
-    o = _Options(int(all_pairs), int(release_scope_ieee), int(atomic_scope_lesser), int(hb_only))
+    o = _Options(int(all_pairs), int(release_scope_ieee), int(atomic_scope_lesser), int(hb_only),
+                 int(forced_barrier), int(version_words))
     ce = np.ascontiguousarray(np.asarray([] if clock_events is None else clock_events, dtype=np.uint64))
     handle = ctypes.c_void_p()
     bad = ctypes.c_uint64(0)
@@ -121,6 +125,10 @@ def run(events, num_agents: int, agents_per_block: int, granularity: int, *, all
         L.oracle_counters(handle, cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
         counters = dict(joins=int(cnt[0]), epoch_test_disagree=int(cnt[1]), loop_visits=int(cnt[2]),
                         partner_tests=int(cnt[3]), invariant_violations=int(cnt[4]))
+        if version_words:
+            vw = np.zeros(2, dtype=np.uint64)
+            L.oracle_versions(handle, vw.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+            counters.update(versions=int(vw[0]), version_words=int(vw[1]))
         out = OracleRun(races, counters)
         c = np.zeros(num_agents, dtype=np.uint32)
         h = np.zeros(num_agents, dtype=np.uint32)
