@@ -362,6 +362,57 @@ def bench_ranker(args, local, torch, gwcp, np, ev, geo, dev):
     return out
 
 
+def bench_compressed(args, local, torch, gwcp, np, geo, dev, races):
+    """The paper's memory mode on the main workload: forced compression at barriers and the
+    clock versions the check reads stored in block/warp compressed form. Reports the bytes
+    of the versions (dense, as stored, as reserved), the time per step and whether the race
+    set equals the dense run's."""
+    stream = torch.cuda.Stream(device=local)
+    n_ev = dev.numel() // 16
+
+    def measure(ctx):
+        ctx.load_trace(dev, *geo.astuple(), stream=stream)
+        for _ in range(max(2, args.warmup)):  # the first run sizes the version pool
+            ctx.compute_order(stream=stream)
+            ctx.race_count(stream=stream)
+        steps, prof = [], {}
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.compute_order(stream=stream)
+            e1.record(stream)
+            ctx.race_count(stream=stream)
+            steps.append(e0.elapsed_time(e1))
+            for name, ms_, _ in ctx.profile():
+                prof.setdefault(name, []).append(ms_)
+        ms = float(np.median(steps))
+        out = {"ms_per_step": ms, "events_per_s": n_ev / (ms / 1e3),
+               "phases_ms": {k: round(float(np.median(v)), 4) for k, v in prof.items()
+                             if k in ("c_forced", "g_propagate", "i_check")},
+               "race_set_identical_to_dense": bool(np.array_equal(ctx.report_races(stream=stream), races)),
+               "counters": {k: v for k, v in ctx.counters().items() if k in ("loop_visits", "joins", "clock_versions")}}
+        return out
+
+    plain = gwcp.Context(local, profile=True)
+    plain.set_clock_mode(gwcp.CLOCKS_DENSE)
+    out_plain = measure(plain)
+    plain.close()
+    forced = gwcp.Context(local, profile=True, forced_barrier=True)
+    forced.set_clock_mode(gwcp.CLOCKS_DENSE)
+    out_forced = measure(forced)
+    forced.close()
+    ctx = gwcp.Context(local, profile=True)
+    ctx.set_clock_mode(gwcp.CLOCKS_COMPRESSED)
+    out = measure(ctx)
+    cb = ctx.clock_bytes()
+    ctx.close()
+    out.update({"version_bytes": cb, "stored_over_dense": cb["stored"] / cb["dense"],
+                "reserved_over_dense": cb["reserved"] / cb["dense"], "forced_barrier_dense": out_forced, "dense": out_plain,
+                "note": "clock versions only; release snapshots stay dense"})
+    return out
+
+
 def bench_configs(args, local, torch, gwcp, tracegen, np):
     """The other single-trace workloads, one entry each: events/s of the whole analysis over
     the device-resident trace (CUDA events on the launching stream; inputs larger than L2
@@ -448,6 +499,7 @@ def main():
                     "(profiling runs); 0 = the full workload")
     ap.add_argument("--workload", default=WORKLOAD, help="a trace shape of tracegen.WORKLOADS")
     ap.add_argument("--no-ranker", action="store_true", help="skip the ranked-check measurement")
+    ap.add_argument("--no-compressed", action="store_true", help="skip the compressed-versions measurement")
     ap.add_argument("--no-configs", action="store_true", help="skip the tiny and 8192-warp workloads")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (512-trace) measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson arrivals) measurement")
@@ -621,6 +673,9 @@ def main():
     if rank == 0 and not args.no_ranker:
         result["ranker"] = bench_ranker(args, local, torch, gwcp, np, ev, geo, dev)
         log(f"ranker section done ({time.perf_counter() - T0:.1f} s)")
+    if rank == 0 and not args.no_compressed:
+        result["compressed"] = bench_compressed(args, local, torch, gwcp, np, geo, dev, races.copy())
+        log(f"compressed section done ({time.perf_counter() - T0:.1f} s)")
     ctx.close()
     ctx_e2e.close()
     del dev, pinned

@@ -103,7 +103,12 @@ typedef struct {
                              GWCP races (the predictable races are the difference) */
   uint32_t pack_walkers;  /* 1 = tile-clock walkers run two CTAs per SM where they fit, which
                              leaves SMs to other streams (fastest alone: 0) */
-  uint32_t reserved[1];
+  uint32_t forced_barrier; /* 1 = forced compression at barriers (section "Vector Clock
+                             Compression"): every member of a barrier leaves it at the same
+                             local time, the highest N_t among the members, so after the join
+                             each member's clock holds one common value for all members.
+                             Local times (and the clocks gwcp_debug_clock shows) change; the
+                             race set does not. Always on with GWCP_CLOCKS_COMPRESSED */
 } gwcp_options;
 
 typedef struct gwcp_ctx gwcp_ctx; /* opaque; owns all device memory it allocates */
@@ -158,16 +163,22 @@ int gwcp_report_races(gwcp_ctx* ctx, gwcp_race* out, uint64_t cap, uint64_t* n_r
  * published by a release (GWCP_ERR_UNSUPPORTED for other events). Synchronous. */
 int gwcp_debug_clock(gwcp_ctx* ctx, uint64_t event_idx, int which, uint32_t* out_W);
 
-/* How clocks are held (the representation only; results are identical):
+/* How clocks are held (the representation only; the race set is identical):
  * GWCP_CLOCKS_DENSE: every clock a row of W words, held in registers by the walker
  *   (num_agents <= 1024; wider traces still use tiles);
  * GWCP_CLOCKS_TILES: clocks as tables of copy-on-write 256-entry tiles (warp granularity,
  *   agents_per_block <= 32, num_agents <= 8192);
+ * GWCP_CLOCKS_COMPRESSED: the paper's memory mode (section "Vector Clock Compression"):
+ *   the dense walker with forced compression at barriers (options.forced_barrier), and
+ *   every clock version the check reads stored in block/warp compressed form - one word
+ *   per block when all its entries are equal, else one word per warp (equal entries) or
+ *   the warp's 32 values. Release snapshots stay dense. num_agents <= 1024; the check is
+ *   the sparse one. gwcp_clock_bytes reports the saving;
  * GWCP_CLOCKS_AUTO (default): tiles from 512 agents on where the trace allows them, else
  *   dense (the two cross near 512 agents on GB300).
  * Applies from the next gwcp_load_trace, which returns GWCP_ERR_UNSUPPORTED when the trace
  * does not allow the requested representation. */
-enum { GWCP_CLOCKS_AUTO = 0, GWCP_CLOCKS_DENSE = 1, GWCP_CLOCKS_TILES = 2 };
+enum { GWCP_CLOCKS_AUTO = 0, GWCP_CLOCKS_DENSE = 1, GWCP_CLOCKS_TILES = 2, GWCP_CLOCKS_COMPRESSED = 3 };
 int gwcp_set_clock_mode(gwcp_ctx* ctx, uint32_t mode);
 
 /* How the per-location check visits partners (results are identical):
@@ -198,6 +209,13 @@ uint64_t gwcp_first_bad_index(const gwcp_ctx* ctx);
  * stream), and the algorithmic bytes it must move (per the kernel's roofline model).
  * Returns GWCP_ERR_ARGS when i is past the end. */
 int gwcp_profile_get(const gwcp_ctx* ctx, int i, const char** name, float* ms, double* bytes);
+
+/* Storage of the clock versions of the last compute (the rows the check reads, one per
+ * agent and clock-changing step), in bytes: [0] as dense rows of W words (W rounded up to
+ * 32 * 2^k), [1] as stored (compressed: headers and written pool words; tiles: tables and
+ * tiles handed out; dense: = [0]), [2] as reserved (compressed: headers and the pool
+ * chunks the walkers took). Release snapshots are not included. */
+int gwcp_clock_bytes(const gwcp_ctx* ctx, uint64_t* out3);
 
 /* Counters of the last compute: [0] accesses, [1] sync entries (acquire, release and
  * barrier participations), [2] critical sections, [3] in-section accesses, [4] clock

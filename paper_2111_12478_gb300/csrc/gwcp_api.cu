@@ -58,7 +58,10 @@ struct gwcp_ctx {
   uint64_t n_races = 0;
   unsigned long long bad_index = ~0ull;
   uint64_t counters[8] = {};
+  uint64_t clock_words[3] = {};  // last compute: tiles, pool words taken, words written
   uint64_t tile_cap_hint = 0;  // wide clocks: pool size that the last run needed
+  bool compressed = false;     // GWCP_CLOCKS_COMPRESSED was in force at gwcp_load_trace
+  uint64_t cv_cap_hint = 0;    // compressed versions: pool words that the last run needed
   cudaStream_t side = nullptr;  // runs the access grouping beside the propagation
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t sync_ev = nullptr;  // options.blocking_sync: host waits sleep on this event
@@ -77,7 +80,8 @@ struct gwcp_ctx {
 namespace {
 
 const uint32_t kNoneHost = 0xFFFFFFFFu;
-const int kRerun = 1;  // run() result: the tile pool was grown, run again
+const int kRerun = 1;  // run() result: the tile or compressed-version pool was grown, run again
+const uint64_t kCvMaxWords = (1ull << 31) - 1;  // compressed-version offsets have 31 bits
 
 // Buffers come from the device's default memory pool, allocated and freed in stream
 // order on the context's current stream (c->alloc_s): growing a buffer neither waits for
@@ -190,7 +194,9 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   z.N = c->n;
   z.hb_only = c->opt.hb_only != 0;
   z.pack_walkers = c->opt.pack_walkers != 0;
-  z.sparse_check = g.nT || c->check_mode == GWCP_CHECK_SPARSE ||
+  z.compress = c->compressed && !g.nT;
+  z.forced_barrier = c->opt.forced_barrier != 0 || z.compress;
+  z.sparse_check = g.nT || z.compress || c->check_mode == GWCP_CHECK_SPARSE ||
                    (c->check_mode == GWCP_CHECK_AUTO && g.W >= kSparseCheckFromAgents);
   z.TA = g.Wp <= 256 ? 2048 : 8192;
   while (uint64_t(g.W) * ((z.N + z.TA - 1) / z.TA) > (1ull << 26)) z.TA <<= 1;  // bounded agent histogram
@@ -239,6 +245,8 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   b.acc_idx = get<uint32_t>(c, "acc_idx", z.n_acc, &oom);
   b.acc_key2 = get<uint64_t>(c, "acc_key2", z.n_acc, &oom);
   b.acc_idx2 = get<uint32_t>(c, "acc_idx2", z.n_acc, &oom);
+  // compressed versions keep local times in 31 bits; a local time is at most 1 + n_sync
+  if (z.compress && z.n_sync >= kCvExpanded - 1) return GWCP_ERR_UNSUPPORTED;
   const size_t ns1 = size_t(z.n_sync) + 1;
   b.sy_cnt = get<uint32_t>(c, "sy_cnt", z.nS / 4096 + 2, &oom);
   b.sy_spos = get<uint32_t>(c, "sy_spos", ns1, &oom);
@@ -274,6 +282,18 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   b.cs_parent = get<uint32_t>(c, "cs_parent", na1, &oom);
   b.acq_dep_off = get<uint32_t>(c, "acq_dep_off", na1, &oom);
   b.acq_dep_cnt = get<uint32_t>(c, "acq_dep_cnt", na1, &oom);
+  if (z.forced_barrier) {
+    const size_t nb1 = size_t(z.n_bar) + 1;
+    b.fb_key = get<uint64_t>(c, "fb_key", nb1, &oom);
+    b.fb_key2 = get<uint64_t>(c, "fb_key2", nb1, &oom);
+    b.fb_val = get<uint32_t>(c, "fb_val", nb1, &oom);
+    b.fb_val2 = get<uint32_t>(c, "fb_val2", nb1, &oom);
+    b.fb_rank = get<uint32_t>(c, "fb_rank", nb1, &oom);
+    b.fb_off = get<uint32_t>(c, "fb_off", nb1, &oom);
+    b.fb_blo = get<uint32_t>(c, "fb_blo", size_t(g.B) + 1, &oom);
+    b.fb_rec = get<uint4>(c, "fb_rec", ns1, &oom);
+    b.fb_boff = get<uint32_t>(c, "fb_boff", ns1, &oom);
+  }
   if (oom) return GWCP_ERR_OOM;
 
   phaseA_scatter(b, g, z, s, c->prof);
@@ -281,6 +301,9 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   cudaMemsetAsync(b.vcount, 0, size_t(g.W + 1) * 4, s);
   cudaMemsetAsync(b.cs_of_sync, 0xFF, ns1 * 4, s);
   phaseC_walk(b, g, z, s, c->prof);
+  // forced compression at barriers renumbers the local times; barriers are validated in
+  // phase A, so an invalid trace skips it
+  if (z.forced_barrier && code != GWCP_ERR_INVALID_TRACE) phaseC_forced(b, g, z, s, c->prof);
   phaseE_locks(b, g, z, lock_mask, s, c->prof);
   phaseE_scan(b, z, s, c->prof);
   {
@@ -335,7 +358,14 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   b.ex_group = get<uint32_t>(c, "ex_group", ne1 + 1, &oom);
   b.ex_dep_off = get<uint32_t>(c, "ex_dep_off", ne1, &oom);
   b.ex_dep_cnt = get<uint32_t>(c, "ex_dep_cnt", ne1, &oom);
-  b.rows = get<uint32_t>(c, "rows", size_t(z.n_rows) * g.RW, &oom);
+  b.rows = get<uint32_t>(c, "rows", size_t(z.n_rows) * (z.compress ? g.B : g.RW), &oom);
+  if (z.compress) {
+    // compressed versions: first sized at half a dense row per version plus every walker's
+    // chunk; later runs take what the last one needed; grown and rerun on exhaustion
+    const uint64_t want = uint64_t(z.n_rows) * (g.W / 2 + 1) + uint64_t(g.W) * kCvChunk + 65536;
+    z.cv_cap = std::min<uint64_t>(c->cv_cap_hint ? c->cv_cap_hint : want, kCvMaxWords);
+    b.cv_pool = get<uint32_t>(c, "cv_pool", z.cv_cap, &oom);
+  }
   b.psnap = get<uint32_t>(c, "psnap", (size_t(z.n_cs) + 1) * g.RW, &oom);
   b.hsnap = get<uint32_t>(c, "hsnap", (size_t(z.n_cs) + 1) * g.RW, &oom);
   if (g.nT) {
@@ -479,6 +509,18 @@ int run(gwcp_ctx* c, cudaStream_t s) {
     c->tile_cap_hint = 2 * z.tile_cap;  // the tile pool ran out: the caller runs again
     return kRerun;
   }
+  if (z.compress) {
+    // the walkers count every chunk they took, also past the end of the pool; the next run
+    // sizes the pool from the count (with room for the chunks' varying tails)
+    const uint64_t used = c->st_host->spare[3];
+    const uint64_t next = used + used / 8 + uint64_t(g.W) * kCvChunk;
+    if (used > z.cv_cap) {
+      if (z.cv_cap >= kCvMaxWords) return GWCP_ERR_UNSUPPORTED;
+      c->cv_cap_hint = next;
+      return kRerun;
+    }
+    c->cv_cap_hint = std::max(c->cv_cap_hint, next);
+  }
   if (code) return code;
   c->n_races = c->st_host->n_races;
   if (c->n_races > z.race_cap && c->opt.race_capacity == 0) {
@@ -511,6 +553,9 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   c->counters[5] = c->st_host->partner_tests;
   c->counters[6] = c->st_host->loop_visits;
   c->counters[7] = c->st_host->joins;
+  c->clock_words[0] = c->st_host->spare[2];  // tiles handed out
+  c->clock_words[1] = c->st_host->spare[3];  // compressed-version pool words handed out
+  c->clock_words[2] = c->st_host->spare[4];  // compressed-version words written
   return cuda_rc();
 }
 
@@ -594,6 +639,7 @@ int gwcp_load_trace(gwcp_ctx* c, const gwcp_event* ev, uint64_t n, const gwcp_ge
       geo->num_agents <= kMaxAgentsWide && geo->granularity == GWCP_GRAN_WARP && geo->agents_per_block <= 32;
   if (geo->num_agents > kMaxAgents && !tiles_ok) return GWCP_ERR_UNSUPPORTED;
   if (c->clock_mode == GWCP_CLOCKS_TILES && !tiles_ok) return GWCP_ERR_UNSUPPORTED;
+  if (c->clock_mode == GWCP_CLOCKS_COMPRESSED && geo->num_agents > kMaxAgents) return GWCP_ERR_UNSUPPORTED;
   // automatic: tiles from kTilesFromAgents agents on (measured faster from there on GB300)
   const bool tiles = geo->num_agents > kMaxAgents || c->clock_mode == GWCP_CLOCKS_TILES ||
                      (c->clock_mode == GWCP_CLOCKS_AUTO && tiles_ok && geo->num_agents >= kTilesFromAgents);
@@ -618,6 +664,7 @@ int gwcp_load_trace(gwcp_ctx* c, const gwcp_event* ev, uint64_t n, const gwcp_ge
     g.RW = kTabW;
   }
   c->g = g;
+  c->compressed = c->clock_mode == GWCP_CLOCKS_COMPRESSED;
   c->n = n;
   c->computed = false;
   c->compute_rc = GWCP_ERR_STATE;
@@ -652,7 +699,9 @@ int gwcp_compute_order(gwcp_ctx* c, void* stream) {
   if (c->n == 0) {
     c->computed = true;
     c->compute_rc = GWCP_OK;
+    c->z = Sizes{};
     std::memset(c->counters, 0, sizeof(c->counters));
+    std::memset(c->clock_words, 0, sizeof(c->clock_words));
     return GWCP_OK;
   }
   int rc = run(c, static_cast<cudaStream_t>(stream));
@@ -714,6 +763,42 @@ void read_clock(gwcp_ctx* c, const uint32_t* src, uint32_t* out) {
   for (uint32_t t = 0; t < g.nT; ++t)
     cudaMemcpy(out + size_t(t) * kTileW, c->b.tiles + size_t(ids[t]) * kTileW, kTileW * 4, cudaMemcpyDeviceToHost);
 }
+
+// clock version `row` into out[Wp]: a published clock, or a compressed version decoded
+// (header word per block, then warp words, then lane values)
+int read_version(gwcp_ctx* c, uint32_t row, uint32_t* out) {
+  const Geo& g = c->g;
+  if (!c->z.compress) {
+    read_clock(c, c->b.rows + size_t(row) * g.RW, out);
+    return GWCP_OK;
+  }
+  const uint32_t gs = cv_group(g.gran), nw = (g.apb + gs - 1) / gs;
+  std::vector<uint32_t> hdr(g.B), wv(nw), lanes(32);
+  cudaMemcpy(hdr.data(), c->b.rows + size_t(row) * g.B, size_t(g.B) * 4, cudaMemcpyDeviceToHost);
+  std::fill(out, out + g.Wp, 0u);
+  for (uint32_t b = 0; b < g.B; ++b) {
+    uint32_t* o = out + size_t(b) * g.apb;
+    if (!(hdr[b] & kCvExpanded)) {
+      std::fill(o, o + g.apb, hdr[b]);
+      continue;
+    }
+    const uint64_t at = hdr[b] & ~kCvExpanded;
+    if (at + nw > c->z.cv_cap) return GWCP_ERR_STATE;
+    cudaMemcpy(wv.data(), c->b.cv_pool + at, size_t(nw) * 4, cudaMemcpyDeviceToHost);
+    for (uint32_t w = 0; w < nw; ++w) {
+      const uint32_t lo = w * gs, hi = std::min(lo + gs, g.apb);
+      if (!(wv[w] & kCvExpanded)) {
+        std::fill(o + lo, o + hi, wv[w]);
+        continue;
+      }
+      const uint64_t at2 = wv[w] & ~kCvExpanded;
+      if (at2 + 32 > c->z.cv_cap) return GWCP_ERR_STATE;
+      cudaMemcpy(lanes.data(), c->b.cv_pool + at2, 32 * 4, cudaMemcpyDeviceToHost);
+      std::copy(lanes.begin(), lanes.begin() + (hi - lo), o + lo);
+    }
+  }
+  return GWCP_OK;
+}
 }  // namespace
 
 int gwcp_debug_clock(gwcp_ctx* c, uint64_t idx, int which, uint32_t* out) {
@@ -728,12 +813,12 @@ int gwcp_debug_clock(gwcp_ctx* c, uint64_t idx, int which, uint32_t* out) {
   cudaMemcpy(&e, c->ev_dev + idx, sizeof(e), cudaMemcpyDeviceToHost);
   std::vector<uint32_t> row(g.Wp);
   uint32_t own = 0;
-  const uint32_t* src = nullptr;
+  uint32_t version = kNoneHost;
   if (e.op <= GWCP_ATOMIC) {
     if (which != 0) return GWCP_ERR_UNSUPPORTED;
     AccInfo inf;
     cudaMemcpy(&inf, b.acc_info + idx, sizeof(inf), cudaMemcpyDeviceToHost);
-    src = b.rows + size_t(inf.row) * g.RW;
+    version = inf.row;
     own = inf.epoch;
   } else if (e.op == GWCP_ACQ || e.op == GWCP_REL) {
     uint32_t k0, k1;
@@ -751,7 +836,7 @@ int gwcp_debug_clock(gwcp_ctx* c, uint64_t idx, int which, uint32_t* out) {
     cudaMemcpy(&cs, b.cs_of_sync + k, 4, cudaMemcpyDeviceToHost);
     own = e.op == GWCP_REL ? N - 1 : N;
     if (which == 0) {
-      src = b.rows + size_t(rb + ver) * g.RW;
+      version = rb + ver;
     } else {
       if (e.op != GWCP_REL || cs == kNoneHost) return GWCP_ERR_UNSUPPORTED;
       read_clock(c, b.hsnap + size_t(cs) * g.RW, row.data());
@@ -761,10 +846,30 @@ int gwcp_debug_clock(gwcp_ctx* c, uint64_t idx, int which, uint32_t* out) {
   } else {
     return GWCP_ERR_UNSUPPORTED;
   }
-  read_clock(c, src, row.data());
+  const int rc = read_version(c, version, row.data());
+  if (rc) return rc;
   row[e.agent] = own;
   std::memcpy(out, row.data(), g.W * 4);
   return cuda_rc();
+}
+
+int gwcp_clock_bytes(const gwcp_ctx* c, uint64_t* out3) {
+  if (!c || !out3) return GWCP_ERR_ARGS;
+  if (!c->computed || c->compute_rc) return GWCP_ERR_STATE;
+  const Geo& g = c->g;
+  const Sizes& z = c->z;
+  const uint64_t rows = z.n_rows;
+  out3[0] = rows * g.Wp * 4;
+  if (z.compress) {
+    out3[1] = c->clock_words[2] * 4;
+    out3[2] = (rows * g.B + c->clock_words[1]) * 4;
+  } else if (g.nT) {
+    const uint64_t tiles = c->clock_words[0];  // handed out, including the zero tile
+    out3[1] = out3[2] = rows * kTabW * 4 + tiles * kTileW * 4;
+  } else {
+    out3[1] = out3[2] = out3[0];
+  }
+  return GWCP_OK;
 }
 
 int gwcp_set_check_mode(gwcp_ctx* c, uint32_t mode) {
@@ -774,7 +879,7 @@ int gwcp_set_check_mode(gwcp_ctx* c, uint32_t mode) {
 }
 
 int gwcp_set_clock_mode(gwcp_ctx* c, uint32_t mode) {
-  if (!c || mode > GWCP_CLOCKS_TILES) return GWCP_ERR_ARGS;
+  if (!c || mode > GWCP_CLOCKS_COMPRESSED) return GWCP_ERR_ARGS;
   c->clock_mode = mode;
   return GWCP_OK;
 }

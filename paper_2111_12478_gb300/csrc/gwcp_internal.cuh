@@ -152,7 +152,8 @@ struct Bufs {
   uint4* recmeta = nullptr;     // [n_cs + 1] (agent, acquire epoch, release index, scope id)
   uint32_t* flat_off = nullptr; // [n_incs + 1] dependency list of each in-section access
   uint32_t* flat = nullptr;     // [pool_cap]
-  uint32_t* rows = nullptr;     // [n_rows * RW]
+  uint32_t* rows = nullptr;     // [n_rows * RW], or [n_rows * B] headers of compressed versions
+  uint32_t* cv_pool = nullptr;  // compressed versions: [cv_cap] warp words and lane values
   uint32_t* psnap = nullptr;    // [n_cs * RW]
   uint32_t* hsnap = nullptr;    // [n_cs * RW]
   uint32_t* tiles = nullptr;    // wide clocks: [tile_cap * kTileW] tile pool, tile 0 = zeros
@@ -160,6 +161,14 @@ struct Bufs {
   uint32_t* cursor = nullptr;   // [W * n_locks]
   uint32_t* bar_j = nullptr;    // [n_bar * 2 * Wp] global-barrier joins
   uint32_t* bar_cnt = nullptr;  // [n_bar]
+  // forced compression at barriers: barriers by block, their members' records, offsets
+  uint64_t *fb_key = nullptr, *fb_key2 = nullptr;  // [n_bar]
+  uint32_t *fb_val = nullptr, *fb_val2 = nullptr;  // [n_bar]
+  uint32_t* fb_rank = nullptr;                     // [n_bar] barrier -> position by block
+  uint32_t* fb_off = nullptr;                      // [n_bar + 1] member counts, then offsets
+  uint32_t* fb_blo = nullptr;                      // [B + 1] each block's first position
+  uint4* fb_rec = nullptr;                         // [n_sync] (entry, N before, member, count)
+  uint32_t* fb_boff = nullptr;                     // [n_sync] offset from each barrier entry on
   // phase I: check
   uint32_t* tails = nullptr;    // [n_chunks * 4 * Wp * 2]
   // wide clocks: accesses regrouped by (location, class, agent)
@@ -293,6 +302,33 @@ __device__ __forceinline__ BarMembers barrier_members(const Event& e, const Geo&
 }
 
 // ---- launchers (defined in the phase files) -----------------------------------------
+// ---- compressed clock versions (section "Vector Clock Compression") ---------------
+// The paper's blockVC / warpVC form of a vector clock: one header word per block, holding
+// the block's common value (bit 31 clear) or kCvExpanded | the pool offset of the block's
+// warp words; a warp word holds the warp's common value or kCvExpanded | the pool offset
+// of its 32 lane values. At warp granularity a warp is one agent, so the warp words of an
+// expanded block are the agents' values. Values must stay below 2^31: every clock entry
+// is a local time, at most 1 + the number of synchronisation entries (forced compression
+// raises a local time only to another member's), which the host bounds.
+constexpr uint32_t kCvExpanded = 0x80000000u;
+constexpr uint32_t kCvChunk = 2048;  // pool words a walker takes at a time
+__host__ __device__ inline uint32_t cv_group(uint32_t gran) { return gran == GWCP_GRAN_WARP ? 1u : 32u; }
+
+// Entry v of the compressed version whose headers start at hdr; offsets at or past cap
+// (headers a failed walk left stale) read as zero.
+__device__ __forceinline__ uint32_t cv_entry(const uint32_t* hdr, const uint32_t* pool, unsigned long long cap,
+                                             uint32_t v, uint32_t apb, uint32_t gs) {
+  const uint32_t h = __ldg(hdr + v / apb);
+  if (!(h & kCvExpanded)) return h;
+  const uint32_t l = v % apb;
+  const unsigned long long o = (h & ~kCvExpanded) + l / gs;
+  if (o >= cap) return 0u;
+  const uint32_t w = __ldg(pool + o);
+  if (!(w & kCvExpanded)) return w;
+  const unsigned long long o2 = (w & ~kCvExpanded) + l % gs;
+  return o2 < cap ? __ldg(pool + o2) : 0u;
+}
+
 struct Sizes {
   uint64_t N = 0;
   uint32_t ntA = 0, TA = 0;
@@ -308,6 +344,9 @@ struct Sizes {
   bool sparse_check = false;  // partner-group check (always with tile clocks)
   bool pack_walkers = false;  // tile walkers: two CTAs per SM where they fit
   uint32_t n_timeline = 0;    // check timeline entries (chunks or check blocks)
+  bool forced_barrier = false;  // members leave a barrier at their highest local time
+  bool compress = false;        // clock versions in the block/warp compressed form
+  uint64_t cv_cap = 0;          // words of the compressed-version pool
 };
 
 // profiling hook: records an event pair around each launch when enabled
@@ -332,6 +371,7 @@ void phaseA_count(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, P
 void phaseA_scatter(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 void phaseB_sync(const Bufs& b, const Geo& g, Sizes& z, cudaStream_t s, Prof& p);
 void phaseC_walk(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
+void phaseC_forced(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 void phaseD_gaps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 void phaseE_locks(Bufs& b, const Geo& g, const Sizes& z, uint64_t lock_mask, cudaStream_t s, Prof& p);
 void phaseE_walk(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);

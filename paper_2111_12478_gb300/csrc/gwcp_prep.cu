@@ -434,6 +434,126 @@ __global__ void k_d_fill(const Event* ev, Geo g, uint32_t n_sync, const uint32_t
   }
 }
 
+// Phase C': forced compression at barriers (section "Vector Clock Compression"). Every
+// member leaves a barrier at the same local time, the highest N_t among the members; the
+// join then gives every member one common value for all members' entries. Local times are
+// the plain ones plus a per-agent offset that changes only at the agent's barriers. A
+// block's barriers involve only its own agents, so one warp per block walks them in trace
+// order: M = max over members of (N before + offset), then offset = M - N before.
+
+// barrier -> (its block, its trace-order position)
+__global__ void k_fb_keys(const Event* ev, Geo g, const uint32_t* bar, uint32_t n_bar, uint64_t* key,
+                          uint32_t* val) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_bar) return;
+  const Event e = ev[bar[i]];
+  key[i] = e.scope == GWCP_SCOPE_CTA ? uint32_t(e.addr) : e.agent / g.apb;
+  val[i] = i;
+}
+
+// position r of the block-sorted order: inverse map, member count, block starts
+__global__ void k_fb_rank(const Event* ev, Geo g, const uint32_t* bar, const uint64_t* skey, const uint32_t* spos,
+                          uint32_t n_bar, uint32_t* rank, uint32_t* cnt, uint32_t* blo) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > n_bar) return;
+  const uint32_t blk = r < n_bar ? uint32_t(skey[r]) : g.B;
+  const uint32_t prev = r > 0 ? uint32_t(skey[r - 1]) : 0u;
+  if (r == 0) {
+    for (uint32_t b = 0; b <= blk; ++b) blo[b] = 0;
+  } else {
+    for (uint32_t b = prev + 1; b <= blk; ++b) blo[b] = r;
+  }
+  if (r == n_bar) {
+    cnt[r] = 0;
+    return;
+  }
+  const uint32_t pos = spos[r];
+  rank[pos] = r;
+  cnt[r] = barrier_members(ev[bar[pos]], g).count;
+}
+
+// one record per barrier participation, grouped by barrier in block order
+__global__ void k_fb_records(const Event* ev, Geo g, uint32_t n_sync, uint32_t n_bar, const uint32_t* sy_start,
+                             const uint32_t* sy_kind, const uint32_t* sy_idx, const uint32_t* sy_aux,
+                             const uint32_t* sy_N, const uint32_t* rank, const uint32_t* off, uint4* rec) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_sync || sy_kind[k] != K_BAR) return;
+  const uint32_t u = lower_bound_dev(sy_start, g.W + 1, k + 1) - 1;  // last agent whose start <= k
+  const BarMembers m = barrier_members(ev[sy_idx[k]], g);
+  const uint32_t d = u - m.first, pos = sy_aux[k];
+  if (!m.ok || d >= (m.mask ? 32u : m.count) || pos >= n_bar) return;  // not on a validated trace
+  const uint32_t j = m.mask ? __popc(m.mask & ((1u << d) - 1u)) : d;
+  if (j < m.count) rec[off[rank[pos]] + j] = make_uint4(k, sy_N[k] - 1, u % g.apb, m.count);
+}
+
+constexpr uint32_t FB_STAGE = 1024;  // records staged in shared memory at a time
+
+__global__ void __launch_bounds__(32) k_fb_walk(Geo g, uint32_t n_sync, const uint32_t* blo, const uint32_t* off,
+                                                const uint4* rec, uint32_t* boff, DevStatus* st) {
+  __shared__ uint32_t off_s[1024];  // per member of the block (agents_per_block <= 1024)
+  __shared__ uint4 rec_s[FB_STAGE];
+  const uint32_t lane = threadIdx.x, b = blockIdx.x;
+  for (uint32_t j = lane; j < g.apb; j += 32) off_s[j] = 0;
+  const uint32_t pend = off[blo[b + 1]];
+  uint32_t p = off[blo[b]], lo = p, hi = p;
+  auto stage = [&](uint32_t at) {
+    __syncwarp();
+    lo = at;
+    hi = min(at + FB_STAGE, pend);
+    for (uint32_t i = lane; i < hi - lo; i += 32) rec_s[i] = rec[lo + i];
+    __syncwarp();
+  };
+  while (p < pend) {
+    if (p >= hi) stage(p);
+    const uint32_t c = rec_s[p - lo].w;
+    if (c == 0 || c > pend - p) {  // cannot happen on a validated trace
+      if (lane == 0) set_error(st, GWCP_ERR_INVALID_TRACE, 0);
+      return;
+    }
+    if (p + c > hi && c <= FB_STAGE) stage(p);
+    const bool staged = p + c <= hi;
+    uint32_t M = 0;
+    bool bad = false;
+    for (uint32_t j = lane; j < c; j += 32) {
+      const uint4 r = staged ? rec_s[p - lo + j] : rec[p + j];
+      bad |= r.z >= g.apb || r.x >= n_sync;
+      M = max(M, r.y + (r.z < g.apb ? off_s[r.z] : 0u));
+    }
+    M = __reduce_max_sync(0xffffffffu, M);
+    if (__any_sync(0xffffffffu, bad)) {  // a record left unwritten: not on a validated trace
+      if (lane == 0) set_error(st, GWCP_ERR_INVALID_TRACE, 0);
+      return;
+    }
+    for (uint32_t j = lane; j < c; j += 32) {
+      const uint4 r = staged ? rec_s[p - lo + j] : rec[p + j];
+      off_s[r.z] = M - r.y;
+      boff[r.x] = M - r.y;
+    }
+    __syncwarp();
+    p += c;
+  }
+}
+
+// N after each entry += the offset of the agent's latest barrier entry at or before it
+__global__ void k_fb_apply(Geo g, const uint32_t* sy_start, const uint32_t* boff, uint32_t* sy_N) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (u >= g.W) return;
+  const uint32_t k0 = sy_start[u], k1 = sy_start[u + 1];
+  const uint32_t le = (2u << lane) - 1u;
+  uint32_t carry = 0;
+  for (uint32_t kb = k0; kb < k1; kb += 32) {
+    const uint32_t k = kb + lane;
+    const bool valid = k < k1;
+    const uint32_t o = valid ? boff[k] : NONE;
+    const uint32_t set = __ballot_sync(0xffffffffu, valid && o != NONE);
+    const uint32_t m = set & le;
+    const uint32_t from = __shfl_sync(0xffffffffu, o, m ? 31 - __clz(m) : 0);
+    if (valid) sy_N[k] += m ? from : carry;
+    if (set) carry = __shfl_sync(0xffffffffu, o, 31 - __clz(set));
+  }
+}
+
 // Phase E
 __global__ void k_e_flags(const uint64_t* key, const uint32_t* kk, uint32_t n, const uint32_t* sy_kind,
                           uint32_t* is_acq, uint32_t* is_new) {
@@ -758,6 +878,32 @@ void phaseC_walk(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Pr
   p.end();
   scan_exclusive(b.incs_cnt, b.incs_cnt, z.n_sync + 1, nullptr, b.scan_tmp, s);
   scan_exclusive(b.vcount, b.vcount, g.W + 1, nullptr, b.scan_tmp, s);
+}
+
+void phaseC_forced(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
+  const uint32_t n = z.n_bar;
+  if (!n) return;
+  p.begin("c_forced", double(n) * 40 + double(z.n_sync) * 24);
+  k_fb_keys<<<blocks(n, 256), 256, 0, s>>>(b.ev, g, b.bar, n, b.fb_key, b.fb_val);
+  count_launch();
+  uint64_t mask = 0;
+  while (mask < g.B - 1) mask = (mask << 1) | 1;
+  const bool second = radix_sort_pairs(b.fb_key, b.fb_val, b.fb_key2, b.fb_val2, n, mask, b.scan_tmp, s);
+  const uint64_t* skey = second ? b.fb_key2 : b.fb_key;
+  const uint32_t* spos = second ? b.fb_val2 : b.fb_val;
+  k_fb_rank<<<blocks(uint64_t(n) + 1, 256), 256, 0, s>>>(b.ev, g, b.bar, skey, spos, n, b.fb_rank, b.fb_off,
+                                                          b.fb_blo);
+  count_launch();
+  scan_exclusive(b.fb_off, b.fb_off, size_t(n) + 1, nullptr, b.scan_tmp, s);
+  cudaMemsetAsync(b.fb_boff, 0xFF, size_t(z.n_sync + 1) * 4, s);
+  k_fb_records<<<blocks(z.n_sync, 256), 256, 0, s>>>(b.ev, g, z.n_sync, n, b.sy_start, b.sy_kind, b.sy_idx, b.sy_aux,
+                                                     b.sy_N, b.fb_rank, b.fb_off, b.fb_rec);
+  count_launch();
+  k_fb_walk<<<g.B, 32, 0, s>>>(g, z.n_sync, b.fb_blo, b.fb_off, b.fb_rec, b.fb_boff, b.st);
+  count_launch();
+  k_fb_apply<<<blocks(uint64_t(g.W) * 32, 128), 128, 0, s>>>(g, b.sy_start, b.fb_boff, b.sy_N);
+  count_launch();
+  p.end();
 }
 
 void phaseD_gaps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {

@@ -44,6 +44,11 @@ struct PropArgs {
   uint32_t *bar_j, *bar_cnt;
   uint32_t n_locks;
   int cta_barriers;
+  // compressed clock versions: rows holds B header words per version
+  uint32_t compress;
+  uint32_t* cv_pool;
+  unsigned long long cv_cap;
+  unsigned long long *cv_used, *cv_words;  // pool words handed out; words written
 };
 
 template <int K>
@@ -88,6 +93,123 @@ __device__ __forceinline__ void store_row_shared(uint32_t* row, const uint32_t (
   uint32_t* p = row + (threadIdx.x & 31) * K;
 #pragma unroll
   for (int j = 0; j < K; ++j) p[j] = x[j];
+}
+
+// Walker state of the compressed-version pool: the chunk being filled, words written.
+struct CvState {
+  unsigned long long cur, end, words;
+};
+
+// Stores the clock the warp left in `scratch` (its Wc shared words, entry e at e) as the
+// compressed version `row` (the blockVC / warpVC form): B header words at rows + row * B;
+// the words of expanded blocks go to the pool, from a chunk of kCvChunk words the walker
+// takes at a time. A version that does not fit the pool gets zero headers, and the host
+// runs again with a larger pool (cv_used keeps counting). Only the compressing walker
+// instantiations contain it.
+__device__ __forceinline__ CvState put_row_c(const PropArgs& a, uint32_t row, const uint32_t* scratch, CvState cs) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t apb = a.g.apb, nb = a.g.B, gs = cv_group(a.g.gran), nw = (apb + gs - 1) / gs;
+  // pass 1: which of the lane's blocks (b = lane + 32 i) are uniform, and the words the
+  // others need: nw warp words, plus 32 lane values per warp that is not uniform
+  uint32_t need = 0, umask = 0;
+  for (uint32_t b = lane, i = 0; b < nb; b += 32, ++i) {
+    const uint32_t* q = scratch + b * apb;
+    bool uni = true;
+    uint32_t ew = 0;
+    for (uint32_t w = 0; w < nw; ++w) {
+      const uint32_t lo = w * gs, hi = min(lo + gs, apb), v = q[lo];
+      bool wu = true;
+      for (uint32_t e = lo; e < hi; ++e) wu &= q[e] == v;
+      uni &= wu && v == q[0];
+      ew += wu ? 0u : 1u;
+    }
+    if (uni)
+      umask |= 1u << i;
+    else
+      need += nw + 32 * ew;
+  }
+  const uint32_t incl = warp_inclusive_scan(need);
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total && cs.cur + total > cs.end) {
+    unsigned long long base = 0;
+    const unsigned long long take = max(total, kCvChunk);
+    if (lane == 0) base = atomicAdd(a.cv_used, take);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    cs.cur = base;
+    cs.end = base + take;
+  }
+  unsigned long long o = cs.cur + (incl - need);
+  cs.cur += total;
+  cs.words += nb + total;
+  const bool fits = cs.cur <= a.cv_cap;  // the whole version lies inside the pool
+  uint32_t* hdr = a.rows + size_t(row) * nb;
+  // pass 2: headers, warp words and lane values
+  for (uint32_t b = lane, i = 0; b < nb; b += 32, ++i) {
+    const uint32_t* q = scratch + b * apb;
+    if ((umask >> i) & 1u) {
+      __stcg(hdr + b, q[0]);
+      continue;
+    }
+    if (!fits) {
+      __stcg(hdr + b, 0u);
+      continue;
+    }
+    __stcg(hdr + b, kCvExpanded | uint32_t(o));
+    unsigned long long o2 = o + nw;
+    for (uint32_t w = 0; w < nw; ++w) {
+      const uint32_t lo = w * gs, hi = min(lo + gs, apb), v = q[lo];
+      bool wu = true;
+      for (uint32_t e = lo; e < hi; ++e) wu &= q[e] == v;
+      if (wu) {
+        __stcg(a.cv_pool + o + w, v);
+      } else {
+        __stcg(a.cv_pool + o + w, kCvExpanded | uint32_t(o2));
+        for (uint32_t e = 0; e < 32; ++e) __stcg(a.cv_pool + o2 + e, lo + e < apb ? q[lo + e] : 0u);
+        o2 += 32;
+      }
+    }
+    o = o2;
+  }
+  __syncwarp();
+  return cs;
+}
+
+// The same store from registers, for warp granularity with K dividing agents_per_block:
+// a block is L = apb / K consecutive lanes, so its uniformity is one ballot and its
+// expanded words are the lanes' own entries (one per agent, in agent order).
+template <int K>
+__device__ __forceinline__ CvState put_row_lanes(const PropArgs& a, uint32_t row, const uint32_t (&x)[K], CvState cs) {
+  const uint32_t lane = threadIdx.x & 31, apb = a.g.apb, nb = a.g.B, L = apb / K;
+  const uint32_t grp = lane / L, first = grp * L;
+  const bool live = grp < nb;  // lanes past the last block hold padding
+  bool same = true;
+#pragma unroll
+  for (int j = 0; j < K; ++j) same &= x[j] == x[0];
+  const uint32_t head_v = __shfl_sync(0xffffffffu, x[0], live ? first : lane);
+  const uint32_t ok = __ballot_sync(0xffffffffu, live && same && x[0] == head_v);
+  const uint32_t gmask = live ? ((L == 32 ? 0xffffffffu : (1u << L) - 1u) << first) : 0u;
+  const bool uni = live && (ok & gmask) == gmask;
+  const bool head = live && lane == first;
+  const uint32_t expm = __ballot_sync(0xffffffffu, head && !uni);  // bit at each expanded block's first lane
+  const uint32_t total = __popc(expm) * apb;
+  if (total && cs.cur + total > cs.end) {
+    unsigned long long base = 0;
+    const unsigned long long take = max(total, kCvChunk);
+    if (lane == 0) base = atomicAdd(a.cv_used, take);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    cs.cur = base;
+    cs.end = base + take;
+  }
+  const unsigned long long o = cs.cur + (unsigned long long)apb * __popc(expm & ((1u << first) - 1u));
+  cs.cur += total;
+  cs.words += nb + total;
+  const bool fits = cs.cur <= a.cv_cap;
+  if (head) __stcg(a.rows + size_t(row) * nb + grp, uni ? x[0] : fits ? kCvExpanded | uint32_t(o) : 0u);
+  if (live && !uni && fits) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) __stcg(a.cv_pool + o + (lane - first) * K + j, x[j]);
+  }
+  return cs;
 }
 
 template <int K>
@@ -246,7 +368,9 @@ __host__ __device__ constexpr int slot_words() {
 // One warp per agent walks the agent's plan (its clock-changing steps in trace order).
 // R > 0: a ring of R shared-memory slots per warp; while entry p is processed, the
 // copies for entry p + R - 1 are in flight (one commit group per entry).
-template <int K, int R, int MAXT>
+// CV: clock versions stored compressed (a separate instantiation, so that the plain
+// walkers' register allocation does not carry it).
+template <int K, int R, int MAXT, bool CV>
 __global__ void __launch_bounds__(MAXT, 1) k_propagate(PropArgs a) {
   constexpr int Wc = 32 * K;
   constexpr int SLOT = slot_words<K>();
@@ -282,10 +406,31 @@ __global__ void __launch_bounds__(MAXT, 1) k_propagate(PropArgs a) {
   bool abort = false;
   uint64_t joins = 0, visits = 0;
   uint32_t nbar = 0;
-  if (a.hb_only)
-    store_row<K>(a.rows + size_t(a.rowbase[u]) * Wc, H);
-  else
-    store_row<K>(a.rows + size_t(a.rowbase[u]) * Wc, P);
+  CvState cvs{0, 0, 0};  // compressed versions
+  const bool cv_lanes = g.gran == GWCP_GRAN_WARP && g.apb % K == 0;
+  auto put_version = [&](uint32_t r) {
+    if constexpr (CV) {
+      if (cv_lanes) {
+        cvs = a.hb_only ? put_row_lanes<K>(a, r, H, cvs) : put_row_lanes<K>(a, r, P, cvs);
+        return;
+      }
+      // the clock goes through the warp's jn scratch words, which are then left holding jn
+      // (the release loop's rule: no word there exceeds jn)
+      if (a.hb_only)
+        store_row_shared<K>(jn_tmp, H);
+      else
+        store_row_shared<K>(jn_tmp, P);
+      __syncwarp();
+      cvs = put_row_c(a, r, jn_tmp, cvs);
+      store_row_shared<K>(jn_tmp, jn);
+      __syncwarp();
+    } else if (a.hb_only) {
+      store_row<K>(a.rows + size_t(r) * Wc, H);
+    } else {
+      store_row<K>(a.rows + size_t(r) * Wc, P);
+    }
+  };
+  put_version(a.rowbase[u]);
   const uint32_t k0 = a.sy_start[u], k1 = a.sy_start[u + 1];
   const uint32_t pb = k0 + a.incs_off[k0], pe = k1 + a.incs_off[k1];
   uint32_t* const cursor_row = a.cursor + size_t(u) * a.n_locks;
@@ -524,6 +669,13 @@ __global__ void __launch_bounds__(MAXT, 1) k_propagate(PropArgs a) {
     } else {
       // sync (Algorithm 1): join C_t and H_t over the barrier's scope
       const uint32_t mode = __shfl_sync(0xffffffffu, eb.x, i);
+      // the local time the agent enters the join with: N_t, or under forced compression
+      // at barriers the highest N among the members
+      const uint32_t Nb = __shfl_sync(0xffffffffu, eb.y, i);
+      if (Nb != N) {
+        N = Nb;
+        set_entry<K>(H, u, N);
+      }
       uint32_t C[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) C[j] = P[j];
@@ -583,10 +735,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_propagate(PropArgs a) {
       set_entry<K>(H, u, N + 1);
       ++N;
     }
-    if (a.hb_only)
-      store_row<K>(a.rows + size_t(row) * Wc, H);
-    else
-      store_row<K>(a.rows + size_t(row) * Wc, P);
+    put_version(row);
     if (i == 31) {  // next batch
       base += 32;
       ea = ea2;
@@ -599,6 +748,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_propagate(PropArgs a) {
   if (lane == 0) {
     atomicAdd(&a.st->joins, (unsigned long long)joins);
     atomicAdd(&a.st->loop_visits, (unsigned long long)visits);
+    if constexpr (CV) atomicAdd(a.cv_words, cvs.words);
   }
 }
 
@@ -672,6 +822,7 @@ __global__ void k_plan_sync(PropArgs a, const uint32_t* sy_kind_, const uint32_t
                                                                           : BAR_GLOBAL;
     ea = make_uint4(P_BAR, row, a.sy_aux[k], bm.count);
     eb.x = mode;
+    eb.y = a.sy_N[k] - 1;  // N_t entering the join (after the barrier, N_t = eb.y + 1)
   }
   (void)sy_match;
   const size_t p = size_t(k) + a.incs_off[k];
@@ -693,9 +844,9 @@ __global__ void k_plan_incs(PropArgs a, const uint32_t* incs_k, const uint32_t* 
                                : make_uint4(0, 0, 0, 0);
 }
 
-template <int K, int R, int MAXT>
+template <int K, int R, int MAXT, bool CV = false>
 int launch(const PropArgs& a, uint32_t grid, uint32_t threads, size_t smem_xchg, cudaStream_t s) {
-  auto kern = k_propagate<K, R, MAXT>;
+  auto kern = k_propagate<K, R, MAXT, CV>;
   const size_t smem = smem_xchg + (R > 0 ? size_t(threads / 32) * R * slot_words<K>() * 4 : 0) +
                      size_t(threads / 32) * 32 * K * 4;
   if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)))
@@ -720,11 +871,17 @@ template <int K>
 int launch_k(const PropArgs& a, uint32_t grid, uint32_t threads, size_t smem_xchg, cudaStream_t s) {
   const size_t per_slot = size_t(threads / 32) * slot_words<K>() * 4;
   const size_t kBudget = 160 * 1024 - size_t(threads / 32) * 32 * K * 4;
+  // compressed versions: the same shapes, instantiated with the compressing store
   if constexpr (K <= 4) {
-    if (threads <= 256 && smem_xchg + 8 * per_slot <= kBudget) return launch<K, 8, 256>(a, grid, threads, smem_xchg, s);
-    if (smem_xchg + 2 * per_slot <= kBudget) return launch<K, 2, 1024>(a, grid, threads, smem_xchg, s);
+    if (threads <= 256 && smem_xchg + 8 * per_slot <= kBudget)
+      return a.compress ? launch<K, 8, 256, true>(a, grid, threads, smem_xchg, s)
+                        : launch<K, 8, 256>(a, grid, threads, smem_xchg, s);
+    if (smem_xchg + 2 * per_slot <= kBudget)
+      return a.compress ? launch<K, 2, 1024, true>(a, grid, threads, smem_xchg, s)
+                        : launch<K, 2, 1024>(a, grid, threads, smem_xchg, s);
   }
-  return launch<K, 0, 1024>(a, grid, threads, smem_xchg, s);
+  return a.compress ? launch<K, 0, 1024, true>(a, grid, threads, smem_xchg, s)
+                    : launch<K, 0, 1024>(a, grid, threads, smem_xchg, s);
 }
 
 // failure-detection test: one warp waits, with the walkers' bounded wait, on a clock row
@@ -798,6 +955,11 @@ int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s
   a.plan = b.plan;
   a.recmeta = b.recmeta;
   a.hb_only = z.hb_only;
+  a.compress = z.compress;
+  a.cv_pool = b.cv_pool;
+  a.cv_cap = z.cv_cap;
+  a.cv_used = reinterpret_cast<unsigned long long*>(&b.st->spare[3]);
+  a.cv_words = reinterpret_cast<unsigned long long*>(&b.st->spare[4]);
   // plan: per-agent stream of clock-changing steps with their static data resolved
   p.begin("g_plan", double(z.n_sync + z.n_incs) * 64 + double(z.n_cs) * 2 * g.RW * 4);
   if (z.n_cs) {

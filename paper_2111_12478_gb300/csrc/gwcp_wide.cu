@@ -337,6 +337,10 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
     } else {
       // barrier: C and H joined over the members
       const uint32_t mode = eb.x;
+      if (eb.y != N) {  // forced compression at barriers: enter with the members' highest N
+        N = eb.y;
+        set_entry_w(a, hid, u, N, dirty);
+      }
       if (mode == BAR_SINGLE) {
         set_entry_w(a, pid, u, N, dirty);  // P_t = C_t
       } else {
@@ -439,6 +443,9 @@ struct WideCheckArgs {
   unsigned long long race_cap;
   DevStatus* st;
   uint32_t dense_wp;             // 0: clocks are tile tables; else dense rows of this many words
+  const uint32_t* cv_pool;       // non-null: compressed versions (rows holds B headers each)
+  unsigned long long cv_cap;
+  uint32_t row_words;            // words per entry of rows
   unsigned long long* chunk_ns;  // optional timeline: globaltimer at each block's end
   uint32_t* chunk_races;         // and the races it found
 };
@@ -503,7 +510,7 @@ __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cn
   const uint32_t bwho = a.s_who[p];
   const uint32_t u = who_agent(bwho), cb = who_class(bwho), bu = who_block(bwho);
   const uint32_t run = a.run_excl[p] + a.flag[p] - 1;
-  const uint32_t* rowtab = a.rows + size_t(a.s_row[p]) * (a.dense_wp ? a.dense_wp : kTabW);
+  const uint32_t* rowtab = a.rows + size_t(a.s_row[p]) * a.row_words;
   const uint32_t any_mask = conflict_classes(cb, false) | conflict_classes(cb, true);
   uint32_t tests = 0;
   for (uint32_t q = 0; q < 4; ++q) {
@@ -531,7 +538,9 @@ __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cn
       const uint32_t ai = a.idx[pos];
       const uint32_t na = a.s_ep[pos];
       uint32_t cv;
-      if (a.dense_wp) {
+      if (a.cv_pool) {
+        cv = cv_entry(rowtab, a.cv_pool, a.cv_cap, v, a.g.apb, cv_group(a.g.gran));
+      } else if (a.dense_wp) {
         cv = __ldg(rowtab + v);
       } else {
         const uint32_t tid = __ldg(rowtab + v / kTileW);
@@ -682,6 +691,9 @@ void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t
   a.race_cap = z.race_cap;
   a.st = b.st;
   a.dense_wp = g.nT ? 0u : g.Wp;
+  a.cv_pool = z.compress ? b.cv_pool : nullptr;
+  a.cv_cap = z.cv_cap;
+  a.row_words = z.compress ? g.B : g.RW;
   a.chunk_ns = b.chunk_ns;
   a.chunk_races = b.chunk_races;
   p.begin("i_check", double(n) * (4 + 16 + 4 + 4 + 4 + 8));

@@ -24,8 +24,9 @@ EXPORTS = ("gwcp_create", "gwcp_load_trace", "gwcp_compute_order", "gwcp_report_
            "gwcp_pool_run_batch", "gwcp_pool_set_active_lanes", "gwcp_pool_autotune", "gwcp_pool_now",
            "gwcp_pool_device_bytes", "gwcp_pool_destroy", "gwcp_set_ranker", "gwcp_location_features",
            "gwcp_rank_scores", "gwcp_rank_grad", "gwcp_rank_train", "gwcp_check_timeline", "gwcp_set_clock_mode",
-           "gwcp_pool_clock_modes", "gwcp_set_check_mode", "gwcp_debug_wait_timeout", "gwcp_pool_settings")
-CLOCKS_AUTO, CLOCKS_DENSE, CLOCKS_TILES = 0, 1, 2
+           "gwcp_pool_clock_modes", "gwcp_set_check_mode", "gwcp_debug_wait_timeout", "gwcp_pool_settings",
+           "gwcp_clock_bytes")
+CLOCKS_AUTO, CLOCKS_DENSE, CLOCKS_TILES, CLOCKS_COMPRESSED = 0, 1, 2, 3
 CHECK_AUTO, CHECK_CHUNKED, CHECK_SPARSE = 0, 1, 2
 
 
@@ -44,7 +45,7 @@ class Geometry(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("race_capacity", ctypes.c_uint64), ("profile", ctypes.c_uint32),
                 ("blocking_sync", ctypes.c_uint32), ("timeline", ctypes.c_uint32), ("hb_only", ctypes.c_uint32),
-                ("pack_walkers", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
+                ("pack_walkers", ctypes.c_uint32), ("forced_barrier", ctypes.c_uint32)]
 
 
 class TrainOptions(ctypes.Structure):
@@ -97,6 +98,8 @@ def load_library():
     L.gwcp_profile_get.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(ctypes.c_double)]
     L.gwcp_counters.argtypes = [vp, ctypes.POINTER(u64)]
+    L.gwcp_clock_bytes.argtypes = [vp, ctypes.POINTER(u64)]
+    L.gwcp_clock_bytes.restype = i32
     L.gwcp_analyze_noalloc.argtypes = [vp, u64, ctypes.POINTER(Geometry), vp, u64, ctypes.POINTER(u64),
                                        ctypes.POINTER(u64), vp]
     L.gwcp_analyze_noalloc.restype = i32
@@ -171,9 +174,9 @@ class Context:
     """One analysis context on one CUDA device (gwcp_ctx)."""
 
     def __init__(self, device: int = 0, race_capacity: int = 0, profile: bool = False, timeline: bool = False,
-                 hb_only: bool = False):
+                 hb_only: bool = False, forced_barrier: bool = False):
         L = load_library()
-        opt = Options(race_capacity, int(profile), 0, int(timeline), int(hb_only))
+        opt = Options(race_capacity, int(profile), 0, int(timeline), int(hb_only), 0, int(forced_barrier))
         h = ctypes.c_void_p()
         rc = L.gwcp_create(ctypes.byref(h), device, ctypes.byref(opt))
         if rc:
@@ -269,7 +272,7 @@ class Context:
         return out
 
     def set_clock_mode(self, mode: int):
-        """CLOCKS_AUTO, CLOCKS_DENSE or CLOCKS_TILES from the next load_trace on."""
+        """CLOCKS_AUTO, CLOCKS_DENSE, CLOCKS_TILES or CLOCKS_COMPRESSED from the next load_trace on."""
         rc = self._L.gwcp_set_clock_mode(self._h, mode)
         if rc:
             raise GwcpError(rc, "gwcp_set_clock_mode")
@@ -343,6 +346,14 @@ class Context:
         keys = ("accesses", "sync_entries", "critical_sections", "in_section_accesses", "clock_versions",
                 "partner_tests", "loop_visits", "joins")
         return dict(zip(keys, [int(v) for v in a]))
+
+    def clock_bytes(self) -> dict:
+        """Bytes of the last compute's clock versions: as dense rows, as stored, as reserved."""
+        a = (ctypes.c_uint64 * 3)()
+        rc = self._L.gwcp_clock_bytes(self._h, a)
+        if rc:
+            raise GwcpError(rc, "gwcp_clock_bytes")
+        return dict(dense=int(a[0]), stored=int(a[1]), reserved=int(a[2]))
 
 
 def debug_wait_timeout(device: int, spin_limit: int) -> int:
