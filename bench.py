@@ -456,6 +456,23 @@ def bench_configs(args, local, torch, gwcp, tracegen, np):
     return out
 
 
+def host_cpu() -> dict:
+    """The host's logical core count and CPU model (first model line of /proc/cpuinfo, or
+    the platform's processor string)."""
+    import platform
+
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine()}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, on the host cores, on a bounded
     prefix of the same workload per step (rank 0 only)."""
@@ -481,7 +498,8 @@ def run_reference(args, rank, world):
            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "events_per_step": n_sample, "seed": SEED},
            "cpu_baseline": {"value": v, "unit": "events/s", "cores": 1, "kind": "oracle",
-                            "sample": f"first {n_sample} events of the {WORKLOAD} trace (seed {SEED}), per step"},
+                            "sample": f"first {n_sample} events of the {WORKLOAD} trace (seed {SEED}), per step",
+                            **host_cpu()},
            "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -633,7 +651,8 @@ def main():
             exact = bool(np.array_equal(ref.races, races[races[:, 1] < k]))
             what = f"the full {n_ev}-event trace" if k == n_ev else f"the first {k} events of the {n_ev}-event trace"
             cpu = {"value": k / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
-                   "sample": f"{what} of this run (seed {SEED}), single-threaded C++ -O2", "seconds": dt}
+                   "sample": f"{what} of this run (seed {SEED}), single-threaded C++ -O2", "seconds": dt,
+                   **host_cpu()}
         peak, peak_kind = read_peaks()
         wp = tracegen.WORKLOADS[args.workload]
         # dominant phase by device time
