@@ -439,15 +439,20 @@ __global__ void k_d_fill(const Event* ev, Geo g, uint32_t n_sync, const uint32_t
 // join then gives every member one common value for all members' entries. Local times are
 // the plain ones plus a per-agent offset that changes only at the agent's barriers. A
 // block's barriers involve only its own agents, so one warp per block walks them in trace
-// order: M = max over members of (N before + offset), then offset = M - N before.
+// order: M = max over members of (N before + offset), then offset = M - N before. When
+// every barrier of a block has all the block's agents as members (always so at warp
+// granularity), each barrier leaves them all at M + 1, so M_i = M_(i-1) + the largest
+// plain increase of a member since the previous barrier: a prefix sum instead of a walk.
+// A barrier with one member changes no offset and is left out.
 
-// barrier -> (its block, its trace-order position)
+// barrier -> (its block, or B for a one-member barrier; its trace-order position)
 __global__ void k_fb_keys(const Event* ev, Geo g, const uint32_t* bar, uint32_t n_bar, uint64_t* key,
                           uint32_t* val) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_bar) return;
   const Event e = ev[bar[i]];
-  key[i] = e.scope == GWCP_SCOPE_CTA ? uint32_t(e.addr) : e.agent / g.apb;
+  const bool single = barrier_members(e, g).count <= 1;
+  key[i] = single ? g.B : e.scope == GWCP_SCOPE_CTA ? uint32_t(e.addr) : e.agent / g.apb;
   val[i] = i;
 }
 
@@ -493,9 +498,35 @@ __global__ void __launch_bounds__(32) k_fb_walk(Geo g, uint32_t n_sync, const ui
   __shared__ uint32_t off_s[1024];  // per member of the block (agents_per_block <= 1024)
   __shared__ uint4 rec_s[FB_STAGE];
   const uint32_t lane = threadIdx.x, b = blockIdx.x;
+  const uint32_t r0 = blo[b], r1 = blo[b + 1];
+  bool partial = false;
+  for (uint32_t r = r0 + lane; r < r1; r += 32) partial |= off[r + 1] - off[r] != g.apb;
+  if (!__any_sync(0xffffffffu, partial)) {
+    // whole-block barriers: d_i = max over members of (N before barrier i - N before
+    // barrier i-1), d_r0 = max N before the first; M_i = sum of d up to i
+    uint32_t carry = 0;
+    for (uint32_t i0 = r0; i0 < r1; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      uint32_t d = 0;
+      if (i < r1) {
+        const uint32_t o = off[i], op = i > r0 ? off[i - 1] : 0u;
+        for (uint32_t j = 0; j < g.apb; ++j) d = max(d, rec[o + j].y - (i > r0 ? rec[op + j].y : 0u));
+      }
+      const uint32_t M = carry + warp_inclusive_scan(d);
+      if (i < r1) {
+        const uint32_t o = off[i];
+        for (uint32_t j = 0; j < g.apb; ++j) {
+          const uint4 r = rec[o + j];
+          if (r.x < n_sync) boff[r.x] = M - r.y;
+        }
+      }
+      carry = __shfl_sync(0xffffffffu, M, 31);
+    }
+    return;
+  }
   for (uint32_t j = lane; j < g.apb; j += 32) off_s[j] = 0;
-  const uint32_t pend = off[blo[b + 1]];
-  uint32_t p = off[blo[b]], lo = p, hi = p;
+  const uint32_t pend = off[r1];
+  uint32_t p = off[r0], lo = p, hi = p;
   auto stage = [&](uint32_t at) {
     __syncwarp();
     lo = at;
@@ -886,8 +917,8 @@ void phaseC_forced(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, 
   p.begin("c_forced", double(n) * 40 + double(z.n_sync) * 24);
   k_fb_keys<<<blocks(n, 256), 256, 0, s>>>(b.ev, g, b.bar, n, b.fb_key, b.fb_val);
   count_launch();
-  uint64_t mask = 0;
-  while (mask < g.B - 1) mask = (mask << 1) | 1;
+  uint64_t mask = 0;  // keys 0..B (B: one-member barriers, left out of the walk)
+  while (mask < g.B) mask = (mask << 1) | 1;
   const bool second = radix_sort_pairs(b.fb_key, b.fb_val, b.fb_key2, b.fb_val2, n, mask, b.scan_tmp, s);
   const uint64_t* skey = second ? b.fb_key2 : b.fb_key;
   const uint32_t* spos = second ? b.fb_val2 : b.fb_val;
