@@ -105,8 +105,8 @@ struct CvState {
 // the words of expanded blocks go to the pool, from a chunk of kCvChunk words the walker
 // takes at a time. A version that does not fit the pool gets zero headers, and the host
 // runs again with a larger pool (cv_used keeps counting). Only the compressing walker
-// instantiations contain it.
-__device__ __forceinline__ CvState put_row_c(const PropArgs& a, uint32_t row, const uint32_t* scratch, CvState cs) {
+// instantiations contain it, out of line (the register path below is the common one).
+__device__ __noinline__ CvState put_row_c(const PropArgs& a, uint32_t row, const uint32_t* scratch, CvState cs) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t apb = a.g.apb, nb = a.g.B, gs = cv_group(a.g.gran), nw = (apb + gs - 1) / gs;
   // pass 1: which of the lane's blocks (b = lane + 32 i) are uniform, and the words the
