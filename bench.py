@@ -34,6 +34,9 @@ SEED = 1
 T0 = time.perf_counter()
 
 
+CLOCK_MODES = {"auto": 0, "dense": 1, "tiles": 2, "compressed": 3}  # gwcp.CLOCKS_*
+
+
 def log(msg):
     print(f"[bench] {msg}", file=sys.stderr, flush=True)
 
@@ -518,6 +521,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, help="a trace shape of tracegen.WORKLOADS")
     ap.add_argument("--no-ranker", action="store_true", help="skip the ranked-check measurement")
     ap.add_argument("--no-compressed", action="store_true", help="skip the compressed-versions measurement")
+    ap.add_argument("--clock-mode", default="auto", choices=list(CLOCK_MODES),
+                    help="clock representation of the main section (compressed: the paper's memory mode)")
     ap.add_argument("--no-configs", action="store_true", help="skip the tiny and 8192-warp workloads")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (512-trace) measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson arrivals) measurement")
@@ -559,6 +564,7 @@ def main():
     stream = torch.cuda.Stream(device=local)
     dev = torch.from_numpy(ev.view(np.uint8).copy()).to(f"cuda:{local}")
     ctx = gwcp.Context(local, profile=True)
+    ctx.set_clock_mode(CLOCK_MODES[args.clock_mode])
     ctx.load_trace(dev, *geo.astuple(), stream=stream)
 
     def step():
@@ -608,6 +614,7 @@ def main():
     pinned = torch.from_numpy(ev.view(np.uint8).copy()).pin_memory()
     host_ptr = pinned.data_ptr()
     ctx_e2e = gwcp.Context(local)
+    ctx_e2e.set_clock_mode(CLOCK_MODES[args.clock_mode])
     e2e_times = []
     d2h = 0
     races = ctx.report_races(stream=stream)
@@ -665,7 +672,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": args.workload, "events": n_ev, "agents": geo.num_agents,
+            "config": {"workload": args.workload, "events": n_ev, "agents": geo.num_agents, "clock_mode": args.clock_mode,
                        "agents_per_block": geo.agents_per_block,
                        "granularity": "warp" if geo.granularity else "thread", "blocks": wp["num_blocks"],
                        "addresses": wp["n_ranks"], "zipf_s": wp["zipf_s"],

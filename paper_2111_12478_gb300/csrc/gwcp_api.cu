@@ -520,6 +520,10 @@ int run(gwcp_ctx* c, cudaStream_t s) {
       return kRerun;
     }
     c->cv_cap_hint = std::max(c->cv_cap_hint, next);
+    // the propagation's algorithmic bytes: the compressed words written, not dense rows
+    for (auto& r : c->prof.recs)
+      if (!std::strcmp(r.name, "g_propagate"))
+        r.bytes = 4.0 * double(c->st_host->spare[4]) + double(z.n_cs) * 2 * g.Wp * 4;
   }
   if (code) return code;
   c->n_races = c->st_host->n_races;
