@@ -44,6 +44,7 @@ struct PropArgs {
   uint32_t *bar_j, *bar_cnt;
   uint32_t n_locks;
   int cta_barriers;
+  uint32_t forced;  // forced compression at barriers: local times come from the plan
   // compressed clock versions: rows holds B header words per version
   uint32_t compress;
   uint32_t* cv_pool;
@@ -669,12 +670,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_propagate(PropArgs a) {
     } else {
       // sync (Algorithm 1): join C_t and H_t over the barrier's scope
       const uint32_t mode = __shfl_sync(0xffffffffu, eb.x, i);
-      // the local time the agent enters the join with: N_t, or under forced compression
-      // at barriers the highest N among the members
-      const uint32_t Nb = __shfl_sync(0xffffffffu, eb.y, i);
-      if (Nb != N) {
-        N = Nb;
-        set_entry<K>(H, u, N);
+      // under forced compression at barriers the agent enters the join with the highest
+      // N among the members (otherwise the plan holds N_t itself)
+      if (a.forced) {
+        const uint32_t Nb = __shfl_sync(0xffffffffu, eb.y, i);
+        if (Nb != N) {
+          N = Nb;
+          set_entry<K>(H, u, N);
+        }
       }
       uint32_t C[K];
 #pragma unroll
@@ -955,6 +958,7 @@ int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s
   a.plan = b.plan;
   a.recmeta = b.recmeta;
   a.hb_only = z.hb_only;
+  a.forced = z.forced_barrier;
   a.compress = z.compress;
   a.cv_pool = b.cv_pool;
   a.cv_cap = z.cv_cap;

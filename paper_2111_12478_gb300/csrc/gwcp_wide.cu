@@ -505,6 +505,11 @@ __device__ __forceinline__ void emit_race(const WideCheckArgs& a, uint64_t v, ui
 }
 
 // partner tests of the access at key-order position p; returns how many were made
+// REP: how the clock versions are held (one instantiation each, so that the common
+// representations keep their registers and occupancy)
+enum : int { REP_TILES = 0, REP_DENSE = 1, REP_COMPRESSED = 2 };
+
+template <int REP>
 __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cnt, uint64_t* s_buf) {
   const uint32_t b = a.idx[p];
   const uint32_t bwho = a.s_who[p];
@@ -538,9 +543,9 @@ __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cn
       const uint32_t ai = a.idx[pos];
       const uint32_t na = a.s_ep[pos];
       uint32_t cv;
-      if (a.cv_pool) {
+      if constexpr (REP == REP_COMPRESSED) {
         cv = cv_entry(rowtab, a.cv_pool, a.cv_cap, v, a.g.apb, cv_group(a.g.gran));
-      } else if (a.dense_wp) {
+      } else if constexpr (REP == REP_DENSE) {
         cv = __ldg(rowtab + v);
       } else {
         const uint32_t tid = __ldg(rowtab + v / kTileW);
@@ -552,7 +557,8 @@ __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cn
   return tests;
 }
 
-__global__ void __launch_bounds__(kCheckThreads) k_wc_check(WideCheckArgs a) {
+template <int REP>
+__global__ void __launch_bounds__(kCheckThreads, 8) k_wc_check(WideCheckArgs a) {
   __shared__ uint32_t s_cnt;
   __shared__ unsigned long long s_base;
   __shared__ uint64_t s_buf[kRaceStage];
@@ -560,7 +566,7 @@ __global__ void __launch_bounds__(kCheckThreads) k_wc_check(WideCheckArgs a) {
   __syncthreads();
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t tests = 0;
-  if (p < a.n) tests = check_one(a, p, &s_cnt, s_buf);
+  if (p < a.n) tests = check_one<REP>(a, p, &s_cnt, s_buf);
   tests = __reduce_add_sync(0xffffffffu, tests);
   if ((threadIdx.x & 31) == 0 && tests) atomicAdd(&a.st->partner_tests, (unsigned long long)tests);
   __syncthreads();
@@ -697,7 +703,12 @@ void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t
   a.chunk_ns = b.chunk_ns;
   a.chunk_races = b.chunk_races;
   p.begin("i_check", double(n) * (4 + 16 + 4 + 4 + 4 + 8));
-  k_wc_check<<<nblk(n, kCheckThreads), kCheckThreads, 0, s>>>(a);
+  if (z.compress)
+    k_wc_check<REP_COMPRESSED><<<nblk(n, kCheckThreads), kCheckThreads, 0, s>>>(a);
+  else if (g.nT)
+    k_wc_check<REP_TILES><<<nblk(n, kCheckThreads), kCheckThreads, 0, s>>>(a);
+  else
+    k_wc_check<REP_DENSE><<<nblk(n, kCheckThreads), kCheckThreads, 0, s>>>(a);
   count_launch();
   p.end();
 }
