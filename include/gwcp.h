@@ -330,7 +330,11 @@ typedef struct {
   uint32_t pack_walkers;  /* as gwcp_options.pack_walkers, for every lane */
   uint64_t mem_budget;    /* device bytes the pool may hold; 0 = 85% of free memory at creation */
   uint64_t race_capacity; /* per lane, as gwcp_options.race_capacity */
-  uint32_t reserved[4];   /* must be 0 */
+  uint32_t compress_versions; /* 1 = the paper's memory mode on every lane: traces of up to
+                                 1024 agents run with GWCP_CLOCKS_COMPRESSED (forced barrier
+                                 compression, compressed clock versions), wider ones with
+                                 tiles; the autotuner then leaves the clock modes alone */
+  uint32_t reserved[3];   /* must be 0 */
 } gwcp_pool_options;
 
 typedef struct {

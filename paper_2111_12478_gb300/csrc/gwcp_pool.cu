@@ -133,7 +133,11 @@ bool trim_idle(gwcp_pool* p, size_t i, std::unique_lock<std::mutex>& lk) {
 
 void run_request(gwcp_pool* p, Lane& L, Request& r) {
   uint64_t nr = 0;
-  gwcp_set_clock_mode(L.ctx, p->clock_mode[width_class(r.t.geo.num_agents)]);
+  // memory mode: compressed versions where the dense walker runs, tiles beyond
+  const uint32_t mode = !p->opt.compress_versions ? p->clock_mode[width_class(r.t.geo.num_agents)]
+                        : r.t.geo.num_agents <= kMaxAgents ? GWCP_CLOCKS_COMPRESSED
+                                                           : GWCP_CLOCKS_AUTO;
+  gwcp_set_clock_mode(L.ctx, mode);
   ctx_set_pack_walkers(L.ctx, p->pack);
   int rc = gwcp_load_trace(L.ctx, r.t.ev, r.t.n, &r.t.geo, r.t.ev_is_device, L.s);
   if (!rc) rc = gwcp_compute_order(L.ctx, L.s);
@@ -221,7 +225,8 @@ int gwcp_pool_create(gwcp_pool** out, int device, const gwcp_pool_options* opt) 
   *out = nullptr;
   gwcp_pool_options o{};
   if (opt) o = *opt;
-  if (o.pack_walkers > 1 || o.reserved[0] || o.reserved[1] || o.reserved[2] || o.reserved[3]) return GWCP_ERR_ARGS;
+  if (o.pack_walkers > 1 || o.compress_versions > 1 || o.reserved[0] || o.reserved[1] || o.reserved[2])
+    return GWCP_ERR_ARGS;
   if (o.lanes == 0) o.lanes = 16;
   if (o.lanes > 256) return GWCP_ERR_ARGS;
   int ndev = 0;
@@ -388,7 +393,7 @@ int gwcp_pool_autotune(gwcp_pool* p, const gwcp_trace_desc* t, uint32_t n, uint3
   static const uint32_t kCand[8] = {1, 2, 4, 8, 12, 16, 24, 32};
   {  // clock representation per width class, timed on a context of this thread
     std::vector<std::vector<uint32_t>> by(kClasses);
-    std::vector<bool> both(kClasses, true);
+    std::vector<bool> both(kClasses, !p->opt.compress_versions);  // memory mode: modes fixed
     for (uint32_t i = 0; i < n; ++i) {
       const int c = width_class(t[i].geo.num_agents);
       by[c].push_back(i);

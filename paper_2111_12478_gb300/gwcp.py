@@ -63,7 +63,8 @@ class TraceDesc(ctypes.Structure):
 
 class PoolOptions(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_uint32), ("pack_walkers", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
-                ("race_capacity", ctypes.c_uint64), ("reserved", ctypes.c_uint32 * 4)]
+                ("race_capacity", ctypes.c_uint64), ("compress_versions", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -447,9 +448,9 @@ class Pool:
     traces concurrently on one GPU, admitted by device memory."""
 
     def __init__(self, device: int = 0, lanes: int = 16, mem_budget: int = 0, race_capacity: int = 0,
-                 pack_walkers: bool = True):
+                 pack_walkers: bool = True, compress_versions: bool = False):
         L = load_library()
-        opt = PoolOptions(lanes, int(pack_walkers), mem_budget, race_capacity)
+        opt = PoolOptions(lanes, int(pack_walkers), mem_budget, race_capacity, int(compress_versions))
         h = ctypes.c_void_p()
         rc = L.gwcp_pool_create(ctypes.byref(h), device, ctypes.byref(opt))
         if rc:

@@ -156,3 +156,25 @@ def test_autotune(gw, mix):
         got = P.run_batch([(ev, geo.astuple()) for ev, geo in traces], [len(w) for w in want])
         for (races, rc, n), w in zip(got, want):
             assert rc == 0 and np.array_equal(races, w)
+
+
+def test_memory_mode_pool(gw, mix):
+    """Lanes in the paper's memory mode (compressed clock versions, forced barrier
+    compression): every trace's race set is the plain single-context one, in a batch, under
+    a tight memory budget, and after the autotuner (which leaves the clock modes alone)."""
+    traces, want = mix
+    batch = [(ev, geo.astuple()) for ev, geo in traces]
+    with gw.Pool(0, lanes=8, compress_versions=True) as P:
+        for _ in range(2):  # the second batch runs on the lanes' grown version pools
+            got = P.run_batch(batch, [len(w) for w in want])
+            for (races, rc, n), w in zip(got, want):
+                assert rc == 0 and n == len(w) and np.array_equal(races, w)
+        P.autotune(batch)
+        assert P.clock_modes() == {}
+        got = P.run_batch(batch, [len(w) for w in want])
+        for (races, rc, n), w in zip(got, want):
+            assert rc == 0 and np.array_equal(races, w)
+    with gw.Pool(0, lanes=8, mem_budget=96 << 20, compress_versions=True) as P:
+        got = P.run_batch(batch, [len(w) for w in want])
+        for (races, rc, n), w in zip(got, want):
+            assert rc == 0 and np.array_equal(races, w)
