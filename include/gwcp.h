@@ -201,6 +201,12 @@ int gwcp_set_check_mode(gwcp_ctx* ctx, uint32_t mode);
  * (GWCP_ERR_TIMEOUT). Synchronous; allocates and frees a small buffer. */
 int gwcp_debug_wait_timeout(int device, uint32_t spin_limit, int* status);
 
+/* Test hook of failure detection: caps the bytes of the buffers the context caches
+ * (0 = no cap). A compute that would need more fails with GWCP_ERR_OOM, as on an exhausted
+ * device, and leaves the context usable: after the cap is raised the next compute runs
+ * normally. Host-side only; no device memory is touched. */
+int gwcp_debug_alloc_limit(gwcp_ctx* ctx, uint64_t bytes);
+
 /* Index of the first event that violates W1-W4 after GWCP_ERR_INVALID_TRACE. */
 uint64_t gwcp_first_bad_index(const gwcp_ctx* ctx);
 

@@ -7,6 +7,8 @@
 #include <map>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gwcp_internal.cuh"
 
 namespace gwcp {
@@ -24,13 +26,17 @@ cudaEvent_t Prof::ev() {
   }
   return pool[used++];
 }
+// Every phase is also an NVTX range on the host thread (profilers can filter launches
+// by phase); the CUDA-event records are kept only with options.profile.
 void Prof::begin(const char* name, double bytes, cudaStream_t on_stream) {
+  nvtxRangePushA(name);
   if (!on) return;
   Rec r{name, ev(), ev(), bytes, on_stream ? on_stream : s};
   cudaEventRecord(r.a, r.s);
   recs.push_back(r);
 }
 void Prof::end() {
+  nvtxRangePop();
   if (!on || recs.empty()) return;
   cudaEventRecord(recs.back().b, recs.back().s);
 }
@@ -62,6 +68,7 @@ struct gwcp_ctx {
   uint64_t tile_cap_hint = 0;  // wide clocks: pool size that the last run needed
   bool compressed = false;     // GWCP_CLOCKS_COMPRESSED was in force at gwcp_load_trace
   uint64_t cv_cap_hint = 0;    // compressed versions: pool words that the last run needed
+  uint64_t alloc_limit = 0;    // gwcp_debug_alloc_limit: cap on the cached buffers' bytes (0 = none)
   cudaStream_t side = nullptr;  // runs the access grouping beside the propagation
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t sync_ev = nullptr;  // options.blocking_sync: host waits sleep on this event
@@ -91,6 +98,14 @@ T* get(gwcp_ctx* c, const char* name, size_t count, bool* oom) {
   const size_t bytes = (count ? count : 1) * sizeof(T);
   auto& a = c->allocs[name];
   if (a.second < bytes) {
+    if (c->alloc_limit) {  // injected memory limit: fail as an exhausted device would
+      size_t held = 0;
+      for (auto& kv : c->allocs) held += kv.second.second;
+      if (held - a.second + bytes + bytes / 8 > c->alloc_limit) {
+        *oom = true;
+        return nullptr;
+      }
+    }
     if (a.first) cudaFreeAsync(a.first, c->alloc_s);
     a.first = nullptr;
     a.second = 0;
@@ -1023,6 +1038,12 @@ int gwcp_check_timeline(gwcp_ctx* c, uint64_t* start_ns, uint64_t* chunk_end_ns,
     cudaMemcpy(chunk_races, c->b.chunk_races, m * 4, cudaMemcpyDeviceToHost);
   }
   return cap < c->n_chunks_timeline ? GWCP_ERR_CAPACITY : cuda_rc();
+}
+
+int gwcp_debug_alloc_limit(gwcp_ctx* c, uint64_t bytes) {
+  if (!c) return GWCP_ERR_ARGS;
+  c->alloc_limit = bytes;
+  return GWCP_OK;
 }
 
 int gwcp_debug_wait_timeout(int device, uint32_t spin_limit, int* status) {

@@ -25,7 +25,7 @@ EXPORTS = ("gwcp_create", "gwcp_load_trace", "gwcp_compute_order", "gwcp_report_
            "gwcp_pool_device_bytes", "gwcp_pool_destroy", "gwcp_set_ranker", "gwcp_location_features",
            "gwcp_rank_scores", "gwcp_rank_grad", "gwcp_rank_train", "gwcp_check_timeline", "gwcp_set_clock_mode",
            "gwcp_pool_clock_modes", "gwcp_set_check_mode", "gwcp_debug_wait_timeout", "gwcp_pool_settings",
-           "gwcp_clock_bytes")
+           "gwcp_clock_bytes", "gwcp_debug_alloc_limit")
 CLOCKS_AUTO, CLOCKS_DENSE, CLOCKS_TILES, CLOCKS_COMPRESSED = 0, 1, 2, 3
 CHECK_AUTO, CHECK_CHUNKED, CHECK_SPARSE = 0, 1, 2
 
@@ -100,6 +100,8 @@ def load_library():
                                    ctypes.POINTER(ctypes.c_double)]
     L.gwcp_counters.argtypes = [vp, ctypes.POINTER(u64)]
     L.gwcp_clock_bytes.argtypes = [vp, ctypes.POINTER(u64)]
+    L.gwcp_debug_alloc_limit.argtypes = [vp, u64]
+    L.gwcp_debug_alloc_limit.restype = i32
     L.gwcp_clock_bytes.restype = i32
     L.gwcp_analyze_noalloc.argtypes = [vp, u64, ctypes.POINTER(Geometry), vp, u64, ctypes.POINTER(u64),
                                        ctypes.POINTER(u64), vp]
@@ -347,6 +349,12 @@ class Context:
         keys = ("accesses", "sync_entries", "critical_sections", "in_section_accesses", "clock_versions",
                 "partner_tests", "loop_visits", "joins")
         return dict(zip(keys, [int(v) for v in a]))
+
+    def debug_alloc_limit(self, nbytes: int):
+        """Test hook: cap the context's cached device buffers at nbytes (0 = no cap)."""
+        rc = self._L.gwcp_debug_alloc_limit(self._h, nbytes)
+        if rc:
+            raise GwcpError(rc, "gwcp_debug_alloc_limit")
 
     def clock_bytes(self) -> dict:
         """Bytes of the last compute's clock versions: as dense rows, as stored, as reserved."""

@@ -337,6 +337,27 @@ def test_bounded_wait_gives_up_and_device_stays_usable(ctx):
     same(ctx, ev, geo)
 
 
+def test_injected_oom_leaves_the_context_usable():
+    # failure detection without a fault: a memory cap on the context makes the analysis
+    # fail with OOM, as an exhausted device would; raised again, the next compute is exact
+    from paper_2111_12478_gb300 import gwcp
+
+    ev, geo, _ = TG.generate(6, n_events=200_000, workload="8blk_64warp_10M")
+    want = O.run(ev, *geo.astuple()).races
+    with gwcp.Context(0) as c:
+        c.load_trace(ev, *geo.astuple())
+        c.debug_alloc_limit(4 << 20)
+        with pytest.raises(gwcp.GwcpError) as ei:
+            c.compute_order()
+        assert ei.value.code == gwcp.ERR_OOM
+        with pytest.raises(gwcp.GwcpError) as ei:
+            c.report_races()
+        assert ei.value.code == gwcp.ERR_OOM
+        c.debug_alloc_limit(0)
+        c.compute_order()
+        assert np.array_equal(c.report_races(), want)
+
+
 def test_device_input_and_stream(ctx):
     import torch
 
