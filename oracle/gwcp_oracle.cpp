@@ -50,6 +50,13 @@
 //   A13 the release loop re-derives C_t after every join and tests acqC <= C_t
 //       component-wise; it also counts how often the one-entry epoch test
 //       acqC[agent] <= C_t[agent] would have answered differently.
+//   C1  (option forced_barrier; section "Vector Clock Compression") after a barrier's
+//       join, every participant's entry in both joined clocks and every participant's
+//       local time become the highest among the participants.
+//   C2  (option version_words) a clock version is P_t (H_t with hb_only) at the start
+//       and after each acquire, release, barrier and access made while holding a lock;
+//       its compressed size is one word per block, plus, for a block whose entries
+//       differ, one word per warp and 32 values per warp whose entries differ.
 
 #include <algorithm>
 #include <array>
