@@ -142,8 +142,8 @@ int gwcp_load_trace(gwcp_ctx* ctx, const gwcp_event* ev, uint64_t n, const gwcp_
  * per-location race check and race compaction. Kernels are enqueued on cuda_stream; the
  * call synchronises that stream three times: twice to size its buffers from device-side
  * counts and once at the end for the status (once more when the automatic race buffer
- * grows and the check runs again; with tile clocks an exhausted tile pool is grown and
- * the analysis run again). Buffers are allocated in stream order on cuda_stream from the
+ * grows and the check runs again; an exhausted tile pool or compressed-version pool is
+ * grown and the analysis run again). Buffers are allocated in stream order on cuda_stream from the
  * device's default memory pool and kept for the next call. Validation errors, a
  * device-side timeout (GWCP_ERR_TIMEOUT) and exhausted device memory (GWCP_ERR_OOM) are
  * returned here and again by gwcp_report_races. */
