@@ -145,9 +145,8 @@ int gwcp_load_trace(gwcp_ctx* ctx, const gwcp_event* ev, uint64_t n, const gwcp_
  * grows and the check runs again; an exhausted tile pool or compressed-version pool is
  * grown and the analysis run again). Buffers are allocated in stream order on
  * cuda_stream from the device's default memory pool and kept for the next call.
- * Validation errors, a
- * device-side timeout (GWCP_ERR_TIMEOUT) and exhausted device memory (GWCP_ERR_OOM) are
- * returned here and again by gwcp_report_races. */
+ * Validation errors, a device-side timeout (GWCP_ERR_TIMEOUT) and exhausted device
+ * memory (GWCP_ERR_OOM) are returned here and again by gwcp_report_races. */
 int gwcp_compute_order(gwcp_ctx* ctx, void* cuda_stream);
 
 /* Waits for the analysis on cuda_stream and copies up to `cap` races into host memory
