@@ -112,3 +112,24 @@ def test_without_a_gpu_contexts_fail_loudly():
     assert ei.value.code == gwcp.ERR_CUDA
     with pytest.raises(gwcp.GwcpError):
         gwcp.Pool(0, lanes=2)
+
+
+def test_argument_checks_before_any_cuda_call():
+    """Entry points reject bad arguments on the host, before any CUDA call (so also here,
+    without a GPU): null contexts, an unknown pool option value, reserved fields."""
+    import ctypes
+
+    from paper_2111_12478_gb300 import build as B
+    from paper_2111_12478_gb300 import gwcp
+
+    B.build()
+    L = gwcp.load_library()
+    out = (ctypes.c_uint64 * 3)()
+    assert L.gwcp_clock_bytes(None, out) == gwcp.ERR_ARGS
+    assert L.gwcp_debug_alloc_limit(None, 0) == gwcp.ERR_ARGS
+    h = ctypes.c_void_p()
+    for opt in (gwcp.PoolOptions(4, 0, 0, 0, 2), gwcp.PoolOptions(4, 2, 0, 0, 0), gwcp.PoolOptions(300, 0, 0, 0, 0)):
+        assert L.gwcp_pool_create(ctypes.byref(h), 0, ctypes.byref(opt)) == gwcp.ERR_ARGS
+    bad = gwcp.PoolOptions(4, 0, 0, 0, 0)
+    bad.reserved[1] = 1
+    assert L.gwcp_pool_create(ctypes.byref(h), 0, ctypes.byref(bad)) == gwcp.ERR_ARGS
