@@ -497,7 +497,9 @@ class Analysis {
     for (Held& h : held_[u]) (write ? h.Wr : h.R).push_back(x);  // A11
     if (!held_[u].empty()) version(u);
 
-    const VC cb = opt_.hb_only ? H_[u] : C(u);
+    // C_b[v] is read only for agents v != u, where C_u = P_u{u := N_u} equals P_u, so the
+    // check reads P_u (H_u with hb_only) in place of forming C_u
+    const VC& cb = opt_.hb_only ? H_[u] : P_[u];
     const uint32_t bu = g_.block(u);
     auto exempt = [&](int ca, uint32_t ba) {
       if (!is_atomic_class(ca) || !is_atomic_class(cls)) return false;
@@ -514,24 +516,28 @@ class Analysis {
       }
       hist.push_back(HistEntry{i, u, cls, N_[u]});
     } else {
-      // agents that never accessed x have no latest access there: only those that did
-      // are visited (in agent order)
-      std::map<uint32_t, std::array<Last, 4>>& last = last_[x];
-      for (const auto& [v, lv] : last) {
-        if (v == u) continue;
-        const Last* best = nullptr;
-        for (int c = 0; c < 4; ++c) {
-          const Last& l = lv[c];
-          if (l.idx == ~uint64_t(0)) continue;
-          if (!is_write_class(c) && !write) continue;  // two reads never conflict
-          if (exempt(c, g_.block(v))) continue;
-          if (!best || l.idx > best->idx) best = &l;
+      // Per location and class, every agent's latest access of that class. Agents that
+      // never accessed x have none and are not visited; neither is a class that b cannot
+      // race with whatever the other agent's block (two reads never conflict; two atomics
+      // may be exempt by scope alone), so the reads of a location nobody writes visit
+      // nothing. a* of agent v is the latest of v's accesses over the remaining classes.
+      std::array<std::map<uint32_t, Last>, 4>& last = last_[x];
+      std::map<uint32_t, const Last*> best;  // agent v -> its a*
+      for (int c = 0; c < 4; ++c) {
+        if (!is_write_class(c) && !write) continue;
+        // exempt(c, .) depends on the other agent's block only through "same block as u"
+        if (exempt(c, bu) && exempt(c, bu + 1)) continue;
+        for (const auto& [v, l] : last[c]) {
+          if (v == u || exempt(c, g_.block(v))) continue;
+          const Last*& b = best[v];
+          if (!b || l.idx > b->idx) b = &l;
         }
-        if (!best) continue;
-        res_->partner_tests++;
-        if (best->epoch > cb[v]) pairs_.emplace_back(best->idx, i);  // A5
       }
-      Last& mine = last[u][cls];
+      for (const auto& [v, b] : best) {
+        res_->partner_tests++;
+        if (b->epoch > cb[v]) pairs_.emplace_back(b->idx, i);  // A5
+      }
+      Last& mine = last[cls][u];
       mine.idx = i;
       mine.epoch = N_[u];
     }
@@ -594,7 +600,7 @@ class Analysis {
   std::unordered_map<uint64_t, LockState> locks_;
   std::map<std::pair<uint64_t, uint64_t>, size_t> cursor_;
   std::unordered_map<LKey, LClocks, LKeyHash> lmap_;
-  std::unordered_map<uint64_t, std::map<uint32_t, std::array<Last, 4>>> last_;  // location -> agent -> class
+  std::unordered_map<uint64_t, std::array<std::map<uint32_t, Last>, 4>> last_;  // location -> class -> agent
   std::unordered_map<uint64_t, std::vector<HistEntry>> hist_;
   std::vector<std::pair<uint64_t, uint64_t>> pairs_;
 };
