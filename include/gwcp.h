@@ -235,9 +235,13 @@ int gwcp_counters(const gwcp_ctx* ctx, uint64_t* out8);
  * that must not call cudaMalloc/cudaFree because those can synchronise the device).
  * Same analysis and same results as gwcp_load_trace(ev_is_device = 1) +
  * gwcp_compute_order + gwcp_report_races, but every intermediate buffer comes from one
- * file-scope __device__ scratch array of 96 MiB that every GPU loading the library
- * holds until the process exits; the call itself allocates nothing (no cudaMalloc,
- * cudaFree or allocating library routine).
+ * file-scope __device__ scratch array of 96 MiB; the call itself allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine). The array is reserved on a device
+ * when the library's device code is loaded there: under CUDA's lazy module loading that
+ * is the first call of this function on the device, which a call with n = 0 performs
+ * without analysing anything. Make that first call at initialisation (where allocating
+ * is allowed) and before any stream capture; the device then holds the array until the
+ * process exits.
  *   ev_dev     device array of n events (read only).
  *   races_dev  device array of races_cap races, written with the first races_cap races
  *              sorted by (later, earlier); may be NULL when races_cap is 0.
@@ -247,11 +251,11 @@ int gwcp_counters(const gwcp_ctx* ctx, uint64_t* out8);
  * Limits: n <= 262144 events, num_agents <= 256, and the trace's intermediates must
  * fit the scratch; beyond any of them the call returns GWCP_ERR_UNSUPPORTED and does
  * nothing else. Returns GWCP_ERR_CAPACITY when races_cap < *n_races.
- * Runs on the current CUDA device and synchronises cuda_stream before returning. The
- * first call on a device looks up the scratch array's device address (a one-time
- * set-up per device); make that first call before any stream capture. All calls share
- * the one scratch array: calls that overlap on the GPU (other streams or threads) race
- * on it and must be serialised by the caller. */
+ * Runs on the current CUDA device and synchronises cuda_stream before returning, also
+ * on an error. Each call looks up the array's device address in the current context.
+ * All calls share the one scratch array, which keeps the previous call's contents (each
+ * call clears what must start at zero): calls that overlap on the GPU (other streams or
+ * threads) race on it and must be serialised by the caller. */
 int gwcp_analyze_noalloc(const gwcp_event* ev_dev, uint64_t n, const gwcp_geometry* geo, gwcp_race* races_dev,
                          uint64_t races_cap, uint64_t* n_races, uint64_t* first_bad_index, void* cuda_stream);
 

@@ -11,8 +11,10 @@
 // The scratch array is shared by every call in the process on a device and keeps the
 // previous call's contents; each call clears what must start at zero. Calls that
 // overlap on the GPU (on different streams, or from different threads) race on it.
+// The array is reserved when this module is loaded on a device, which lazy module
+// loading defers to the first call here (n = 0 is enough): callers make that call at
+// initialisation, before any stream capture.
 #include <algorithm>
-#include <mutex>
 
 #include "gwcp_internal.cuh"
 
@@ -30,28 +32,24 @@ namespace {
 constexpr size_t kScratchBytes = size_t(96) << 20;  // 96 MiB per device
 constexpr uint64_t kMaxEventsNoalloc = uint64_t(1) << 18;
 constexpr uint32_t kMaxAgentsNoalloc = 256;
-constexpr int kMaxDevices = 64;
 
 // Device-side scratch. In host code this name is only a stand-in for the symbol: its
-// device address comes from cudaGetSymbolAddress, once per device.
+// device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// device address of the scratch array on the current device (set up on first use)
-int scratch_base(int dev, unsigned char** out) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return GWCP_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = p;
+// Device address of the scratch array in the current device's context. Looked up on
+// every call: an address belongs to a context, and a cached one would go stale after
+// cudaDeviceReset or under another context on the same ordinal. The first lookup on a
+// device loads this library's module there (lazy module loading), which is when the
+// array is reserved; later lookups are cheap.
+int scratch_base(unsigned char** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return GWCP_ERR_CUDA;
   }
-  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  *out = static_cast<unsigned char*>(p);
   return GWCP_OK;
 }
 
@@ -174,6 +172,15 @@ int analyze(const Event* ev, uint64_t n, const Geo& g, gwcp_race* out, uint64_t 
   const uint32_t slots = std::min<uint32_t>(g.B + 1, lock_scope_cap(g.B));
   z.pool_cap = z.n_cs * slots + z.n_exp * 2 * slots + 64;
   b.dep_pool = A.take<uint32_t>(z.pool_cap);
+  if (A.full) return GWCP_ERR_UNSUPPORTED;
+  // the last validity check (W3) needs only the buffers carved so far: an invalid trace is
+  // reported with its first bad index before the rest of the scratch is sized
+  phaseE_walk(b, g, z, s, prof);
+  if (code == GWCP_ERR_INVALID_TRACE) {
+    if (int rc = read_back(s, &st, b.st, v, nullptr, 0)) return rc;
+    if (bad_index) *bad_index = st.bad_index;
+    return GWCP_ERR_INVALID_TRACE;
+  }
   const size_t ni1 = size_t(z.n_incs) + 1;
   const size_t ne1 = std::max<size_t>(size_t(z.n_exp), size_t(z.n_incs) * kMaxNest) + 1;
   b.acc_info = A.take<AccInfo>(z.N);
@@ -219,12 +226,6 @@ int analyze(const Event* ev, uint64_t n, const Geo& g, gwcp_race* out, uint64_t 
   uint32_t* race_tmp = A.take<uint32_t>(race_tmp_elems);
   if (A.full || !z.race_cap) return GWCP_ERR_UNSUPPORTED;
 
-  phaseE_walk(b, g, z, s, prof);
-  if (code == GWCP_ERR_INVALID_TRACE) {
-    if (int rc = read_back(s, &st, b.st, v, nullptr, 0)) return rc;
-    if (bad_index) *bad_index = st.bad_index;
-    return GWCP_ERR_INVALID_TRACE;
-  }
   cudaMemsetAsync(b.done, 0, (size_t(z.n_cs) + 1) * 4, s);
   cudaMemsetAsync(b.cursor, 0, size_t(g.W) * (z.n_locks + 1) * 4, s);
   if (global_bars && z.n_bar) {
@@ -271,11 +272,10 @@ extern "C" int gwcp_analyze_noalloc(const gwcp_event* ev_dev, uint64_t n, const 
       geo->num_agents % geo->agents_per_block != 0 || geo->granularity > 1)
     return GWCP_ERR_ARGS;
   if (n > kMaxEventsNoalloc || geo->num_agents > kMaxAgentsNoalloc) return GWCP_ERR_UNSUPPORTED;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GWCP_ERR_CUDA;
-  if (n == 0) return GWCP_OK;
+  // set-up first, so that a zero-length call loads the module and reserves the array
   unsigned char* scratch = nullptr;
-  if (int rc = scratch_base(dev, &scratch)) return rc;
+  if (int rc = scratch_base(&scratch)) return rc;
+  if (n == 0) return GWCP_OK;
   Geo g{};
   g.W = geo->num_agents;
   g.apb = geo->agents_per_block;
@@ -287,6 +287,14 @@ extern "C" int gwcp_analyze_noalloc(const gwcp_event* ev_dev, uint64_t n, const 
   g.Wp = 32 * k;
   g.nT = 0;
   g.RW = g.Wp;
-  return analyze(reinterpret_cast<const Event*>(ev_dev), n, g, races_dev, races_cap, n_races, first_bad_index,
-                 static_cast<cudaStream_t>(cuda_stream), scratch);
+  const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int rc = analyze(reinterpret_cast<const Event*>(ev_dev), n, g, races_dev, races_cap, n_races,
+                         first_bad_index, s, scratch);
+  // an early error return may leave work queued that writes the scratch: drain it, so that
+  // a caller's next call (on any stream) does not overlap it
+  if (rc != GWCP_OK && rc != GWCP_ERR_CAPACITY) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+  }
+  return rc;
 }
