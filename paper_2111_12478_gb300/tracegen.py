@@ -240,7 +240,10 @@ def build_generator(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_GEN_LIB), exist_ok=True)
     if force or not os.path.exists(_GEN_LIB) or os.path.getmtime(_GEN_LIB) < os.path.getmtime(_GEN_SRC):
         tmp = _GEN_LIB + ".tmp"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _GEN_SRC])
+        # no fused multiply-add contraction (gcc's default on aarch64): the same seed gives
+        # the same trace on x86-64 and aarch64 hosts
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp,
+                               _GEN_SRC])
         os.replace(tmp, _GEN_LIB)
     return _GEN_LIB
 

@@ -171,21 +171,6 @@ def test_tiled_workload(ctx, blocks, n, seed):
     assert len(got) > 0
 
 
-def test_full_8192warp_200M(ctx):
-    # the 8192-warp workload at full size (200M events): the races whose later access lies
-    # in the first million events equal the oracle's races on that prefix (a race (a, b)
-    # depends only on the events up to b), and every race involves a planted access
-    ev, geo, planted = TG.generate(1, workload="256blk_8192warp_200M")
-    got = gpu_races(ctx, ev, geo)
-    assert len(got) > 0
-    pl = np.zeros(len(ev), dtype=bool)
-    pl[planted] = True
-    assert (pl[got[:, 0]] | pl[got[:, 1]]).all()
-    k = 1_000_000
-    want = O.run(ev[:k], *geo.astuple()).races
-    assert np.array_equal(got[got[:, 1] < k], want)
-
-
 def test_invalid_traces_first_bad_index(ctx):
     from paper_2111_12478_gb300 import gwcp
 
