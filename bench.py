@@ -1,10 +1,13 @@
 """Benchmark: GWCP race analysis throughput (trace events/s) on one GB300 per rank.
 
-Workload: the 8-block x 256-thread trace analysed at warp granularity (64 agents),
-10M events, 1M addresses drawn Zipf(1.1), 3% synchronisation (scoped locks, atomics,
-fences, barriers), ~0.1% planted races; seeded synthetic. One step = one full analysis
-(gwcp_compute_order: decode/validate, epochs, critical sections, clock propagation,
-access grouping, per-location check, race sort) over the resident trace.
+Headline workload: 256 blocks x 1024 threads analysed at warp granularity (8192 agents,
+clocks of 8192 entries held as 256-entry tiles), 200M events, 64M addresses drawn
+Zipf(1.05), 1% scoped synchronisation (70% block / 30% device scope), ~0.1% planted
+races; seeded synthetic. One step = one full analysis (gwcp_compute_order: decode and
+validate, epochs, critical sections, clock propagation, access grouping, per-location
+check, race sort) over the resident trace. Beside it: the 8-block, 64-warp, 10M-event
+workload (with the ranker and the compressed-clock mode), the tiny 64-thread trace,
+the 512-trace batch and the Poisson-served stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -25,10 +28,14 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+sys.path.insert(1, os.path.join(ROOT, "tests"))  # race digests and ranker metrics (measurement helpers)
 
-WORKLOAD = "8blk_64warp_10M"
+WORKLOAD = "256blk_8192warp_200M"
+C2 = "8blk_64warp_10M"
+TINY = "tiny_1blk_64thr_10k"
 METRIC = "trace events/sec, race set bit-exact; batched/served vs plain; p50/p99 lat"
 SEED = 1
+DIGESTS = os.path.join(ROOT, "tests", "golden", "oracle_digests.json")
 
 
 T0 = time.perf_counter()
@@ -124,22 +131,78 @@ def source_hash(names):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"g_propagate": ["gwcp_propagate.cu"], "i_check": ["gwcp_wide.cu"], "h_sort": ["gwcp_prims.cu"],
-                  "a_scatter": ["gwcp_prep.cu"], "a_count": ["gwcp_prep.cu"], "d_gaps": ["gwcp_prep.cu"]}
+KERNEL_SOURCES = {"k_prop_wide": ["gwcp_wide.cu"], "k_propagate": ["gwcp_propagate.cu"], "k_wc_check": ["gwcp_wide.cu"]}
 
 
-def traffic_for(phase):
-    """DRAM bytes per launch of a phase from the committed ncu summary, if the kernel's
-    source has not changed since the counters were taken."""
+def traffic_for(kernel, workload):
+    """DRAM bytes per launch of a kernel on a workload from the committed ncu summary
+    (profiles/traffic.json), if the kernel's source has not changed since the counters
+    were taken; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        e = t.get(phase)
-        if e and e.get("source_sha") == source_hash(KERNEL_SOURCES.get(phase, [])):
+        e = t.get(f"{kernel}@{workload}")
+        if e and e.get("source_sha") == source_hash(KERNEL_SOURCES.get(kernel, [])):
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
+
+
+def load_digests():
+    try:
+        with open(DIGESTS) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+def digest_check(ev, races, workload, seed):
+    """The race set against the oracle's, through the stored oracle digests of this
+    workload and seed (tests/golden/oracle_digests.json): the races whose later access
+    lies in the oracle's prefix, bucket by bucket, after checking that the trace is the
+    one the oracle ran on."""
+    from race_digest import bucket_digests, trace_sha256
+
+    d = load_digests()
+    for e in (d or {}).get("c3", []):
+        if e["workload"] == workload and e["seed"] == seed and len(ev) >= e["events"]:
+            same_trace = trace_sha256(ev, e["events"]) == e["trace_sha256"]
+            same = bucket_digests(races, e["bucket"], e["events"] // e["bucket"]) == e["buckets"]
+            return {"events_checked": e["events"], "identical": bool(same_trace and same), "trace_matches": same_trace,
+                    "how": f"stored oracle digests per {e['bucket']}-event bucket of the later access"}
+    return None
+
+
+def prop_roofline(kernel, workload, ms, cnt, W, tiles, peak, peak_kind):
+    """Roofline of the clock propagation with the algorithmic bytes of the method: a
+    vector-clock join of width W reads two clocks and writes one (12 W bytes), each
+    release-loop record visit compares one epoch (8 bytes); with tiled clocks also the
+    bytes of the 1 KB tiles the walkers actually read and wrote."""
+    joins, visits = cnt["joins"], cnt["loop_visits"]
+    dense = 12.0 * W * joins + 8.0 * visits
+    ach = dense / (ms / 1e3) / 1e9
+    out = {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+           "peak_kind": f"{peak_kind} hbm_gbs", "traffic": traffic_for(kernel, workload), "algorithmic_bytes": dense,
+           "avg_ms": ms, "bytes_per_unit": "12*W per join (W = %d) + 8 per release-loop visit" % W,
+           "joins": joins, "loop_visits": visits}
+    if tiles:
+        tb = 1024.0 * (cnt["tiles_read"] + cnt["tiles_written"]) + 8.0 * visits
+        out["tile_sparse"] = {"algorithmic_bytes": tb, "achieved": tb / (ms / 1e3) / 1e9,
+                              "frac": tb / (ms / 1e3) / 1e9 / peak, "tiles_read": cnt["tiles_read"],
+                              "tiles_written": cnt["tiles_written"]}
+    return out
+
+
+def check_roofline(ms, prof_bytes, cnt, n_races, workload, peak, peak_kind):
+    """Roofline of the per-location check: the bytes it reads per access (sorted index,
+    record fields, run flags), 8 bytes per partner test and 16 per race written."""
+    b = prof_bytes + 8.0 * cnt["partner_tests"] + 16.0 * n_races
+    ach = b / (ms / 1e3) / 1e9
+    tr = traffic_for("k_wc_check", workload)
+    return {"bound": "hbm", "kernel": "k_wc_check", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": f"{peak_kind} hbm_gbs", "traffic": tr, "algorithmic_bytes": b, "avg_ms": ms,
+            "dram_frac": (tr / (ms / 1e3) / 1e9 / peak) if tr else None}
 
 
 def replica_reduce(t_local: float, events_local: int, dist=None, device="cpu"):
@@ -329,6 +392,7 @@ def bench_ranker(args, local, torch, gwcp, np, ev, geo, dev):
     among the first 10% of locations checked, in location order and in ranked order. The
     ranker's features, scores and re-sort run beside the propagation; the race sets of the
     two orders must be identical."""
+    import ranker_metrics
     from paper_2111_12478_gb300 import ranker
 
     theta = ranker.load_weights()
@@ -356,7 +420,7 @@ def bench_ranker(args, local, torch, gwcp, np, ev, geo, dev):
         ctx.close()
         med = {k: float(np.median([s_[k] for s_ in summ])) for k in summ[0] if k.endswith("_us")}
         out[name] = {**med, "races_in_first_10pct_chunks": summ[-1]["races_in_first_10pct_chunks"],
-                     "racy_location_recall_first_10pct": ranker.racy_location_recall(
+                     "racy_location_recall_first_10pct": ranker_metrics.racy_location_recall(
                          ev, geo.agents_per_block, races, keys.cpu().numpy().view(np.uint64), 0.1),
                      "ms_per_step": 1e3 * float(np.median(steps)), "h_rank_ms": prof.get("h_rank"),
                      "i_check_ms": prof.get("i_check"), "n_races": int(n)}
@@ -416,46 +480,99 @@ def bench_compressed(args, local, torch, gwcp, np, geo, dev, races):
     return out
 
 
-def bench_configs(args, local, torch, gwcp, tracegen, np):
-    """The other single-trace workloads, one entry each: events/s of the whole analysis over
-    the device-resident trace (CUDA events on the launching stream; inputs larger than L2
-    for the 200M-event trace, the tiny trace sits in L2) and the race set against the
-    oracle (whole trace, or the races whose later access lies in the first 1M events)."""
-    out = {}
-    for name, warm, steps, prefix in (("tiny_1blk_64thr_10k", 3, 20, 0), ("256blk_8192warp_200M", 1, 2, 1_000_000)):
-        ev, geo, _ = tracegen.generate(SEED, workload=name)
-        dev = torch.from_numpy(ev.view(np.uint8)).to(f"cuda:{local}")
-        s = torch.cuda.Stream(device=local)
-        ctx = gwcp.Context(local)
-        ctx.load_trace(dev, *geo.astuple(), stream=s)
-        for _ in range(warm):
-            ctx.compute_order(stream=s)
-        ms = []
-        for _ in range(steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            ctx.compute_order(stream=s)
-            e1.record(s)
-            ctx.race_count(stream=s)
-            ms.append(e0.elapsed_time(e1))
-        races = ctx.report_races(stream=s)
-        ctx.close()
-        entry = {"events": int(len(ev)), "agents": geo.num_agents, "value": len(ev) / (statistics.median(ms) / 1e3),
-                 "unit": "events/s", "ms_per_step": statistics.median(ms), "steps": steps, "warmup": warm,
-                 "n_races": int(len(races))}
-        if not args.no_cpu_baseline:
-            from oracle import oracle
+def run_steps(ctx, stream, steps, torch, gwcp, on_step=None):
+    """K analyses of the resident trace, each bracketed by CUDA events on its stream, and
+    the step's result read (the race count, which synchronises). Returns (per-step ms,
+    per-phase [ms, bytes, count], races, launches)."""
+    torch.cuda.synchronize()
+    launches0 = gwcp.launch_count()
+    prof, per_step, n_races = {}, [], 0
+    for _ in range(steps):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        ctx.compute_order(stream=stream)
+        s1.record(stream)
+        n_races = ctx.race_count(stream=stream)
+        per_step.append((s0, s1))
+        for name, ms, by in ctx.profile():
+            a = prof.setdefault(name, [0.0, 0.0, 0])
+            a[0] += ms
+            a[1] += by
+            a[2] += 1
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in per_step], prof, n_races, gwcp.launch_count() - launches0
 
-            k = prefix or len(ev)
-            t0 = time.perf_counter()
-            want = oracle.run(ev[:k], *geo.astuple()).races
-            dt = time.perf_counter() - t0
-            entry["race_set_vs_oracle"] = {"events_checked": k, "identical": bool(
-                np.array_equal(want, races[races[:, 1] < k]))}
-            entry["cpu_oracle"] = {"value": k / dt, "unit": "events/s", "cores": 1,
-                                   "sample": f"first {k} events" if prefix else "whole trace"}
-        out[name] = entry
-        del dev, ev
+
+def bench_c2(args, local, torch, gwcp, tracegen, np, peak, peak_kind):
+    """The 8-block x 256-thread workload at warp granularity (64 agents, 10M events, 1M
+    addresses Zipf(1.1), 3% synchronisation): events/s over the device-resident trace,
+    phases, the propagation's and the check's rooflines, the whole race set against the
+    oracle (which is also its CPU baseline), then the ranker and the compressed-clock mode
+    on the same trace."""
+    ev, geo, _ = tracegen.generate(SEED, workload=C2)
+    dev = torch.from_numpy(ev.view(np.uint8).copy()).to(f"cuda:{local}")
+    stream = torch.cuda.Stream(device=local)
+    ctx = gwcp.Context(local, profile=True)
+    ctx.load_trace(dev, *geo.astuple(), stream=stream)
+    for _ in range(args.warmup):
+        ctx.compute_order(stream=stream)
+    ms, prof, n_races, launches = run_steps(ctx, stream, args.c2_steps, torch, gwcp)
+    races = ctx.report_races(stream=stream)
+    cnt = ctx.counters()
+    ctx.close()
+    phases = {k: (v[0] / v[2], v[1] / v[2]) for k, v in prof.items()}
+    med = statistics.median(ms)
+    out = {"workload": C2, "events": int(len(ev)), "agents": geo.num_agents, "value": len(ev) / (med / 1e3),
+           "unit": "events/s", "ms_per_step": med, "steps": args.c2_steps, "warmup": args.warmup,
+           "n_races": int(n_races), "gpu_launches_per_step": launches / max(1, args.c2_steps),
+           "phases_ms": {k: round(v[0], 4) for k, v in sorted(phases.items(), key=lambda kv: -kv[1][0])},
+           "roofline": prop_roofline("k_propagate", C2, phases["g_propagate"][0], cnt, geo.num_agents, False, peak,
+                                     peak_kind),
+           "roofline_check": check_roofline(phases["i_check"][0], phases["i_check"][1], cnt, len(races), C2, peak,
+                                            peak_kind) if "i_check" in phases else None}
+    if not args.no_cpu_baseline:
+        from oracle import oracle
+
+        t0 = time.perf_counter()
+        want = oracle.run(ev, *geo.astuple()).races
+        dt = time.perf_counter() - t0
+        out["race_set_vs_oracle"] = {"events_checked": int(len(ev)), "identical": bool(np.array_equal(want, races))}
+        out["cpu_oracle"] = {"value": len(ev) / dt, "unit": "events/s", "cores": 1, "sample": "whole trace"}
+    log(f"c2 main done ({time.perf_counter() - T0:.1f} s)")
+    if not args.no_ranker:
+        out["ranker"] = bench_ranker(args, local, torch, gwcp, np, ev, geo, dev)
+        log(f"ranker section done ({time.perf_counter() - T0:.1f} s)")
+    if not args.no_compressed:
+        out["compressed"] = bench_compressed(args, local, torch, gwcp, np, geo, dev, races.copy())
+        log(f"compressed section done ({time.perf_counter() - T0:.1f} s)")
+    del dev
+    return out
+
+
+def bench_tiny(args, local, torch, gwcp, tracegen, np):
+    """The tiny 64-thread trace (thread granularity, 10k events): events/s and the race
+    set against the oracle."""
+    ev, geo, _ = tracegen.generate(SEED, workload=TINY)
+    dev = torch.from_numpy(ev.view(np.uint8).copy()).to(f"cuda:{local}")
+    s = torch.cuda.Stream(device=local)
+    ctx = gwcp.Context(local)
+    ctx.load_trace(dev, *geo.astuple(), stream=s)
+    for _ in range(3):
+        ctx.compute_order(stream=s)
+    ms, _, n_races, _ = run_steps(ctx, s, 20, torch, gwcp)
+    races = ctx.report_races(stream=s)
+    ctx.close()
+    out = {"events": int(len(ev)), "agents": geo.num_agents, "value": len(ev) / (statistics.median(ms) / 1e3),
+           "unit": "events/s", "ms_per_step": statistics.median(ms), "steps": 20, "warmup": 3,
+           "n_races": int(n_races)}
+    if not args.no_cpu_baseline:
+        from oracle import oracle
+
+        t0 = time.perf_counter()
+        want = oracle.run(ev, *geo.astuple()).races
+        dt = time.perf_counter() - t0
+        out["race_set_vs_oracle"] = {"events_checked": int(len(ev)), "identical": bool(np.array_equal(want, races))}
+        out["cpu_oracle"] = {"value": len(ev) / dt, "unit": "events/s", "cores": 1, "sample": "whole trace"}
     return out
 
 
@@ -485,8 +602,9 @@ def run_reference(args, rank, world):
     from paper_2111_12478_gb300 import tracegen
 
     n_sample = args.ref_events
-    ev, geo, _ = tracegen.generate(SEED, workload=WORKLOAD)
-    ev = ev[:n_sample]  # a prefix of a well-formed trace is well-formed
+    # the workload's first n_sample events (the generator's stream does not depend on the
+    # requested length, and a prefix of a well-formed trace is well-formed)
+    ev, geo, _ = tracegen.generate(SEED, workload=WORKLOAD, n_events=n_sample)
     for _ in range(args.warmup):
         oracle.run(ev, *geo.astuple())
     times = []
@@ -510,28 +628,32 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gwcp", choices=["gwcp", "reference"])
-    ap.add_argument("--ref-events", type=int, default=1_000_000)
+    ap.add_argument("--ref-events", type=int, default=500_000,
+                    help="events of the headline workload the reference arm's oracle analyses per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--events", type=int, default=0, help="analyse only this many events of the workload "
                     "(profiling runs); 0 = the full workload")
     ap.add_argument("--workload", default=WORKLOAD, help="a trace shape of tracegen.WORKLOADS")
+    ap.add_argument("--c2-steps", type=int, default=20, help="timed steps of the 64-warp workload")
+    ap.add_argument("--no-c2", action="store_true", help="skip the 64-warp workload (and its ranker and "
+                    "compressed-clock measurements)")
     ap.add_argument("--no-ranker", action="store_true", help="skip the ranked-check measurement")
     ap.add_argument("--no-compressed", action="store_true", help="skip the compressed-versions measurement")
     ap.add_argument("--clock-mode", default="auto", choices=list(CLOCK_MODES),
-                    help="clock representation of the main section (compressed: the paper's memory mode)")
-    ap.add_argument("--no-configs", action="store_true", help="skip the tiny and 8192-warp workloads")
+                    help="clock representation of the headline section")
+    ap.add_argument("--no-configs", action="store_true", help="skip the tiny workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (512-trace) measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson arrivals) measurement")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--lanes", type=int, default=32, help="lanes of the batched/served pool")
-    ap.add_argument("--cpu-events", type=int, default=0, help="events of the trace the oracle runs on for the "
-                    "CPU baseline and the exactness check (a prefix); 0 = the whole trace up to 1024 agents, "
-                    "300000 events beyond")
+    ap.add_argument("--cpu-events", type=int, default=0, help="events of the headline trace the oracle runs on "
+                    "for the CPU baseline and the live exactness check (a prefix); 0 = the whole trace up to 1024 "
+                    "agents, 3M events beyond")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -562,118 +684,91 @@ def main():
     ev, geo, planted = tracegen.generate(SEED + rank, workload=args.workload, n_events=args.events or None)
     n_ev = len(ev)
     stream = torch.cuda.Stream(device=local)
-    dev = torch.from_numpy(ev.view(np.uint8).copy()).to(f"cuda:{local}")
+    dev = torch.from_numpy(ev.view(np.uint8)).to(f"cuda:{local}")
     ctx = gwcp.Context(local, profile=True)
     ctx.set_clock_mode(CLOCK_MODES[args.clock_mode])
     ctx.load_trace(dev, *geo.astuple(), stream=stream)
 
-    def step():
-        ctx.compute_order(stream=stream)
-
     clocks = ClockSampler(local).__enter__()  # started early: nvidia-smi takes a moment to start
     for _ in range(args.warmup):
-        step()
+        ctx.compute_order(stream=stream)
     torch.cuda.synchronize()
-    launches0 = gwcp.launch_count()
-    prof_acc = {}
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
-    per_step = []
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
     clocks.mark_start()
-    for _ in range(args.steps):
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        if not per_step:
-            start.record(stream)
-        step()
-        s1.record(stream)
-        n_races = ctx.race_count(stream=stream)  # synchronises; the result read of the step
-        per_step.append((s0, s1))
-        for name, ms, by in ctx.profile():
-            a = prof_acc.setdefault(name, [0.0, 0.0, 0])
-            a[0] += ms
-            a[1] += by
-            a[2] += 1
-    end.record(stream)
-    torch.cuda.synchronize()
+    step_ms, prof_acc, n_races, launches = run_steps(ctx, stream, args.steps, torch, gwcp)
     clocks.mark_end()
     clocks.__exit__(None, None, None)
-    launches = gwcp.launch_count() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in per_step]
-    total_ms = sum(step_ms)
-    t_local = total_ms / 1e3
+    t_local = sum(step_ms) / 1e3
     t_max, ev_total = replica_reduce(t_local, n_ev * args.steps, dist, device=f"cuda:{local}")
     value = ev_total / t_max
     ms_per_step = t_max * 1e3 / args.steps
+    races = ctx.report_races(stream=stream)
+    cnt = ctx.counters()
+    ctx.close()
+    del dev
+    log(f"headline timed ({time.perf_counter() - T0:.1f} s)")
 
     # end to end through the C ABI: pinned host trace -> device, compute, races -> host
-    pinned = torch.from_numpy(ev.view(np.uint8).copy()).pin_memory()
-    host_ptr = pinned.data_ptr()
+    pinned = torch.from_numpy(ev.view(np.uint8)).pin_memory()
     ctx_e2e = gwcp.Context(local)
     ctx_e2e.set_clock_mode(CLOCK_MODES[args.clock_mode])
-    e2e_times = []
-    d2h = 0
-    races = ctx.report_races(stream=stream)
+    e2e_times, d2h = [], 0
     # the step's result lands in a reused pinned buffer (one DMA, no page faults)
     out_pinned = torch.empty((max(len(races), 1) + 1024) * 2, dtype=torch.int64).pin_memory()
     out_np = out_pinned.numpy().view(np.uint64).reshape(-1, 2)
     for it in range(args.e2e_steps + 1 if args.e2e_steps else 0):
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         t0 = time.perf_counter()
-        rc = ctx_e2e._L.gwcp_load_trace(ctx_e2e._h, host_ptr, n_ev, gwcp.Geometry(*geo.astuple(), 0), 0,
+        rc = ctx_e2e._L.gwcp_load_trace(ctx_e2e._h, pinned.data_ptr(), n_ev, gwcp.Geometry(*geo.astuple(), 0), 0,
                                         stream.cuda_stream)
         assert rc == 0, rc
         ctx_e2e.compute_order(stream=stream)
-        races = ctx_e2e.report_races(stream=stream, out=out_np)
+        got = ctx_e2e.report_races(stream=stream, out=out_np)
         e1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        if it:  # first round warms the context's buffers
+        if it:  # the first round sizes the context's buffers
             e2e_times.append(max(wall, e0.elapsed_time(e1) / 1e3))
-        d2h = races.nbytes + 8
+        d2h = got.nbytes + 8
     e2e_value = n_ev * world / statistics.mean(e2e_times) if e2e_times else None
+    ctx_e2e.close()
+    del pinned, out_pinned
+    log(f"e2e done ({time.perf_counter() - T0:.1f} s)")
 
-    # correctness of this run: the race set against the oracle (CPU), and the CPU baseline
     result = None
     if rank == 0:
-        cpu = None
-        exact = None
+        cpu, exact = None, None
         if not args.no_cpu_baseline:
             from oracle import oracle
 
             # a race (a, b) depends only on the events up to b, so the races of a prefix are
             # the full trace's races whose later access lies in it
-            k = args.cpu_events or (n_ev if geo.num_agents <= 1024 else 300_000)
+            k = args.cpu_events or (n_ev if geo.num_agents <= 1024 else 3_000_000)
             k = min(k, n_ev)
             t0 = time.perf_counter()
             ref = oracle.run(ev[:k], *geo.astuple())
             dt = time.perf_counter() - t0
-            exact = bool(np.array_equal(ref.races, races[races[:, 1] < k]))
+            exact = {"events_checked": k, "identical": bool(np.array_equal(ref.races, races[races[:, 1] < k])),
+                     "how": "the oracle run of the CPU baseline"}
             what = f"the full {n_ev}-event trace" if k == n_ev else f"the first {k} events of the {n_ev}-event trace"
             cpu = {"value": k / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
                    "sample": f"{what} of this run (seed {SEED}), single-threaded C++ -O2", "seconds": dt,
                    **host_cpu()}
+        stored = digest_check(ev, races, args.workload, SEED + rank) if not args.events else None
         peak, peak_kind = read_peaks()
         wp = tracegen.WORKLOADS[args.workload]
-        # dominant phase by device time
         phases = {k: (v[0] / v[2], v[1] / v[2]) for k, v in prof_acc.items()}
-        dom = max(phases, key=lambda k: phases[k][0])
-        dom_ms, dom_bytes = phases[dom]
-        achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+        tiles = cnt["tiles_read"] + cnt["tiles_written"] > 0
         clk = clocks.summary()
         result = {
             "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": args.workload, "events": n_ev, "agents": geo.num_agents, "clock_mode": args.clock_mode,
-                       "agents_per_block": geo.agents_per_block,
+            "config": {"workload": args.workload, "events": n_ev, "agents": geo.num_agents,
+                       "clock_mode": args.clock_mode, "agents_per_block": geo.agents_per_block,
                        "granularity": "warp" if geo.granularity else "thread", "blocks": wp["num_blocks"],
                        "addresses": wp["n_ranks"], "zipf_s": wp["zipf_s"],
                        "sync_frac": round(wp["p_acqrel"] + wp["p_fence"] + wp["p_barrier"] + wp["p_atomic"], 6),
@@ -681,41 +776,34 @@ def main():
                        "l2": f"inputs larger than L2 ({ev.nbytes / 1e6:.0f} MB trace; larger working set per step)"},
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": int(ev.nbytes),
                     "d2h_bytes_per_step": int(d2h)} if e2e_value else None,
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
-                         "traffic": traffic_for(dom), "algorithmic_bytes": dom_bytes, "avg_ms": dom_ms},
-            "roofline_check": ({"bound": "hbm", "kernel": "i_check", "achieved": phases["i_check"][1] / (phases["i_check"][0] / 1e3) / 1e9,
-                                "peak": peak, "unit": "GB/s", "frac": phases["i_check"][1] / (phases["i_check"][0] / 1e3) / 1e9 / peak,
-                                "traffic": traffic_for("i_check"), "algorithmic_bytes": phases["i_check"][1],
-                                "avg_ms": phases["i_check"][0],
-                                "dram_frac": (traffic_for("i_check") / (phases["i_check"][0] / 1e3) / 1e9 / peak
-                                              if traffic_for("i_check") else None)} if "i_check" in phases else None),
+            "roofline": prop_roofline("k_prop_wide" if tiles else "k_propagate", args.workload,
+                                      phases["g_propagate"][0], cnt, geo.num_agents, tiles, peak, peak_kind),
+            "roofline_check": (check_roofline(phases["i_check"][0], phases["i_check"][1], cnt, len(races),
+                                              args.workload, peak, peak_kind) if "i_check" in phases else None),
             "phases_ms": {k: round(v[0], 4) for k, v in sorted(phases.items(), key=lambda kv: -kv[1][0])},
+            "counters": cnt,
             "cpu_baseline": cpu,
-            "race_set_bit_exact": exact, "n_races": int(n_races),
-            "gpu_launches": int(launches), "clocks": clk,
+            "race_set_vs_oracle": {"live": exact, "stored_digests": stored},
+            "race_set_bit_exact": (bool(exact["identical"]) if exact else None) if not stored else
+                                  bool(stored["identical"] and (exact is None or exact["identical"])),
+            "n_races": int(n_races), "gpu_launches": int(launches), "clocks": clk,
         }
-    log(f"main section done ({time.perf_counter() - T0:.1f} s)")
-    if rank == 0 and not args.no_ranker:
-        result["ranker"] = bench_ranker(args, local, torch, gwcp, np, ev, geo, dev)
-        log(f"ranker section done ({time.perf_counter() - T0:.1f} s)")
-    if rank == 0 and not args.no_compressed:
-        result["compressed"] = bench_compressed(args, local, torch, gwcp, np, geo, dev, races.copy())
-        log(f"compressed section done ({time.perf_counter() - T0:.1f} s)")
-    ctx.close()
-    ctx_e2e.close()
-    del dev, pinned
+    del ev
+    log(f"headline section done ({time.perf_counter() - T0:.1f} s)")
+    if rank == 0 and not args.no_c2:
+        result["c2"] = bench_c2(args, local, torch, gwcp, tracegen, np, *read_peaks())
     if rank == 0 and not args.no_configs:
-        result["configs"] = bench_configs(args, local, torch, gwcp, tracegen, np)
-        log(f"configs section done ({time.perf_counter() - T0:.1f} s)")
+        result["tiny"] = bench_tiny(args, local, torch, gwcp, tracegen, np)
+        log(f"tiny done ({time.perf_counter() - T0:.1f} s)")
+    b = None
     if not args.no_batched:
         b = bench_batched(args, local, torch, gwcp, tracegen, np)
         if result is not None:
             result["batched"] = b
         log(f"batched section done ({time.perf_counter() - T0:.1f} s)")
     if not args.no_served:
-        v = bench_served(args, local, torch, gwcp, tracegen, np, b["lanes"] if not args.no_batched else 16,
-                         b["pack_walkers"] if not args.no_batched else True)
+        v = bench_served(args, local, torch, gwcp, tracegen, np, b["lanes"] if b else 16,
+                         b["pack_walkers"] if b else True)
         if result is not None:
             result["served"] = v
         log(f"served section done ({time.perf_counter() - T0:.1f} s)")

@@ -229,6 +229,15 @@ int gwcp_clock_bytes(const gwcp_ctx* ctx, uint64_t* out3);
  * [7] vector-clock joins in the propagation. Synchronous. */
 int gwcp_counters(const gwcp_ctx* ctx, uint64_t* out8);
 
+/* The counters of gwcp_counters followed by: [8] clock tiles (256 entries, 1 KB) that the
+ * propagation's joins and copies read, [9] tiles it wrote (both 0 with dense clocks).
+ * Writes the first min(n, GWCP_N_COUNTERS) counters into out (host array). A vector-clock
+ * join of width W moves 12 W bytes (two clocks read, one written; the paper's Algorithms
+ * 1-2 join full clocks), so [7] x 12 W is the dense join traffic and ([8] + [9]) x 1 KB
+ * the traffic of the tiles actually moved. Synchronous. */
+#define GWCP_N_COUNTERS 10
+int gwcp_counters_ex(const gwcp_ctx* ctx, uint64_t* out, uint32_t n);
+
 /* Allocation-free analysis of a small trace (the paper has no counterpart: this is an
  * interface for callers that cannot allocate device memory when they need a trace
  * analysed, e.g. code running while another component owns the memory pool, or a hook

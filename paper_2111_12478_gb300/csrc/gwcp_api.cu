@@ -63,7 +63,7 @@ struct gwcp_ctx {
   bool races_second = false;
   uint64_t n_races = 0;
   unsigned long long bad_index = ~0ull;
-  uint64_t counters[8] = {};
+  uint64_t counters[GWCP_N_COUNTERS] = {};
   uint64_t clock_words[3] = {};  // last compute: tiles, pool words taken, words written
   uint64_t tile_cap_hint = 0;  // wide clocks: pool size that the last run needed
   bool compressed = false;     // GWCP_CLOCKS_COMPRESSED was in force at gwcp_load_trace
@@ -345,11 +345,16 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   b.scan_tmp = get<uint32_t>(c, "scan_tmp", need2, &oom);
   if (oom) return GWCP_ERR_OOM;
   phaseE_walk(b, g, z, s, c->prof);  // W3; runs on invalid traces too, for the first bad index
-  if (code == GWCP_ERR_INVALID_TRACE) {
+  {
+    // the last validation (W3) and the acquires' dependency lists are done: no later phase
+    // runs on an invalid trace or after an error (their inputs would be incomplete)
     int rc = read_status(c, s, nullptr, 0);
     if (rc) return rc;
+  }
+  code = c->st_host->code;
+  if (code) {
     c->bad_index = c->st_host->bad_index;
-    return GWCP_ERR_INVALID_TRACE;
+    return code;
   }
 
   // ---- remaining buffers ------------------------------------------------------------
@@ -572,6 +577,8 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   c->counters[5] = c->st_host->partner_tests;
   c->counters[6] = c->st_host->loop_visits;
   c->counters[7] = c->st_host->joins;
+  c->counters[8] = c->st_host->tiles_read;
+  c->counters[9] = c->st_host->tiles_written;
   c->clock_words[0] = c->st_host->spare[2];  // tiles handed out
   c->clock_words[1] = c->st_host->spare[3];  // compressed-version pool words handed out
   c->clock_words[2] = c->st_host->spare[4];  // compressed-version words written
@@ -1067,7 +1074,13 @@ int gwcp_profile_get(const gwcp_ctx* c, int i, const char** name, float* ms, dou
 
 int gwcp_counters(const gwcp_ctx* c, uint64_t* out8) {
   if (!c || !out8) return GWCP_ERR_ARGS;
-  std::memcpy(out8, c->counters, sizeof(c->counters));
+  std::memcpy(out8, c->counters, 8 * sizeof(uint64_t));
+  return GWCP_OK;
+}
+
+int gwcp_counters_ex(const gwcp_ctx* c, uint64_t* out, uint32_t n) {
+  if (!c || (n && !out)) return GWCP_ERR_ARGS;
+  std::memcpy(out, c->counters, std::min<uint32_t>(n, GWCP_N_COUNTERS) * sizeof(uint64_t));
   return GWCP_OK;
 }
 

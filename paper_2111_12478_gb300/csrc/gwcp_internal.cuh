@@ -54,6 +54,7 @@ struct DevStatus {
   unsigned long long loop_visits;
   unsigned long long joins;
   unsigned long long spare[6];
+  unsigned long long tiles_read, tiles_written;  // wide clocks: 1 KB tiles the walkers read / wrote
 };
 
 struct Geo {

@@ -176,10 +176,10 @@ int analyze(const Event* ev, uint64_t n, const Geo& g, gwcp_race* out, uint64_t 
   // the last validity check (W3) needs only the buffers carved so far: an invalid trace is
   // reported with its first bad index before the rest of the scratch is sized
   phaseE_walk(b, g, z, s, prof);
-  if (code == GWCP_ERR_INVALID_TRACE) {
-    if (int rc = read_back(s, &st, b.st, v, nullptr, 0)) return rc;
+  if (int rc = read_back(s, &st, b.st, v, nullptr, 0)) return rc;
+  if (st.code) {  // no later phase runs on an invalid trace or after an error
     if (bad_index) *bad_index = st.bad_index;
-    return GWCP_ERR_INVALID_TRACE;
+    return st.code;
   }
   const size_t ni1 = size_t(z.n_incs) + 1;
   const size_t ne1 = std::max<size_t>(size_t(z.n_exp), size_t(z.n_incs) * kMaxNest) + 1;

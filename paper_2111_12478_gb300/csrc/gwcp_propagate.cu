@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_propagate(PropArgs a) {
             H[j] = max(H[j], srcp[Wc + j]);
           }
         }
-        joins += 2 * nwarps;
+        joins += 2;  // this member's C_t and H_t joined into the block's
         ++nbar;
       } else {
         const uint32_t bid = z, count = w;
@@ -778,9 +778,16 @@ __global__ void k_recmeta(uint32_t n_cs, const uint32_t* cs_agent, const uint32_
   if (c < n_cs) recmeta[c] = make_uint4(cs_agent[c] | (cs_sid[c] << 16), cs_epoch[c], cs_rel_idx[c], cs_rel_epoch[c]);
 }
 
-__global__ void k_flatcount(uint32_t n_incs, const uint32_t* exp_off, const uint32_t* ex_dep_cnt, uint32_t* cnt) {
+// (both flattening kernels stand down after an error: the per-record lists are then
+// incomplete)
+__global__ void k_flatcount(uint32_t n_incs, const uint32_t* exp_off, const uint32_t* ex_dep_cnt, uint32_t* cnt,
+                            const DevStatus* st) {
   const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_incs) return;
+  if (st->code) {
+    cnt[r] = 0;
+    return;
+  }
   uint32_t t = 0;
   for (uint32_t e = exp_off[r]; e < exp_off[r + 1]; ++e) t += ex_dep_cnt[e];
   cnt[r] = t;
@@ -788,9 +795,9 @@ __global__ void k_flatcount(uint32_t n_incs, const uint32_t* exp_off, const uint
 
 __global__ void k_flatfill(uint32_t n_incs, const uint32_t* exp_off, const uint32_t* ex_dep_off,
                            const uint32_t* ex_dep_cnt, const uint32_t* pool, const uint32_t* flat_off,
-                           uint32_t* flat) {
+                           uint32_t* flat, const DevStatus* st) {
   const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n_incs) return;
+  if (r >= n_incs || st->code) return;
   uint32_t o = flat_off[r];
   for (uint32_t e = exp_off[r]; e < exp_off[r + 1]; ++e)
     for (uint32_t q = 0; q < ex_dep_cnt[e]; ++q) flat[o++] = pool[ex_dep_off[e] + q];
@@ -975,11 +982,11 @@ int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s
     cudaMemsetAsync(b.hsnap, 0xFF, size_t(z.n_cs) * g.RW * 4, s);
   }
   if (z.n_incs) {
-    k_flatcount<<<(z.n_incs + 255) / 256, 256, 0, s>>>(z.n_incs, b.exp_off, b.ex_dep_cnt, b.flat_off);
+    k_flatcount<<<(z.n_incs + 255) / 256, 256, 0, s>>>(z.n_incs, b.exp_off, b.ex_dep_cnt, b.flat_off, b.st);
     count_launch();
     scan_exclusive(b.flat_off, b.flat_off, size_t(z.n_incs) + 1, nullptr, b.scan_tmp, s);
     k_flatfill<<<(z.n_incs + 255) / 256, 256, 0, s>>>(z.n_incs, b.exp_off, b.ex_dep_off, b.ex_dep_cnt, b.dep_pool,
-                                                       b.flat_off, b.flat);
+                                                       b.flat_off, b.flat, b.st);
     count_launch();
     k_plan_incs<<<(z.n_incs + 255) / 256, 256, 0, s>>>(a, b.incs_k, b.incs_ver, b.flat_off, z.n_incs);
     count_launch();

@@ -10,7 +10,10 @@
 // result keeps an input's id when it equals that input, else it is written as a new
 // tile. Clocks shared after a barrier or an acquire therefore share their tiles, and a
 // clock version (the row the check reads) is a 128-byte table. A release snapshot is
-// two tables; the increment H_t[t] = N_t after it copies the one tile holding t.
+// two tables. H_t[t] = N_t is kept implicit: the walker holds N_t in a register and the
+// table's own entry may lag, so an increment copies no tile; the release snapshot of H_t
+// writes the entry out (one tile copy), and a barrier raises every member's own entry to
+// its local time while it joins the members' tables, as it does for C_t.
 //
 // Publication: a writer fences after writing new tiles and before storing a table that
 // refers to them; tables are written once over SENTINEL words, so a reader accepts a
@@ -63,21 +66,38 @@ __device__ __forceinline__ uint4* tile_dst(const WideArgs& a, uint32_t id) {
   return reinterpret_cast<uint4*>(a.tiles + size_t(id) * kTileW) + (threadIdx.x & 31) * 2;
 }
 
-// a fresh tile id (warp-uniform); 0 when the pool is exhausted (GWCP_ERR_OOM set)
-__device__ __forceinline__ uint32_t alloc_tile(const WideArgs& a) {
-  unsigned long long id = 0;
-  if ((threadIdx.x & 31) == 0) {
-    id = atomicAdd(a.tile_ctr, 1ull);
-    if (id >= a.tile_cap) {
-      atomicCAS(&a.st->code, 0, GWCP_ERR_OOM);
-      id = 0;
+// Tile ids are handed to each warp kTileChunk at a time (one atomic per chunk instead of
+// one per tile on a single counter); the warp-uniform state lives in the walker.
+constexpr uint32_t kTileChunk = 8;
+struct TileAlloc {
+  uint32_t next = 0, end = 0;  // ids [next, end) are the warp's; both clamped to the pool size
+  uint32_t* cnt = nullptr;     // shared words: tiles read, tiles written (lane 0 adds)
+  __device__ __forceinline__ void count(uint32_t rd, uint32_t wr) const {
+    if ((threadIdx.x & 31) == 0) {
+      cnt[0] += rd;
+      cnt[1] += wr;
     }
   }
-  return uint32_t(__shfl_sync(0xffffffffu, id, 0));
+};
+
+// a fresh tile id (warp-uniform); 0 when the pool is exhausted (GWCP_ERR_OOM set)
+__device__ __forceinline__ uint32_t alloc_tile(const WideArgs& a, TileAlloc& ta) {
+  if (ta.next == ta.end) {
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31) == 0) base = atomicAdd(a.tile_ctr, (unsigned long long)kTileChunk);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    ta.next = uint32_t(min(base, a.tile_cap));
+    ta.end = uint32_t(min(base + kTileChunk, a.tile_cap));
+    if (ta.next == ta.end) {
+      if ((threadIdx.x & 31) == 0) atomicCAS(&a.st->code, 0, GWCP_ERR_OOM);
+      return 0;
+    }
+  }
+  return ta.next++;
 }
 
 // my |= src, tile by tile (lane T < nT holds the ids of tile T)
-__device__ void merge_table(const WideArgs& a, uint32_t& my, uint32_t src, bool& dirty) {
+__device__ void merge_table(const WideArgs& a, uint32_t& my, uint32_t src, bool& dirty, TileAlloc& ta) {
   const int lane = threadIdx.x & 31;
   bool need = lane < int(a.g.nT) && src != 0 && src != my;
   if (need && my == 0) {
@@ -96,10 +116,13 @@ __device__ void merge_table(const WideArgs& a, uint32_t& my, uint32_t src, bool&
     uint32_t nid;
     if (__all_sync(0xffffffffu, eq4(r0, x0) && eq4(r1, x1))) {
       nid = ia;
+      ta.count(2, 0);
     } else if (__all_sync(0xffffffffu, eq4(r0, y0) && eq4(r1, y1))) {
       nid = ib;
+      ta.count(2, 0);
     } else {
-      nid = alloc_tile(a);
+      nid = alloc_tile(a, ta);
+      ta.count(2, 1);
       if (nid) {
         uint4* d = tile_dst(a, nid);
         d[0] = r0;
@@ -114,7 +137,7 @@ __device__ void merge_table(const WideArgs& a, uint32_t& my, uint32_t src, bool&
 }
 
 // copy of tile `id` with entry e set to val; returns the new id (warp-uniform)
-__device__ uint32_t cow_set(const WideArgs& a, uint32_t id, uint32_t e, uint32_t val, bool& dirty) {
+__device__ uint32_t cow_set(const WideArgs& a, uint32_t id, uint32_t e, uint32_t val, bool& dirty, TileAlloc& ta) {
   const int lane = threadIdx.x & 31;
   const uint4* p = tile_src(a, id);
   uint4 x0 = __ldcg(p), x1 = __ldcg(p + 1);
@@ -126,7 +149,8 @@ __device__ uint32_t cow_set(const WideArgs& a, uint32_t id, uint32_t e, uint32_t
     if (c == 2) w[2] = val;
     if (c == 3) w[3] = val;
   }
-  const uint32_t nid = alloc_tile(a);
+  const uint32_t nid = alloc_tile(a, ta);
+  ta.count(1, 1);
   if (!nid) return id;
   uint4* d = tile_dst(a, nid);
   d[0] = x0;
@@ -136,10 +160,11 @@ __device__ uint32_t cow_set(const WideArgs& a, uint32_t id, uint32_t e, uint32_t
 }
 
 // entry t of the table held by the warp := val (copy of the tile holding t)
-__device__ __forceinline__ void set_entry_w(const WideArgs& a, uint32_t& my, uint32_t t, uint32_t val, bool& dirty) {
+__device__ __forceinline__ void set_entry_w(const WideArgs& a, uint32_t& my, uint32_t t, uint32_t val, bool& dirty,
+                                            TileAlloc& ta) {
   const uint32_t T = t / kTileW;
   const uint32_t id = __shfl_sync(0xffffffffu, my, T);
-  const uint32_t nid = cow_set(a, id, t % kTileW, val, dirty);
+  const uint32_t nid = cow_set(a, id, t % kTileW, val, dirty, ta);
   if ((threadIdx.x & 31) == int(T)) my = nid;
 }
 
@@ -176,46 +201,55 @@ __device__ __forceinline__ uint32_t entry_of(const WideArgs& a, uint32_t my, uin
   return ok ? __ldcg(a.tiles + size_t(id) * kTileW + t % kTileW) : 0u;
 }
 
-// Join of one tile over a CTA's members (lane m holds member m's id for the tile):
-// the result keeps a member's id when only one distinct tile is present and no epoch
-// override falls in it; otherwise the maximum (with the overrides C_m[u_m] = N_m) is
-// written as a new tile, or replaced by an input it equals.
+// Join of one tile over a CTA's members (lane m holds member m's id for the tile), with
+// the members' own entries raised to their local times (C_m[u_m] = N_m; H_m[u_m] = N_m,
+// which the walker keeps implicit). One pass over the distinct input tiles keeps the
+// running maximum and which input equals it so far (an input equals the final maximum
+// iff it is >= every other input); the result keeps that input's id when the own
+// entries raise nothing, else it is written as a new tile.
 __device__ uint32_t join_members(const WideArgs& a, uint32_t idm, uint32_t nm, uint32_t apb, uint32_t first,
-                                 uint32_t T, bool overrides, bool& dirty) {
+                                 uint32_t T, bool& dirty, TileAlloc& ta) {
   const int lane = threadIdx.x & 31;
   const bool act = uint32_t(lane) < apb && idm != 0;
   const uint32_t same = __match_any_sync(0xffffffffu, act ? idm : 0xFFFFFFFFu);
   const uint32_t leaders = __ballot_sync(0xffffffffu, act && (__ffs(same) - 1) == lane);
   // members whose own entry lies in tile T
   const uint32_t lo = T * kTileW, hi = lo + kTileW;
-  const bool own_here = overrides && uint32_t(lane) < apb && first + lane >= lo && first + lane < hi;
+  const bool own_here = uint32_t(lane) < apb && first + lane >= lo && first + lane < hi;
   const uint32_t ovm = __ballot_sync(0xffffffffu, own_here);
   if (!ovm && __popc(leaders) <= 1) return leaders ? __shfl_sync(0xffffffffu, idm, __ffs(leaders) - 1) : 0u;
   uint4 r0 = make_uint4(0, 0, 0, 0), r1 = r0;
+  bool have = leaders == 0;  // no input: the zero tile (id 0) equals the maximum so far
+  uint32_t cid = 0;          // id of an input equal to the maximum so far (when have)
   for (uint32_t m = leaders; m; m &= m - 1) {
     const uint32_t id = __shfl_sync(0xffffffffu, idm, __ffs(m) - 1);
     const uint4* p = tile_src(a, id);
-    r0 = max4(r0, __ldcg(p));
-    r1 = max4(r1, __ldcg(p + 1));
+    const uint4 x0 = __ldcg(p), x1 = __ldcg(p + 1);
+    const bool le = __all_sync(0xffffffffu, eq4(max4(r0, x0), r0) && eq4(max4(r1, x1), r1));  // x <= r
+    const bool ge = __all_sync(0xffffffffu, eq4(max4(r0, x0), x0) && eq4(max4(r1, x1), x1));  // x >= r
+    r0 = max4(r0, x0);
+    r1 = max4(r1, x1);
+    if (!(le && have)) cid = id;
+    have = (le && have) || ge;
   }
+  bool raised = false;
   for (uint32_t m = ovm; m; m &= m - 1) {
     const int mm = __ffs(m) - 1;
     const uint32_t e = first + mm - lo, val = __shfl_sync(0xffffffffu, nm, mm);
     if (lane == int(e >> 3)) {
       uint32_t* w = (e & 4) ? &r1.x : &r0.x;
       const uint32_t c = e & 3;
+      raised |= w[c] < val;
       if (c == 0) w[0] = max(w[0], val);
       if (c == 1) w[1] = max(w[1], val);
       if (c == 2) w[2] = max(w[2], val);
       if (c == 3) w[3] = max(w[3], val);
     }
   }
-  for (uint32_t m = leaders; m; m &= m - 1) {  // an input that equals the result keeps its id
-    const uint32_t id = __shfl_sync(0xffffffffu, idm, __ffs(m) - 1);
-    const uint4* p = tile_src(a, id);
-    if (__all_sync(0xffffffffu, eq4(r0, __ldcg(p)) && eq4(r1, __ldcg(p + 1)))) return id;
-  }
-  const uint32_t nid = alloc_tile(a);
+  const bool keep = have && !__any_sync(0xffffffffu, raised);
+  ta.count(__popc(leaders), keep ? 0u : 1u);
+  if (keep) return cid;
+  const uint32_t nid = alloc_tile(a, ta);
   if (!nid) return leaders ? __shfl_sync(0xffffffffu, idm, __ffs(leaders) - 1) : 0u;
   uint4* d = tile_dst(a, nid);
   d[0] = r0;
@@ -237,14 +271,19 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
   uint32_t* tabs = sm;                  // [apb][2][32] member tables
   uint32_t* nbuf = sm + apb * 64;       // [apb] member epochs
   uint32_t* J = nbuf + 32;              // [2][32] joined tables
+  uint32_t* tcnt = J + 64 + warp * 2;   // [apb][2] tiles this warp read and wrote (lane 0 counts)
   __shared__ int start_code;
   if (threadIdx.x == 0) start_code = *(volatile int*)&a.st->code;
   __syncthreads();
   if (start_code) return;
   const bool act = lane < int(g.nT);
   bool dirty = false, abort = false;
+  TileAlloc ta;
+  ta.cnt = tcnt;
+  if (lane == 0) tcnt[0] = tcnt[1] = 0;
+  // H_t = bottom{t := 1}: the table starts at bottom and H_t[t] = N_t is kept implicit (in
+  // N), so no tile is copied when it increments; a release snapshot writes it out
   uint32_t pid = 0, hid = 0;
-  set_entry_w(a, hid, u, 1u, dirty);  // H_t = bottom{t := 1}
   uint32_t N = 1;
   unsigned long long joins = 0, visits = 0;
   if (act) a.rows[size_t(a.rowbase[u]) * kTabW + lane] = a.hb_only ? hid : 0u;
@@ -276,11 +315,11 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
         if (t == P_ACQ) {
           const uint32_t sp = read_table(a, a.psnap + size_t(x) * kTabW, abort);
           const uint32_t sh = read_table(a, a.hsnap + size_t(x) * kTabW, abort);
-          merge_table(a, pid, sp, dirty);
-          merge_table(a, hid, sh, dirty);
+          merge_table(a, pid, sp, dirty, ta);
+          merge_table(a, hid, sh, dirty, ta);
           joins += 2;
         } else {
-          merge_table(a, pid, read_table(a, a.hsnap + size_t(x) * kTabW, abort), dirty);
+          merge_table(a, pid, read_table(a, a.hsnap + size_t(x) * kTabW, abort), dirty, ta);
           joins += 1;
         }
       }
@@ -313,7 +352,7 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
           visits += __popc(__ballot_sync(0xffffffffu, in && uint32_t(lane) <= f && !mine));
           for (uint32_t wm = wave; wm; wm &= wm - 1) {
             const uint32_t r = lo + cur + (__ffs(wm) - 1);
-            merge_table(a, pid, read_table(a, a.hsnap + size_t(r) * kTabW, abort), dirty);
+            merge_table(a, pid, read_table(a, a.hsnap + size_t(r) * kTabW, abort), dirty, ta);
             ++joins;
           }
           if (f == nbr) {
@@ -330,19 +369,17 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
         cur += start;
       }
       if (lane == 0) __stcg(cursor_row + L, cur);
+      uint32_t hp = hid;  // the snapshot of H_t carries its own entry N_t
+      set_entry_w(a, hp, u, N, dirty, ta);
       publish(a, a.psnap + size_t(c) * kTabW, pid, dirty);
-      publish(a, a.hsnap + size_t(c) * kTabW, hid, dirty);
-      set_entry_w(a, hid, u, N + 1, dirty);  // H_t[t] = N_t after the increment
-      ++N;
+      publish(a, a.hsnap + size_t(c) * kTabW, hp, dirty);
+      ++N;  // H_t[t] = N_t, implicit
     } else {
       // barrier: C and H joined over the members
       const uint32_t mode = eb.x;
-      if (eb.y != N) {  // forced compression at barriers: enter with the members' highest N
-        N = eb.y;
-        set_entry_w(a, hid, u, N, dirty);
-      }
+      if (eb.y != N) N = eb.y;  // forced compression at barriers: enter with the members' highest N
       if (mode == BAR_SINGLE) {
-        set_entry_w(a, pid, u, N, dirty);  // P_t = C_t
+        set_entry_w(a, pid, u, N, dirty, ta);  // P_t = C_t
       } else {
         if (act) {
           tabs[(warp * 2) * 32 + lane] = pid;
@@ -356,8 +393,8 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
           const bool mem = uint32_t(lane) < apb;
           const uint32_t cm = mem ? tabs[(lane * 2) * 32 + T] : 0, hm = mem ? tabs[(lane * 2 + 1) * 32 + T] : 0;
           const uint32_t nm = mem ? nbuf[lane] : 0;
-          const uint32_t jc = join_members(a, cm, nm, apb, first, T, true, wrote);
-          const uint32_t jh = join_members(a, hm, nm, apb, first, T, false, wrote);
+          const uint32_t jc = join_members(a, cm, nm, apb, first, T, wrote, ta);
+          const uint32_t jh = join_members(a, hm, nm, apb, first, T, wrote, ta);
           if (lane == 0) {
             J[T] = jc;
             J[32 + T] = jh;
@@ -367,12 +404,11 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
         __syncthreads();
         pid = act ? J[lane] : 0;
         hid = act ? J[32 + lane] : 0;
-        joins += 2 * nw;
+        joins += 2;  // this member's C_t and H_t joined into the block's
         // J is rewritten only after the next barrier's first __syncthreads, which every
         // member reaches after reading it here
       }
-      set_entry_w(a, hid, u, N + 1, dirty);
-      ++N;
+      ++N;  // H_t[t] = N_t, implicit
     }
     if (act) a.rows[size_t(row) * kTabW + lane] = a.hb_only ? hid : pid;
   }
@@ -380,6 +416,8 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
   if (lane == 0) {
     atomicAdd(&a.st->joins, joins);
     atomicAdd(&a.st->loop_visits, visits);
+    atomicAdd(&a.st->tiles_read, (unsigned long long)tcnt[0]);
+    atomicAdd(&a.st->tiles_written, (unsigned long long)tcnt[1]);
   }
 }
 
@@ -611,7 +649,7 @@ int phaseG_wide(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s) {
   a.n_locks = z.n_locks;
   a.hb_only = z.hb_only;
   const uint32_t threads = g.apb * 32;
-  const size_t smem = (size_t(g.apb) * 64 + 32 + 64) * 4;
+  const size_t smem = (size_t(g.apb) * 64 + 32 + 64 + 2 * size_t(g.apb)) * 4;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -25,7 +25,7 @@ EXPORTS = ("gwcp_create", "gwcp_load_trace", "gwcp_compute_order", "gwcp_report_
            "gwcp_pool_device_bytes", "gwcp_pool_destroy", "gwcp_set_ranker", "gwcp_location_features",
            "gwcp_rank_scores", "gwcp_rank_grad", "gwcp_rank_train", "gwcp_check_timeline", "gwcp_set_clock_mode",
            "gwcp_pool_clock_modes", "gwcp_set_check_mode", "gwcp_debug_wait_timeout", "gwcp_pool_settings",
-           "gwcp_clock_bytes", "gwcp_debug_alloc_limit")
+           "gwcp_clock_bytes", "gwcp_debug_alloc_limit", "gwcp_counters_ex")
 CLOCKS_AUTO, CLOCKS_DENSE, CLOCKS_TILES, CLOCKS_COMPRESSED = 0, 1, 2, 3
 CHECK_AUTO, CHECK_CHUNKED, CHECK_SPARSE = 0, 1, 2
 
@@ -99,6 +99,7 @@ def load_library():
     L.gwcp_profile_get.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(ctypes.c_double)]
     L.gwcp_counters.argtypes = [vp, ctypes.POINTER(u64)]
+    L.gwcp_counters_ex.argtypes = [vp, ctypes.POINTER(u64), ctypes.c_uint32]
     L.gwcp_clock_bytes.argtypes = [vp, ctypes.POINTER(u64)]
     L.gwcp_debug_alloc_limit.argtypes = [vp, u64]
     L.gwcp_debug_alloc_limit.restype = i32
@@ -150,7 +151,7 @@ def load_library():
     L.gwcp_strerror.argtypes = [i32]
     L.gwcp_strerror.restype = ctypes.c_char_p
     for name in ("gwcp_create", "gwcp_load_trace", "gwcp_compute_order", "gwcp_report_races", "gwcp_debug_clock",
-                 "gwcp_profile_get", "gwcp_counters"):
+                 "gwcp_profile_get", "gwcp_counters", "gwcp_counters_ex"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -344,10 +345,10 @@ class Context:
         return out
 
     def counters(self) -> dict:
-        a = (ctypes.c_uint64 * 8)()
-        self._L.gwcp_counters(self._h, a)
+        a = (ctypes.c_uint64 * 10)()
+        self._L.gwcp_counters_ex(self._h, a, 10)
         keys = ("accesses", "sync_entries", "critical_sections", "in_section_accesses", "clock_versions",
-                "partner_tests", "loop_visits", "joins")
+                "partner_tests", "loop_visits", "joins", "tiles_read", "tiles_written")
         return dict(zip(keys, [int(v) for v in a]))
 
     def debug_alloc_limit(self, nbytes: int):

@@ -38,7 +38,7 @@ def test_serve_requests_are_poisson():
 
 
 def test_location_keys_match_the_oracles():
-    from paper_2111_12478_gb300 import ranker
+    import ranker_metrics as ranker
 
     ev, _ = TG.random_small(4, "mixed", n_events=300, num_agents=16, agents_per_block=4)
     acc = ev[ev["op"] <= TG.ATOMIC]
@@ -46,7 +46,7 @@ def test_location_keys_match_the_oracles():
 
 
 def test_racy_location_recall_by_brute_force():
-    from paper_2111_12478_gb300 import ranker
+    import ranker_metrics as ranker
 
     ev, _ = TG.random_small(5, "nosync", n_events=200, num_agents=8, agents_per_block=4, n_keys=12)
     keys = np.unique(ranker.location_keys(ev[ev["op"] <= TG.ATOMIC], 4))
