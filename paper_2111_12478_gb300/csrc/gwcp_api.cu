@@ -400,6 +400,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   b.flat_off = get<uint32_t>(c, "flat_off", ni1, &oom);
   b.flat = get<uint32_t>(c, "flat", z.pool_cap, &oom);
   b.cursor = get<uint32_t>(c, "cursor", size_t(g.W) * (z.n_locks + 1), &oom);
+  b.jsnap = g.nT ? get<uint32_t>(c, "jsnap", (size_t(z.n_cs) + 1) * g.RW, &oom) : nullptr;
   const size_t smem = size_t(2) * g.apb * 2 * g.Wp * 4;
   z.cta_barriers = g.nT ? true : (g.apb <= 32 && smem <= 96 * 1024);
   const bool global_bars = !z.cta_barriers || g.gran == GWCP_GRAN_THREAD;

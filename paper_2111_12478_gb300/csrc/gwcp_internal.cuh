@@ -160,6 +160,7 @@ struct Bufs {
   uint32_t* tiles = nullptr;    // wide clocks: [tile_cap * kTileW] tile pool, tile 0 = zeros
   uint32_t* done = nullptr;     // [n_cs]
   uint32_t* cursor = nullptr;   // [W * n_locks]
+  uint32_t* jsnap = nullptr;    // wide clocks: [n_cs * RW] JN tables published at releases
   uint32_t* bar_j = nullptr;    // [n_bar * 2 * Wp] global-barrier joins
   uint32_t* bar_cnt = nullptr;  // [n_bar]
   // forced compression at barriers: barriers by block, their members' records, offsets

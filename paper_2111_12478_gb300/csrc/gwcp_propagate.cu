@@ -980,6 +980,7 @@ int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s
     // snapshot rows start as SENTINEL: a reader accepts a row once none is left
     cudaMemsetAsync(b.psnap, 0xFF, size_t(z.n_cs) * g.RW * 4, s);
     cudaMemsetAsync(b.hsnap, 0xFF, size_t(z.n_cs) * g.RW * 4, s);
+    if (g.nT) cudaMemsetAsync(b.jsnap, 0xFF, size_t(z.n_cs) * g.RW * 4, s);
   }
   if (z.n_incs) {
     k_flatcount<<<(z.n_incs + 255) / 256, 256, 0, s>>>(z.n_incs, b.exp_off, b.ex_dep_cnt, b.flat_off, b.st);

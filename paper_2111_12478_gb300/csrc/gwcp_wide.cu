@@ -46,7 +46,7 @@ struct WideArgs {
   const uint4* plan;
   const uint4* recmeta;
   const uint32_t *pool, *flat;
-  uint32_t *rows, *psnap, *hsnap, *cursor;
+  uint32_t *rows, *psnap, *hsnap, *jsnap, *cursor;
   uint32_t* tiles;
   unsigned long long* tile_ctr;
   unsigned long long tile_cap;
@@ -64,6 +64,36 @@ __device__ __forceinline__ const uint4* tile_src(const WideArgs& a, uint32_t id)
 }
 __device__ __forceinline__ uint4* tile_dst(const WideArgs& a, uint32_t id) {
   return reinterpret_cast<uint4*>(a.tiles + size_t(id) * kTileW) + (threadIdx.x & 31) * 2;
+}
+
+// A lane holds 8 consecutive entries of a tile as (x0, x1). These update entry c (0..7)
+// with register selects only, so the pair is never addressed through memory.
+__device__ __forceinline__ uint32_t sel_raise(uint32_t x, bool hit, uint32_t val, bool& up) {
+  const bool h = hit && x < val;
+  up |= h;
+  return h ? val : x;
+}
+__device__ __forceinline__ bool raise8(uint4& x0, uint4& x1, uint32_t c, uint32_t val) {
+  bool up = false;
+  x0.x = sel_raise(x0.x, c == 0, val, up);
+  x0.y = sel_raise(x0.y, c == 1, val, up);
+  x0.z = sel_raise(x0.z, c == 2, val, up);
+  x0.w = sel_raise(x0.w, c == 3, val, up);
+  x1.x = sel_raise(x1.x, c == 4, val, up);
+  x1.y = sel_raise(x1.y, c == 5, val, up);
+  x1.z = sel_raise(x1.z, c == 6, val, up);
+  x1.w = sel_raise(x1.w, c == 7, val, up);
+  return up;
+}
+__device__ __forceinline__ void set8(uint4& x0, uint4& x1, uint32_t c, uint32_t val) {
+  x0.x = c == 0 ? val : x0.x;
+  x0.y = c == 1 ? val : x0.y;
+  x0.z = c == 2 ? val : x0.z;
+  x0.w = c == 3 ? val : x0.w;
+  x1.x = c == 4 ? val : x1.x;
+  x1.y = c == 5 ? val : x1.y;
+  x1.z = c == 6 ? val : x1.z;
+  x1.w = c == 7 ? val : x1.w;
 }
 
 // Tile ids are handed to each warp kTileChunk at a time (one atomic per chunk instead of
@@ -97,7 +127,7 @@ __device__ __forceinline__ uint32_t alloc_tile(const WideArgs& a, TileAlloc& ta)
 }
 
 // my |= src, tile by tile (lane T < nT holds the ids of tile T)
-__device__ void merge_table(const WideArgs& a, uint32_t& my, uint32_t src, bool& dirty, TileAlloc& ta) {
+__device__ __noinline__ void merge_table(const WideArgs& a, uint32_t& my, uint32_t src, bool& dirty, TileAlloc& ta) {
   const int lane = threadIdx.x & 31;
   bool need = lane < int(a.g.nT) && src != 0 && src != my;
   if (need && my == 0) {
@@ -137,18 +167,11 @@ __device__ void merge_table(const WideArgs& a, uint32_t& my, uint32_t src, bool&
 }
 
 // copy of tile `id` with entry e set to val; returns the new id (warp-uniform)
-__device__ uint32_t cow_set(const WideArgs& a, uint32_t id, uint32_t e, uint32_t val, bool& dirty, TileAlloc& ta) {
+__device__ __forceinline__ uint32_t cow_set(const WideArgs& a, uint32_t id, uint32_t e, uint32_t val, bool& dirty, TileAlloc& ta) {
   const int lane = threadIdx.x & 31;
   const uint4* p = tile_src(a, id);
   uint4 x0 = __ldcg(p), x1 = __ldcg(p + 1);
-  if (lane == int(e >> 3)) {
-    uint32_t* w = (e & 4) ? &x1.x : &x0.x;
-    const uint32_t c = e & 3;
-    if (c == 0) w[0] = val;
-    if (c == 1) w[1] = val;
-    if (c == 2) w[2] = val;
-    if (c == 3) w[3] = val;
-  }
+  if (lane == int(e >> 3)) set8(x0, x1, e & 7, val);
   const uint32_t nid = alloc_tile(a, ta);
   ta.count(1, 1);
   if (!nid) return id;
@@ -169,7 +192,7 @@ __device__ __forceinline__ void set_entry_w(const WideArgs& a, uint32_t& my, uin
 }
 
 // a published table: wait (bounded) until none of its nT words is SENTINEL
-__device__ uint32_t read_table(const WideArgs& a, const uint32_t* tab, bool& abort) {
+__device__ __forceinline__ uint32_t read_table(const WideArgs& a, const uint32_t* tab, bool& abort) {
   const int lane = threadIdx.x & 31;
   const bool act = lane < int(a.g.nT);
   uint32_t v = act ? __ldcg(tab + lane) : 0;
@@ -207,15 +230,15 @@ __device__ __forceinline__ uint32_t entry_of(const WideArgs& a, uint32_t my, uin
 // running maximum and which input equals it so far (an input equals the final maximum
 // iff it is >= every other input); the result keeps that input's id when the own
 // entries raise nothing, else it is written as a new tile.
-__device__ uint32_t join_members(const WideArgs& a, uint32_t idm, uint32_t nm, uint32_t apb, uint32_t first,
-                                 uint32_t T, bool& dirty, TileAlloc& ta) {
+__device__ __noinline__ uint32_t join_members(const WideArgs& a, uint32_t idm, uint32_t nm, uint32_t apb, uint32_t first,
+                                 uint32_t T, bool own, bool& dirty, TileAlloc& ta) {
   const int lane = threadIdx.x & 31;
   const bool act = uint32_t(lane) < apb && idm != 0;
   const uint32_t same = __match_any_sync(0xffffffffu, act ? idm : 0xFFFFFFFFu);
   const uint32_t leaders = __ballot_sync(0xffffffffu, act && (__ffs(same) - 1) == lane);
   // members whose own entry lies in tile T
   const uint32_t lo = T * kTileW, hi = lo + kTileW;
-  const bool own_here = uint32_t(lane) < apb && first + lane >= lo && first + lane < hi;
+  const bool own_here = own && uint32_t(lane) < apb && first + lane >= lo && first + lane < hi;
   const uint32_t ovm = __ballot_sync(0xffffffffu, own_here);
   if (!ovm && __popc(leaders) <= 1) return leaders ? __shfl_sync(0xffffffffu, idm, __ffs(leaders) - 1) : 0u;
   uint4 r0 = make_uint4(0, 0, 0, 0), r1 = r0;
@@ -236,15 +259,7 @@ __device__ uint32_t join_members(const WideArgs& a, uint32_t idm, uint32_t nm, u
   for (uint32_t m = ovm; m; m &= m - 1) {
     const int mm = __ffs(m) - 1;
     const uint32_t e = first + mm - lo, val = __shfl_sync(0xffffffffu, nm, mm);
-    if (lane == int(e >> 3)) {
-      uint32_t* w = (e & 4) ? &r1.x : &r0.x;
-      const uint32_t c = e & 3;
-      raised |= w[c] < val;
-      if (c == 0) w[0] = max(w[0], val);
-      if (c == 1) w[1] = max(w[1], val);
-      if (c == 2) w[2] = max(w[2], val);
-      if (c == 3) w[3] = max(w[3], val);
-    }
+    if (lane == int(e >> 3)) raised |= raise8(r0, r1, e & 7, val);
   }
   const bool keep = have && !__any_sync(0xffffffffu, raised);
   ta.count(__popc(leaders), keep ? 0u : 1u);
@@ -268,10 +283,10 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
   const uint32_t apb = g.apb;
   const uint32_t first = blockIdx.x * apb;
   const uint32_t u = first + warp;
-  uint32_t* tabs = sm;                  // [apb][2][32] member tables
-  uint32_t* nbuf = sm + apb * 64;       // [apb] member epochs
-  uint32_t* J = nbuf + 32;              // [2][32] joined tables
-  uint32_t* tcnt = J + 64 + warp * 2;   // [apb][2] tiles this warp read and wrote (lane 0 counts)
+  uint32_t* tabs = sm;                  // [apb][3][32] member tables (P, H, JN)
+  uint32_t* nbuf = sm + apb * 96;       // [apb] member epochs
+  uint32_t* J = nbuf + 32;              // [3][32] joined tables
+  uint32_t* tcnt = J + 96 + warp * 2;   // [apb][2] tiles this warp read and wrote (lane 0 counts)
   __shared__ int start_code;
   if (threadIdx.x == 0) start_code = *(volatile int*)&a.st->code;
   __syncthreads();
@@ -283,7 +298,11 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
   if (lane == 0) tcnt[0] = tcnt[1] = 0;
   // H_t = bottom{t := 1}: the table starts at bottom and H_t[t] = N_t is kept implicit (in
   // N), so no tile is copied when it increments; a release snapshot writes it out
-  uint32_t pid = 0, hid = 0;
+  // JN_t (jid): the join of every H snapshot joined into P_t, carried along with P_t (joined
+  // at acquires from the lock's published JN, at barriers over the members). H moves only by
+  // whole-clock joins, so JN_t[v] >= e means P_t already holds the H snapshot of v's release
+  // at epoch e: such a join (release loop, in-section access) changes nothing and is skipped.
+  uint32_t pid = 0, hid = 0, jid = 0;
   uint32_t N = 1;
   unsigned long long joins = 0, visits = 0;
   if (act) a.rows[size_t(a.rowbase[u]) * kTabW + lane] = a.hb_only ? hid : 0u;
@@ -315,12 +334,20 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
         if (t == P_ACQ) {
           const uint32_t sp = read_table(a, a.psnap + size_t(x) * kTabW, abort);
           const uint32_t sh = read_table(a, a.hsnap + size_t(x) * kTabW, abort);
+          const uint32_t sj = read_table(a, a.jsnap + size_t(x) * kTabW, abort);
           merge_table(a, pid, sp, dirty, ta);
           merge_table(a, hid, sh, dirty, ta);
+          merge_table(a, jid, sj, dirty, ta);
           joins += 2;
         } else {
-          merge_table(a, pid, read_table(a, a.hsnap + size_t(x) * kTabW, abort), dirty, ta);
-          joins += 1;
+          // L^w / L^r: the H snapshot of section x's release, unless JN_t already covers it
+          const uint4 mx = __ldg(a.recmeta + x);
+          if (entry_of(a, jid, mx.x & 0xFFFF) < mx.w) {
+            const uint32_t sx = read_table(a, a.hsnap + size_t(x) * kTabW, abort);
+            merge_table(a, pid, sx, dirty, ta);
+            merge_table(a, jid, sx, dirty, ta);
+            joins += 1;
+          }
         }
       }
     } else if (t == P_REL) {
@@ -340,19 +367,23 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
         const bool mine = mag == u;
         const bool joinable = !mine && m.z != NONE && m.z < my_idx && scopes_overlap(msid, s);
         uint32_t start = 0;
-        uint32_t pv = entry_of(a, pid, mag);
+        uint32_t pv = entry_of(a, pid, mag), jv = entry_of(a, jid, mag);
         while (start < nbr) {
           const bool in = uint32_t(lane) >= start && uint32_t(lane) < nbr;
           const uint32_t fail = __ballot_sync(0xffffffffu, in && !mine && m.y > pv);
           const uint32_t f = fail ? uint32_t(__ffs(fail) - 1) : nbr;
           const uint32_t popped = __ballot_sync(0xffffffffu, in && uint32_t(lane) < f && joinable);
-          // of one agent's popped records only the latest is joined (its H dominates)
-          const uint32_t same = __match_any_sync(0xffffffffu, ((popped >> lane) & 1u) ? mag : 0xFFFFFFFFu);
-          const uint32_t wave = __ballot_sync(0xffffffffu, ((popped >> lane) & 1u) && (same >> lane) <= 1u);
+          // join only releases not already in P, and of one agent's popped records only the
+          // latest (records of one agent are in acquire order, so its H dominates)
+          const bool cand = ((popped >> lane) & 1u) && m.w > jv;
+          const uint32_t same = __match_any_sync(0xffffffffu, cand ? mag : 0xFFFFFFFFu);
+          const uint32_t wave = __ballot_sync(0xffffffffu, cand && (same >> lane) <= 1u);
           visits += __popc(__ballot_sync(0xffffffffu, in && uint32_t(lane) <= f && !mine));
           for (uint32_t wm = wave; wm; wm &= wm - 1) {
             const uint32_t r = lo + cur + (__ffs(wm) - 1);
-            merge_table(a, pid, read_table(a, a.hsnap + size_t(r) * kTabW, abort), dirty, ta);
+            const uint32_t sx = read_table(a, a.hsnap + size_t(r) * kTabW, abort);
+            merge_table(a, pid, sx, dirty, ta);
+            merge_table(a, jid, sx, dirty, ta);
             ++joins;
           }
           if (f == nbr) {
@@ -360,6 +391,7 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
           } else if (wave) {
             start = f;  // P grew: test the failing record again
             pv = entry_of(a, pid, mag);
+            jv = entry_of(a, jid, mag);
           } else {
             stop = true;  // P unchanged: the record stays unordered
             start = f;
@@ -373,6 +405,7 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
       set_entry_w(a, hp, u, N, dirty, ta);
       publish(a, a.psnap + size_t(c) * kTabW, pid, dirty);
       publish(a, a.hsnap + size_t(c) * kTabW, hp, dirty);
+      publish(a, a.jsnap + size_t(c) * kTabW, jid, dirty);
       ++N;  // H_t[t] = N_t, implicit
     } else {
       // barrier: C and H joined over the members
@@ -382,8 +415,9 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
         set_entry_w(a, pid, u, N, dirty, ta);  // P_t = C_t
       } else {
         if (act) {
-          tabs[(warp * 2) * 32 + lane] = pid;
-          tabs[(warp * 2 + 1) * 32 + lane] = hid;
+          tabs[(warp * 3) * 32 + lane] = pid;
+          tabs[(warp * 3 + 1) * 32 + lane] = hid;
+          tabs[(warp * 3 + 2) * 32 + lane] = jid;
         }
         if (lane == 0) nbuf[warp] = N;
         __syncthreads();
@@ -391,19 +425,23 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
         bool wrote = false;
         for (uint32_t T = warp; T < g.nT; T += nw) {
           const bool mem = uint32_t(lane) < apb;
-          const uint32_t cm = mem ? tabs[(lane * 2) * 32 + T] : 0, hm = mem ? tabs[(lane * 2 + 1) * 32 + T] : 0;
+          const uint32_t cm = mem ? tabs[(lane * 3) * 32 + T] : 0, hm = mem ? tabs[(lane * 3 + 1) * 32 + T] : 0;
+          const uint32_t jm = mem ? tabs[(lane * 3 + 2) * 32 + T] : 0;
           const uint32_t nm = mem ? nbuf[lane] : 0;
-          const uint32_t jc = join_members(a, cm, nm, apb, first, T, wrote, ta);
-          const uint32_t jh = join_members(a, hm, nm, apb, first, T, wrote, ta);
+          const uint32_t jc = join_members(a, cm, nm, apb, first, T, true, wrote, ta);
+          const uint32_t jh = join_members(a, hm, nm, apb, first, T, true, wrote, ta);
+          const uint32_t jj = join_members(a, jm, nm, apb, first, T, false, wrote, ta);
           if (lane == 0) {
             J[T] = jc;
             J[32 + T] = jh;
+            J[64 + T] = jj;
           }
         }
         if (wrote) __threadfence();  // members may publish the joined tiles at once
         __syncthreads();
         pid = act ? J[lane] : 0;
         hid = act ? J[32 + lane] : 0;
+        jid = act ? J[64 + lane] : 0;
         joins += 2;  // this member's C_t and H_t joined into the block's
         // J is rewritten only after the next barrier's first __syncthreads, which every
         // member reaches after reading it here
@@ -643,13 +681,14 @@ int phaseG_wide(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s) {
   a.psnap = b.psnap;
   a.hsnap = b.hsnap;
   a.cursor = b.cursor;
+  a.jsnap = b.jsnap;
   a.tiles = b.tiles;
   a.tile_ctr = reinterpret_cast<unsigned long long*>(&b.st->spare[2]);
   a.tile_cap = z.tile_cap;
   a.n_locks = z.n_locks;
   a.hb_only = z.hb_only;
   const uint32_t threads = g.apb * 32;
-  const size_t smem = (size_t(g.apb) * 64 + 32 + 64 + 2 * size_t(g.apb)) * 4;
+  const size_t smem = (size_t(g.apb) * 96 + 32 + 96 + 2 * size_t(g.apb)) * 4;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -178,9 +178,10 @@ class Context:
     """One analysis context on one CUDA device (gwcp_ctx)."""
 
     def __init__(self, device: int = 0, race_capacity: int = 0, profile: bool = False, timeline: bool = False,
-                 hb_only: bool = False, forced_barrier: bool = False):
+                 hb_only: bool = False, forced_barrier: bool = False, pack_walkers: bool = False):
         L = load_library()
-        opt = Options(race_capacity, int(profile), 0, int(timeline), int(hb_only), 0, int(forced_barrier))
+        opt = Options(race_capacity, int(profile), 0, int(timeline), int(hb_only), int(pack_walkers),
+                      int(forced_barrier))
         h = ctypes.c_void_p()
         rc = L.gwcp_create(ctypes.byref(h), device, ctypes.byref(opt))
         if rc:
