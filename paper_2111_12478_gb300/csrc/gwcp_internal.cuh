@@ -106,6 +106,7 @@ struct Bufs {
   uint32_t* sy_ver = nullptr;    // version index after the entry
   uint32_t* sy_match = nullptr;  // REL: its acquire; ACQ: the enclosing acquire
   uint32_t* sy_relk = nullptr;   // ACQ: the matching release (NONE if never released)
+  uint32_t* sy_agent = nullptr;  // agent of the entry
   uint32_t* incs_cnt = nullptr;  // [n_sync + 1] in-section accesses in the gap after k
   uint32_t* vcount = nullptr;    // [W + 1] versions per agent -> row base (scanned)
   // phase D: accesses

@@ -284,7 +284,8 @@ __global__ void k_b_starts(const uint32_t* seg, uint32_t W, const uint32_t* sy_s
 __global__ void k_c_walk(const Event* ev, Geo g, const uint32_t* seg, const uint32_t* sy_start,
                          const uint32_t* sy_spos, const uint32_t* sy_idx, const uint32_t* sy_kind, uint32_t* sy_N,
                          uint32_t* sy_depth, uint32_t* sy_inner, uint32_t* sy_ver, uint32_t* sy_match,
-                         uint32_t* sy_relk, uint32_t* incs_cnt, uint32_t* vcount, DevStatus* st) {
+                         uint32_t* sy_relk, uint32_t* incs_cnt, uint32_t* vcount, uint32_t* sy_agent,
+                         DevStatus* st) {
   const int lane = threadIdx.x & 31;
   const uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (u >= g.W) return;
@@ -366,6 +367,7 @@ __global__ void k_c_walk(const Event* ev, Geo g, const uint32_t* seg, const uint
       if (kind == K_REL && d_before > 0 && (match == NONE || mlock != lock || msid != sid))
         set_error(st, GWCP_ERR_INVALID_TRACE, idx);
       sy_N[k] = N_after;
+      sy_agent[k] = u;
       sy_depth[k] = uint32_t(max(d_after, 0));
       sy_inner[k] = d_after > 0 ? inner : NONE;
       sy_ver[k] = ver_after;
@@ -391,7 +393,8 @@ __global__ void k_c_walk(const Event* ev, Geo g, const uint32_t* seg, const uint
 
 // Phase D: one warp per gap between consecutive synchronisation entries of an agent.
 __global__ void k_d_fill(const Event* ev, Geo g, uint32_t n_sync, const uint32_t* S, const uint32_t* seg,
-                         const uint32_t* sy_start, const uint32_t* sy_spos, const uint32_t* sy_N,
+                         const uint32_t* sy_start, const uint32_t* sy_agent, const uint32_t* sy_spos,
+                         const uint32_t* sy_N,
                          const uint32_t* sy_depth, const uint32_t* sy_ver, const uint32_t* incs_off,
                          const uint32_t* rowbase, AccInfo* acc_info, uint32_t* incs_idx, uint32_t* incs_ver,
                          uint32_t* incs_k, uint64_t* incs_key, uint32_t* incs_wr, const DevStatus* st) {
@@ -408,7 +411,7 @@ __global__ void k_d_fill(const Event* ev, Geo g, uint32_t n_sync, const uint32_t
     vbase = 0;
   } else {
     k = uint32_t(gid - g.W);
-    u = lower_bound_dev(sy_start, g.W + 1, k + 1) - 1;  // last agent whose start <= k
+    u = sy_agent[k];
     lo = sy_spos[k] + 1;
     hi = (k + 1 < sy_start[u + 1]) ? sy_spos[k + 1] : seg[u + 1];
     epoch = sy_N[k];
@@ -478,12 +481,12 @@ __global__ void k_fb_rank(const Event* ev, Geo g, const uint32_t* bar, const uin
 }
 
 // one record per barrier participation, grouped by barrier in block order
-__global__ void k_fb_records(const Event* ev, Geo g, uint32_t n_sync, uint32_t n_bar, const uint32_t* sy_start,
+__global__ void k_fb_records(const Event* ev, Geo g, uint32_t n_sync, uint32_t n_bar, const uint32_t* sy_agent,
                              const uint32_t* sy_kind, const uint32_t* sy_idx, const uint32_t* sy_aux,
                              const uint32_t* sy_N, const uint32_t* rank, const uint32_t* off, uint4* rec) {
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_sync || sy_kind[k] != K_BAR) return;
-  const uint32_t u = lower_bound_dev(sy_start, g.W + 1, k + 1) - 1;  // last agent whose start <= k
+  const uint32_t u = sy_agent[k];
   const BarMembers m = barrier_members(ev[sy_idx[k]], g);
   const uint32_t d = u - m.first, pos = sy_aux[k];
   if (!m.ok || d >= (m.mask ? 32u : m.count) || pos >= n_bar) return;  // not on a validated trace
@@ -904,7 +907,7 @@ void phaseC_walk(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Pr
   cudaMemsetAsync(b.incs_cnt, 0, size_t(z.n_sync + 1) * 4, s);
   k_c_walk<<<blocks(uint64_t(g.W) * 32, 128), 128, 0, s>>>(b.ev, g, b.seg, b.sy_start, b.sy_spos, b.sy_idx, b.sy_kind,
                                                            b.sy_N, b.sy_depth, b.sy_inner, b.sy_ver, b.sy_match,
-                                                           b.sy_relk, b.incs_cnt, b.vcount, b.st);
+                                                           b.sy_relk, b.incs_cnt, b.vcount, b.sy_agent, b.st);
   count_launch();
   p.end();
   scan_exclusive(b.incs_cnt, b.incs_cnt, z.n_sync + 1, nullptr, b.scan_tmp, s);
@@ -927,7 +930,7 @@ void phaseC_forced(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, 
   count_launch();
   scan_exclusive(b.fb_off, b.fb_off, size_t(n) + 1, nullptr, b.scan_tmp, s);
   cudaMemsetAsync(b.fb_boff, 0xFF, size_t(z.n_sync + 1) * 4, s);
-  k_fb_records<<<blocks(z.n_sync, 256), 256, 0, s>>>(b.ev, g, z.n_sync, n, b.sy_start, b.sy_kind, b.sy_idx, b.sy_aux,
+  k_fb_records<<<blocks(z.n_sync, 256), 256, 0, s>>>(b.ev, g, z.n_sync, n, b.sy_agent, b.sy_kind, b.sy_idx, b.sy_aux,
                                                      b.sy_N, b.fb_rank, b.fb_off, b.fb_rec);
   count_launch();
   k_fb_walk<<<g.B, 32, 0, s>>>(g, z.n_sync, b.fb_blo, b.fb_off, b.fb_rec, b.fb_boff, b.st);
@@ -940,7 +943,8 @@ void phaseC_forced(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, 
 void phaseD_gaps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   p.begin("d_gaps", double(z.n_acc) * (4 + 16 + 16), s);
   const uint64_t gaps = uint64_t(g.W) + z.n_sync;
-  k_d_fill<<<blocks(gaps * 32, 256), 256, 0, s>>>(b.ev, g, z.n_sync, b.S, b.seg, b.sy_start, b.sy_spos, b.sy_N,
+  k_d_fill<<<blocks(gaps * 32, 256), 256, 0, s>>>(b.ev, g, z.n_sync, b.S, b.seg, b.sy_start, b.sy_agent, b.sy_spos,
+                                                  b.sy_N,
                                                   b.sy_depth, b.sy_ver, b.incs_cnt, b.vcount, b.acc_info, b.incs_idx,
                                                   b.incs_ver, b.incs_k, b.incs_key, b.incs_wr, b.st);
   count_launch();

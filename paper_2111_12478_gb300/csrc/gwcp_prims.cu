@@ -92,14 +92,24 @@ __global__ void k_radix_hist(const uint64_t* keys, size_t n, int shift, uint32_t
 }
 
 // Stable scatter: warp w of a tile owns items [w*256, w*256+256) of the tile, visited in
-// rounds of 32 consecutive items; ranks within a round follow lane order.
-__global__ void k_radix_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
-                                size_t n, int shift, const uint32_t* offs, uint32_t ntiles) {
+// rounds of 32 consecutive items; ranks within a round follow lane order. The tile is
+// first put in digit order in shared memory, then written out so that consecutive threads
+// write consecutive positions of one digit's run (coalesced stores instead of one sector
+// per item).
+__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint64_t* kin, const uint32_t* vin,
+                                                              uint64_t* kout, uint32_t* vout, size_t n, int shift,
+                                                              const uint32_t* offs, uint32_t ntiles) {
   __shared__ uint32_t cnt[RS_THREADS / 32][256];
+  __shared__ uint32_t tile_off[256];  // first position of each digit in the tile's digit order
+  __shared__ uint32_t glob[256];      // global position of the tile's first item of each digit
+  __shared__ uint64_t sk[RS_TILE];
+  __shared__ uint32_t sv[RS_TILE];
+  __shared__ uint32_t tot;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int d = lane; d < 256; d += 32) cnt[warp][d] = 0;
   __syncwarp();
-  const size_t base = size_t(blockIdx.x) * RS_TILE + size_t(warp) * (RS_ITEMS * 32);
+  const size_t tile_base = size_t(blockIdx.x) * RS_TILE;
+  const size_t base = tile_base + size_t(warp) * (RS_ITEMS * 32);
   uint64_t k[RS_ITEMS];
   uint32_t v[RS_ITEMS], dig[RS_ITEMS], rank[RS_ITEMS];
   const uint32_t lt = lanemask_lt();
@@ -121,23 +131,34 @@ __global__ void k_radix_scatter(const uint64_t* kin, const uint32_t* vin, uint64
   }
   __syncthreads();
   {
-    const uint32_t d = threadIdx.x;  // one digit per thread
-    uint32_t run = offs[size_t(d) * ntiles + blockIdx.x];
+    const uint32_t d = threadIdx.x;  // one digit per thread: warp prefixes, tile count
+    uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < RS_THREADS / 32; ++w) {
       uint32_t t = cnt[w][d];
       cnt[w][d] = run;
       run += t;
     }
+    glob[d] = offs[size_t(d) * ntiles + blockIdx.x];
+    tile_off[d] = block_exclusive_scan(run, &tot);
   }
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < RS_ITEMS; ++r) {
     if (dig[r] < 256) {
-      uint32_t pos = cnt[warp][dig[r]] + rank[r];
-      kout[pos] = k[r];
-      if (vout) vout[pos] = v[r];
+      const uint32_t lp = tile_off[dig[r]] + cnt[warp][dig[r]] + rank[r];
+      sk[lp] = k[r];
+      sv[lp] = v[r];
     }
+  }
+  __syncthreads();
+  const uint32_t nvalid = n - tile_base < size_t(RS_TILE) ? uint32_t(n - tile_base) : uint32_t(RS_TILE);
+  for (uint32_t i = threadIdx.x; i < nvalid; i += RS_THREADS) {
+    const uint64_t key = sk[i];
+    const uint32_t d = uint32_t((key >> shift) & 255u);
+    const uint32_t pos = glob[d] + (i - tile_off[d]);
+    kout[pos] = key;
+    if (vout) vout[pos] = sv[i];
   }
 }
 

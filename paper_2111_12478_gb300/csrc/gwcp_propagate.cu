@@ -30,7 +30,7 @@ struct PropArgs {
   Geo g;
   const Event* ev;
   DevStatus* st;
-  const uint32_t *sy_start, *sy_idx, *sy_kind, *sy_N, *sy_ver, *sy_aux;
+  const uint32_t *sy_start, *sy_idx, *sy_kind, *sy_N, *sy_ver, *sy_aux, *sy_agent;
   const uint32_t *incs_off, *incs_ver, *incs_k, *exp_off, *ex_dep_off, *ex_dep_cnt;
   const uint32_t* rowbase;
   const uint32_t *cs_of_sync, *cs_agent, *cs_sid, *cs_epoch, *cs_rel_idx, *cs_lock, *lock_cs_lo, *cs_rel_epoch;
@@ -757,17 +757,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_propagate(PropArgs a) {
 
 // ---- plan construction -------------------------------------------------------------
 
-__device__ __forceinline__ uint32_t agent_of_sync(const uint32_t* sy_start, uint32_t W, uint32_t k) {
-  uint32_t lo = 0, hi = W + 1;  // last u with sy_start[u] <= k
-  while (lo < hi) {
-    uint32_t mid = (lo + hi) >> 1;
-    if (sy_start[mid] <= k)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  return lo - 1;
-}
 
 // section record as the release loop reads it: (agent | scope id << 16, acquire epoch,
 // release index, release epoch)
@@ -808,7 +797,7 @@ __global__ void k_plan_sync(PropArgs a, const uint32_t* sy_kind_, const uint32_t
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_sync) return;
   const Geo& g = a.g;
-  const uint32_t u = agent_of_sync(a.sy_start, g.W, k);
+  const uint32_t u = a.sy_agent[k];
   const uint32_t row = a.rowbase[u] + sy_ver[k];
   const uint32_t kind = sy_kind_[k];
   uint4 ea, eb = make_uint4(0, 0, 0, 0);
@@ -845,7 +834,7 @@ __global__ void k_plan_incs(PropArgs a, const uint32_t* incs_k, const uint32_t* 
   const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_incs) return;
   const uint32_t k = incs_k[r];
-  const uint32_t u = agent_of_sync(a.sy_start, a.g.W, k);
+  const uint32_t u = a.sy_agent[k];
   const size_t p = size_t(k) + 1 + r;
   const uint32_t off = flat_off[r], cnt = flat_off[r + 1] - off;
   a.plan[2 * p] = make_uint4(P_INCS, a.rowbase[u] + incs_ver[r], off, cnt);
@@ -934,6 +923,7 @@ int phaseG_propagate(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s
   a.sy_N = b.sy_N;
   a.sy_ver = b.sy_ver;
   a.sy_aux = b.sy_aux;
+  a.sy_agent = b.sy_agent;
   a.incs_off = b.incs_cnt;
   a.incs_ver = b.incs_ver;
   a.incs_k = b.incs_k;
