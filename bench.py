@@ -175,22 +175,30 @@ def digest_check(ev, races, workload, seed):
 
 
 def prop_roofline(kernel, workload, ms, cnt, W, tiles, peak, peak_kind):
-    """Roofline of the clock propagation with the algorithmic bytes of the method: a
-    vector-clock join of width W reads two clocks and writes one (12 W bytes), each
-    release-loop record visit compares one epoch (8 bytes); with tiled clocks also the
-    bytes of the 1 KB tiles the walkers actually read and wrote."""
+    """Roofline of the clock propagation with the method's algorithmic bytes:
+    a vector-clock join of width W reads two clocks and writes one (12 W bytes), each
+    release-loop record visit compares one epoch (8 bytes). With clocks held as 256-entry
+    tiles the walkers join only the tiles that differ, so the bytes they must move are the
+    1 KB tiles read and written plus the epoch compares; that tile-sparse figure is the
+    roofline's `achieved` and `frac`, and the dense figure (which can exceed the peak, since
+    shared and unchanged tiles are never moved) is reported beside it."""
     joins, visits = cnt["joins"], cnt["loop_visits"]
     dense = 12.0 * W * joins + 8.0 * visits
-    ach = dense / (ms / 1e3) / 1e9
-    out = {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-           "peak_kind": f"{peak_kind} hbm_gbs", "traffic": traffic_for(kernel, workload), "algorithmic_bytes": dense,
-           "avg_ms": ms, "bytes_per_unit": "12*W per join (W = %d) + 8 per release-loop visit" % W,
-           "joins": joins, "loop_visits": visits}
+    dense_out = {"algorithmic_bytes": dense, "achieved": dense / (ms / 1e3) / 1e9,
+                 "frac": dense / (ms / 1e3) / 1e9 / peak,
+                 "bytes_per_unit": "12*W per join (W = %d) + 8 per release-loop visit" % W}
     if tiles:
-        tb = 1024.0 * (cnt["tiles_read"] + cnt["tiles_written"]) + 8.0 * visits
-        out["tile_sparse"] = {"algorithmic_bytes": tb, "achieved": tb / (ms / 1e3) / 1e9,
-                              "frac": tb / (ms / 1e3) / 1e9 / peak, "tiles_read": cnt["tiles_read"],
-                              "tiles_written": cnt["tiles_written"]}
+        b = 1024.0 * (cnt["tiles_read"] + cnt["tiles_written"]) + 8.0 * visits
+        unit = "1 KB per tile read or written + 8 per release-loop visit"
+    else:
+        b, unit = dense, dense_out["bytes_per_unit"]
+    ach = b / (ms / 1e3) / 1e9
+    out = {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+           "peak_kind": f"{peak_kind} hbm_gbs", "traffic": traffic_for(kernel, workload), "algorithmic_bytes": b,
+           "avg_ms": ms, "bytes_per_unit": unit, "joins": joins, "loop_visits": visits}
+    if tiles:
+        out["tiles_read"], out["tiles_written"] = cnt["tiles_read"], cnt["tiles_written"]
+        out["dense_equivalent"] = dense_out
     return out
 
 

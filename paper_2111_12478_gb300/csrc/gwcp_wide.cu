@@ -59,6 +59,23 @@ __device__ __forceinline__ uint4 max4(uint4 x, uint4 y) {
 }
 __device__ __forceinline__ bool eq4(uint4 x, uint4 y) { return x.x == y.x && x.y == y.y && x.z == y.z && x.w == y.w; }
 
+// Tiles are immutable once written and a tile id becomes known to a walker only through a
+// table published after the tile (or through its own CTA after a barrier), so no L1 line
+// can hold a tile's address before the tile is written (L1 starts clean each launch):
+// tile reads may go through L1, and a merge first prefetches every tile it will read.
+__device__ __forceinline__ void prefetch_tile(const WideArgs& a, uint32_t id) {
+  const char* p = reinterpret_cast<const char*>(a.tiles + size_t(id) * kTileW);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) asm volatile("prefetch.global.L1 [%0];" ::"l"(p + q * 128));
+}
+// the tiles a merge of `src` into the table `my` will read (lane T: tile T of each)
+__device__ __forceinline__ void prefetch_merge(const WideArgs& a, uint32_t my, uint32_t src) {
+  if ((threadIdx.x & 31) < int(a.g.nT) && src != 0 && src != my && my != 0) {
+    prefetch_tile(a, my);
+    prefetch_tile(a, src);
+  }
+}
+
 __device__ __forceinline__ const uint4* tile_src(const WideArgs& a, uint32_t id) {
   return reinterpret_cast<const uint4*>(a.tiles + size_t(id) * kTileW) + (threadIdx.x & 31) * 2;
 }
@@ -134,6 +151,10 @@ __device__ __noinline__ void merge_table(const WideArgs& a, uint32_t& my, uint32
     my = src;
     need = false;
   }
+  if (need) {
+    prefetch_tile(a, my);
+    prefetch_tile(a, src);
+  }
   uint32_t m = __ballot_sync(0xffffffffu, need);
   while (m) {
     const int T = __ffs(m) - 1;
@@ -141,7 +162,7 @@ __device__ __noinline__ void merge_table(const WideArgs& a, uint32_t& my, uint32
     const uint32_t ia = __shfl_sync(0xffffffffu, my, T), ib = __shfl_sync(0xffffffffu, src, T);
     const uint4* pa = tile_src(a, ia);
     const uint4* pb = tile_src(a, ib);
-    const uint4 x0 = __ldcg(pa), x1 = __ldcg(pa + 1), y0 = __ldcg(pb), y1 = __ldcg(pb + 1);
+    const uint4 x0 = __ldca(pa), x1 = __ldca(pa + 1), y0 = __ldca(pb), y1 = __ldca(pb + 1);
     const uint4 r0 = max4(x0, y0), r1 = max4(x1, y1);
     uint32_t nid;
     if (__all_sync(0xffffffffu, eq4(r0, x0) && eq4(r1, x1))) {
@@ -170,7 +191,7 @@ __device__ __noinline__ void merge_table(const WideArgs& a, uint32_t& my, uint32
 __device__ __forceinline__ uint32_t cow_set(const WideArgs& a, uint32_t id, uint32_t e, uint32_t val, bool& dirty, TileAlloc& ta) {
   const int lane = threadIdx.x & 31;
   const uint4* p = tile_src(a, id);
-  uint4 x0 = __ldcg(p), x1 = __ldcg(p + 1);
+  uint4 x0 = __ldca(p), x1 = __ldca(p + 1);
   if (lane == int(e >> 3)) set8(x0, x1, e & 7, val);
   const uint32_t nid = alloc_tile(a, ta);
   ta.count(1, 1);
@@ -247,7 +268,7 @@ __device__ __noinline__ uint32_t join_members(const WideArgs& a, uint32_t idm, u
   for (uint32_t m = leaders; m; m &= m - 1) {
     const uint32_t id = __shfl_sync(0xffffffffu, idm, __ffs(m) - 1);
     const uint4* p = tile_src(a, id);
-    const uint4 x0 = __ldcg(p), x1 = __ldcg(p + 1);
+    const uint4 x0 = __ldca(p), x1 = __ldca(p + 1);
     const bool le = __all_sync(0xffffffffu, eq4(max4(r0, x0), r0) && eq4(max4(r1, x1), r1));  // x <= r
     const bool ge = __all_sync(0xffffffffu, eq4(max4(r0, x0), x0) && eq4(max4(r1, x1), x1));  // x >= r
     r0 = max4(r0, x0);
@@ -332,9 +353,18 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
         else
           x = __ldcg(list + off + q);
         if (t == P_ACQ) {
-          const uint32_t sp = read_table(a, a.psnap + size_t(x) * kTabW, abort);
-          const uint32_t sh = read_table(a, a.hsnap + size_t(x) * kTabW, abort);
-          const uint32_t sj = read_table(a, a.jsnap + size_t(x) * kTabW, abort);
+          // the three published tables are loaded together (a table still being written is
+          // then waited for), and every tile the three merges read is prefetched first
+          uint32_t sp = lane < int(g.nT) ? __ldcg(a.psnap + size_t(x) * kTabW + lane) : 0;
+          uint32_t sh = lane < int(g.nT) ? __ldcg(a.hsnap + size_t(x) * kTabW + lane) : 0;
+          uint32_t sj = lane < int(g.nT) ? __ldcg(a.jsnap + size_t(x) * kTabW + lane) : 0;
+          if (!__all_sync(0xffffffffu, sp != SENT && sh != SENT && sj != SENT)) {
+            sp = read_table(a, a.psnap + size_t(x) * kTabW, abort);
+            sh = read_table(a, a.hsnap + size_t(x) * kTabW, abort);
+            sj = read_table(a, a.jsnap + size_t(x) * kTabW, abort);
+          }
+          prefetch_merge(a, hid, sh);
+          prefetch_merge(a, jid, sj);
           merge_table(a, pid, sp, dirty, ta);
           merge_table(a, hid, sh, dirty, ta);
           merge_table(a, jid, sj, dirty, ta);
@@ -344,6 +374,7 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
           const uint4 mx = __ldg(a.recmeta + x);
           if (entry_of(a, jid, mx.x & 0xFFFF) < mx.w) {
             const uint32_t sx = read_table(a, a.hsnap + size_t(x) * kTabW, abort);
+            prefetch_merge(a, jid, sx);
             merge_table(a, pid, sx, dirty, ta);
             merge_table(a, jid, sx, dirty, ta);
             joins += 1;
@@ -382,6 +413,7 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
           for (uint32_t wm = wave; wm; wm &= wm - 1) {
             const uint32_t r = lo + cur + (__ffs(wm) - 1);
             const uint32_t sx = read_table(a, a.hsnap + size_t(r) * kTabW, abort);
+            prefetch_merge(a, jid, sx);
             merge_table(a, pid, sx, dirty, ta);
             merge_table(a, jid, sx, dirty, ta);
             ++joins;
@@ -428,6 +460,9 @@ __global__ void __launch_bounds__(1024, MINB) k_prop_wide(WideArgs a) {
           const uint32_t cm = mem ? tabs[(lane * 3) * 32 + T] : 0, hm = mem ? tabs[(lane * 3 + 1) * 32 + T] : 0;
           const uint32_t jm = mem ? tabs[(lane * 3 + 2) * 32 + T] : 0;
           const uint32_t nm = mem ? nbuf[lane] : 0;
+          if (cm) prefetch_tile(a, cm);
+          if (hm) prefetch_tile(a, hm);
+          if (jm) prefetch_tile(a, jm);
           const uint32_t jc = join_members(a, cm, nm, apb, first, T, true, wrote, ta);
           const uint32_t jh = join_members(a, hm, nm, apb, first, T, true, wrote, ta);
           const uint32_t jj = join_members(a, jm, nm, apb, first, T, false, wrote, ta);
