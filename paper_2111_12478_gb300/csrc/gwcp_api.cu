@@ -410,7 +410,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   if (z.sparse_check) {
     const size_t na = size_t(z.n_acc) + 1;
     b.wc_flag = get<uint32_t>(c, "wc_flag", na, &oom);
-    b.wc_run = get<uint32_t>(c, "wc_run", na, &oom);
+    b.wc_run = get<uint32_t>(c, "wc_run", na + 1, &oom);  // [n] runs, [n + 1] accesses kept by the regrouping
     b.wc_key = get<uint64_t>(c, "wc_key", na, &oom);
     b.wc_val = get<uint32_t>(c, "wc_val", na, &oom);
     b.wc_key2 = get<uint64_t>(c, "wc_key2", na, &oom);

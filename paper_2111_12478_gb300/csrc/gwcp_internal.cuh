@@ -208,10 +208,11 @@ void scan_exclusive(const uint32_t* in, uint32_t* out, size_t n, uint32_t* total
                     cudaStream_t s);
 // Stable LSD radix sort of (key, val) pairs on the bits set in `mask`, 8-bit digits.
 // Ping-pongs between (k0, v0) and (k1, v1); returns true if the result is in (k1, v1).
-// tmp must hold radix_tmp_need(n) u32.
+// tmp must hold radix_tmp_need(n) u32. With n_dev, only the first min(n, *n_dev) pairs are
+// sorted (a count known on the device only; n bounds it).
 size_t radix_tmp_need(size_t n);
 bool radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, size_t n, uint64_t mask,
-                      uint32_t* tmp, cudaStream_t s);
+                      uint32_t* tmp, cudaStream_t s, const uint32_t* n_dev = nullptr);
 // Digit windows covering the bits of `mask` (low bit of each window).
 std::vector<int> radix_windows(uint64_t mask);
 

@@ -77,9 +77,11 @@ __global__ void k_scan_apply(const uint32_t* in, uint32_t* out, size_t n, const 
 
 constexpr int RS_THREADS = 256, RS_ITEMS = 8, RS_TILE = RS_THREADS * RS_ITEMS;
 
-__global__ void k_radix_hist(const uint64_t* keys, size_t n, int shift, uint32_t* hist, uint32_t ntiles) {
+__global__ void k_radix_hist(const uint64_t* keys, size_t n, const uint32_t* n_dev, int shift, uint32_t* hist,
+                             uint32_t ntiles) {
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
+  if (n_dev && *n_dev < n) n = *n_dev;  // the count may be known on the device only
   __syncthreads();
   const size_t base = size_t(blockIdx.x) * RS_TILE;
 #pragma unroll
@@ -97,8 +99,10 @@ __global__ void k_radix_hist(const uint64_t* keys, size_t n, int shift, uint32_t
 // write consecutive positions of one digit's run (coalesced stores instead of one sector
 // per item).
 __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint64_t* kin, const uint32_t* vin,
-                                                              uint64_t* kout, uint32_t* vout, size_t n, int shift,
+                                                              uint64_t* kout, uint32_t* vout, size_t n,
+                                                              const uint32_t* n_dev, int shift,
                                                               const uint32_t* offs, uint32_t ntiles) {
+  if (n_dev && *n_dev < n) n = *n_dev;
   __shared__ uint32_t cnt[RS_THREADS / 32][256];
   __shared__ uint32_t tile_off[256];  // first position of each digit in the tile's digit order
   __shared__ uint32_t glob[256];      // global position of the tile's first item of each digit
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint64_t* ki
     }
   }
   __syncthreads();
-  const uint32_t nvalid = n - tile_base < size_t(RS_TILE) ? uint32_t(n - tile_base) : uint32_t(RS_TILE);
+  const uint32_t nvalid = tile_base >= n ? 0u : n - tile_base < size_t(RS_TILE) ? uint32_t(n - tile_base) : uint32_t(RS_TILE);
   for (uint32_t i = threadIdx.x; i < nvalid; i += RS_THREADS) {
     const uint64_t key = sk[i];
     const uint32_t d = uint32_t((key >> shift) & 255u);
@@ -202,7 +206,7 @@ size_t radix_tmp_need(size_t n) {
 }
 
 bool radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, size_t n, uint64_t mask,
-                      uint32_t* tmp, cudaStream_t s) {
+                      uint32_t* tmp, cudaStream_t s, const uint32_t* n_dev) {
   if (n <= 1) return false;
   const uint32_t ntiles = uint32_t((n + RS_TILE - 1) / RS_TILE);
   uint32_t* hist = tmp;
@@ -213,10 +217,10 @@ bool radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, si
     uint32_t* vin = in_second ? v1 : v0;
     uint64_t* kout = in_second ? k0 : k1;
     uint32_t* vout = in_second ? v0 : v1;
-    k_radix_hist<<<ntiles, RS_THREADS, 0, s>>>(kin, n, lo, hist, ntiles);
+    k_radix_hist<<<ntiles, RS_THREADS, 0, s>>>(kin, n, n_dev, lo, hist, ntiles);
     count_launch();
     scan_exclusive(hist, hist, size_t(256) * ntiles, nullptr, stmp, s);
-    k_radix_scatter<<<ntiles, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, lo, hist, ntiles);
+    k_radix_scatter<<<ntiles, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, n_dev, lo, hist, ntiles);
     count_launch();
     in_second = !in_second;
   }

@@ -519,10 +519,30 @@ __global__ void k_wc_compose(const uint32_t* run_excl, const uint32_t* flag, con
   s_ep[p] = in.epoch;
 }
 
-// group starts over the sorted composite keys, and per (run, class) group counts
-__global__ void k_wc_groupflags(const uint64_t* ck, uint32_t n, uint32_t* gflag) {
+// A location that no write-class access touches has no races (two reads never conflict):
+// its accesses are left out of the regrouping, so the check finds no partner groups there.
+__global__ void k_wc_runwrite(const uint64_t* ck, uint32_t n, uint32_t* run_w) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n && ((ck[p] >> 13) & 3u) != C_READ) run_w[ck[p] >> 15] = 1u;
+}
+__global__ void k_wc_keep(const uint64_t* ck, uint32_t n, const uint32_t* run_w, uint32_t* keep) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) keep[p] = run_w[ck[p] >> 15];
+}
+__global__ void k_wc_compact(const uint64_t* ck, const uint32_t* cv, const uint32_t* keep, const uint32_t* kpos,
+                             uint32_t n, uint64_t* ck2, uint32_t* cv2) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n && keep[p]) {
+    ck2[kpos[p]] = ck[p];
+    cv2[kpos[p]] = cv[p];
+  }
+}
+
+// group starts over the sorted composite keys (the first *n_dev of n), and per (run, class)
+// group counts
+__global__ void k_wc_groupflags(const uint64_t* ck, uint32_t n, const uint32_t* n_dev, uint32_t* gflag) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) gflag[i] = (i == 0 || ck[i] != ck[i - 1]) ? 1u : 0u;
+  if (i < n) gflag[i] = (i < *n_dev && (i == 0 || ck[i] != ck[i - 1])) ? 1u : 0u;
 }
 
 __global__ void k_wc_groups(const uint64_t* ck, const uint32_t* gflag, const uint32_t* gexcl, uint32_t n,
@@ -694,7 +714,9 @@ __global__ void __launch_bounds__(kCheckThreads, 8) k_wc_check(WideCheckArgs a) 
   }
 }
 
-__global__ void k_wc_grp_end(const uint32_t* n_groups, uint32_t n, uint32_t* grp_lo) { grp_lo[*n_groups] = n; }
+__global__ void k_wc_grp_end(const uint32_t* n_groups, const uint32_t* n_dev, uint32_t* grp_lo) {
+  grp_lo[*n_groups] = *n_dev;
+}
 
 inline uint32_t nblk(uint64_t n, uint32_t t) { return uint32_t((n + t - 1) / t); }
 
@@ -760,24 +782,42 @@ void phaseI_wide_group(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStrea
   k_wc_compose<<<nblk(n, 256), 256, 0, s>>>(b.wc_run, b.wc_flag, b.acc_idx, b.acc_info, n, b.wc_key, b.wc_val,
                                             b.wc_who, b.wc_row, b.wc_ep);
   count_launch();
+  // accesses of locations with a write-class access, compacted (count on the device, at
+  // wc_gexcl[n]); wc_grp_lo, wc_gflag and wc_gexcl serve as scratch until the groups are built
+  uint32_t* run_w = b.wc_grp_lo;
+  uint32_t* keep = b.wc_gflag;
+  uint32_t* kpos = b.wc_gexcl;
+  uint32_t* n_keep = b.wc_gexcl + n;
+  cudaMemsetAsync(run_w, 0, (size_t(n) + 1) * 4, s);
+  k_wc_runwrite<<<nblk(n, 256), 256, 0, s>>>(b.wc_key, n, run_w);
+  count_launch();
+  k_wc_keep<<<nblk(n, 256), 256, 0, s>>>(b.wc_key, n, run_w, keep);
+  count_launch();
+  scan_exclusive(keep, kpos, n, n_keep, tmp, s);
+  k_wc_compact<<<nblk(n, 256), 256, 0, s>>>(b.wc_key, b.wc_val, keep, kpos, n, b.wc_key2, b.wc_val2);
+  count_launch();
+  std::swap(b.wc_key, b.wc_key2);
+  std::swap(b.wc_val, b.wc_val2);
+  uint32_t* const n_kept = b.wc_run + n + 1;  // the count, copied out of the scratch
+  cudaMemcpyAsync(n_kept, n_keep, 4, cudaMemcpyDeviceToDevice, s);
   // runs < n <= 2^30: key bits 15 .. 15 + ceil(log2 n); class bits 13-14; agent bits below
   // 13, of which only ceil(log2 W) vary
   uint32_t rb = 1, ab = 0;
   while ((1ull << rb) < n) ++rb;
   while ((1u << ab) < g.W) ++ab;
   const uint64_t mask = (((1ull << rb) - 1) << 15) | (3ull << 13) | ((1ull << ab) - 1);
-  if (radix_sort_pairs(b.wc_key, b.wc_val, b.wc_key2, b.wc_val2, n, mask, tmp, s)) {
+  if (radix_sort_pairs(b.wc_key, b.wc_val, b.wc_key2, b.wc_val2, n, mask, tmp, s, n_kept)) {
     std::swap(b.wc_key, b.wc_key2);
     std::swap(b.wc_val, b.wc_val2);
   }
-  k_wc_groupflags<<<nblk(n, 256), 256, 0, s>>>(b.wc_key, n, b.wc_gflag);
+  k_wc_groupflags<<<nblk(n, 256), 256, 0, s>>>(b.wc_key, n, n_kept, b.wc_gflag);
   count_launch();
   scan_exclusive(b.wc_gflag, b.wc_gexcl, n, b.wc_gexcl + n, tmp, s);
   cudaMemsetAsync(b.wc_rc, 0, (size_t(n) * 4 + 2) * 4, s);
   k_wc_groups<<<nblk(n, 256), 256, 0, s>>>(b.wc_key, b.wc_gflag, b.wc_gexcl, n, b.wc_grp_lo, b.wc_grp_agent,
                                           b.wc_rc);
   count_launch();
-  k_wc_grp_end<<<1, 1, 0, s>>>(b.wc_gexcl + n, n, b.wc_grp_lo);  // grp_lo[n_groups] = n
+  k_wc_grp_end<<<1, 1, 0, s>>>(b.wc_gexcl + n, n_kept, b.wc_grp_lo);  // grp_lo[n_groups] = kept count
   count_launch();
   scan_exclusive(b.wc_rc, b.wc_rc, size_t(n) * 4 + 1, nullptr, tmp, s);
   p.end();
