@@ -363,6 +363,11 @@ typedef struct {
   uint64_t n_races;         /* total races (also when the caller's cap was smaller) */
   uint64_t first_bad_index; /* after GWCP_ERR_INVALID_TRACE */
   double t_submit, t_admit, t_done; /* seconds on the pool's steady clock (gwcp_pool_now) */
+  double t_first_race;      /* when the check found the request's first race, on the same
+                               clock (converted from the GPU's global timer, calibrated
+                               to a few microseconds when the pool is created); 0 if the
+                               request has no race or failed. t_done comes later by the rest
+                               of the check, the race sort and the copy of the races */
 } gwcp_request_info;
 
 typedef struct gwcp_pool gwcp_pool; /* opaque; owns its lanes, threads and device memory */

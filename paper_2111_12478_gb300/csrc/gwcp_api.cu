@@ -64,6 +64,7 @@ struct gwcp_ctx {
   uint64_t n_races = 0;
   unsigned long long bad_index = ~0ull;
   uint64_t counters[GWCP_N_COUNTERS] = {};
+  unsigned long long first_race_ns = 0;  // last compute: %globaltimer of its first race (0: none)
   uint64_t clock_words[3] = {};  // last compute: tiles, pool words taken, words written
   uint64_t tile_cap_hint = 0;  // wide clocks: pool size that the last run needed
   bool compressed = false;     // GWCP_CLOCKS_COMPRESSED was in force at gwcp_load_trace
@@ -201,6 +202,7 @@ int read_status(gwcp_ctx* c, cudaStream_t s, const uint32_t* const* extra, int n
 
 int run(gwcp_ctx* c, cudaStream_t s) {
   use_stream(c, s);
+  c->first_race_ns = 0;
   Bufs& b = c->b;
   Sizes& z = c->z;
   const Geo& g = c->g;
@@ -579,6 +581,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   c->counters[5] = c->st_host->partner_tests;
   c->counters[6] = c->st_host->loop_visits;
   c->counters[7] = c->st_host->joins;
+  c->first_race_ns = c->st_host->first_race_ns;
   c->counters[8] = c->st_host->tiles_read;
   c->counters[9] = c->st_host->tiles_written;
   c->clock_words[0] = c->st_host->spare[2];  // tiles handed out
@@ -597,6 +600,8 @@ size_t ctx_device_bytes(const gwcp_ctx* c) {
   return t;
 }
 void ctx_set_pack_walkers(gwcp_ctx* c, bool pack) { c->opt.pack_walkers = pack ? 1u : 0u; }
+// %globaltimer (ns) at which the last compute's check found its first race; 0 if none
+unsigned long long ctx_first_race_ns(const gwcp_ctx* c) { return c->computed ? c->first_race_ns : 0; }
 // false when the last compute found more races than the device race buffer holds
 bool ctx_races_complete(const gwcp_ctx* c) { return c->n_races <= c->z.race_cap; }
 // releases the cached buffers (the next compute allocates them again); the caller makes

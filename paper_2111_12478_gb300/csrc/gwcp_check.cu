@@ -265,7 +265,10 @@ __global__ void __launch_bounds__(CHK_WARPS * 32) k_check(ChunkArgs a) {
       found += cnt;
       if (cnt) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&a.st->n_races, (unsigned long long)cnt);
+        if (lane == 0) {
+          base = atomicAdd(&a.st->n_races, (unsigned long long)cnt);
+          if (base == 0 && cnt) atomicCAS(&a.st->first_race_ns, 0ull, global_ns());  // the first races found
+        }
         base = __shfl_sync(0xffffffffu, base, 0);
 #pragma unroll
         for (int j = 0; j < K; ++j) {

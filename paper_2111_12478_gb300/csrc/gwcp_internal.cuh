@@ -55,7 +55,15 @@ struct DevStatus {
   unsigned long long joins;
   unsigned long long spare[6];
   unsigned long long tiles_read, tiles_written;  // wide clocks: 1 KB tiles the walkers read / wrote
+  unsigned long long first_race_ns;              // %globaltimer when the check found its first race (0: none)
 };
+
+// %globaltimer (ns); the check stamps its first race with it
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 struct Geo {
   uint32_t W, apb, B, gran, Wp, K;  // Wp = W rounded up to 32 * K, K = Wp / 32 (a power of two)

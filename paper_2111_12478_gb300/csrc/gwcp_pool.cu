@@ -33,6 +33,7 @@ size_t ctx_device_bytes(const gwcp_ctx* c);
 void ctx_trim(gwcp_ctx* c);
 bool ctx_races_complete(const gwcp_ctx* c);
 void ctx_set_pack_walkers(gwcp_ctx* c, bool pack);
+unsigned long long ctx_first_race_ns(const gwcp_ctx* c);
 }  // namespace gwcp
 
 using namespace gwcp;
@@ -86,11 +87,42 @@ struct gwcp_pool {
   double bpe[kClasses];    // estimated device bytes per event, by width class
   uint32_t clock_mode[kClasses];  // clock representation per width class (autotuned)
   bool pack = false;              // tile walkers two CTAs per SM (autotuned)
+  double gt_offset = 0;           // pool clock (s) minus %globaltimer (s), measured at creation
 };
 
 namespace {
 
 double now_s(const gwcp_pool* p) { return std::chrono::duration<double>(Clock::now() - p->t0).count(); }
+
+__global__ void k_read_globaltimer(unsigned long long* out) {
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(*out));
+}
+
+// Offset from the GPU's %globaltimer to the pool's clock: the stamp of a one-thread kernel
+// against the midpoint of the host times around it (best of a few tries; a few µs).
+double globaltimer_offset(gwcp_pool* p) {
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.0;
+  }
+  double best = 1e30, off = 0.0;
+  for (int k = 0; k < 5; ++k) {
+    const double h0 = now_s(p);
+    k_read_globaltimer<<<1, 1>>>(d);
+    count_launch();
+    unsigned long long g = 0;
+    if (cudaMemcpy(&g, d, sizeof(g), cudaMemcpyDeviceToHost) != cudaSuccess) break;
+    const double h1 = now_s(p);
+    if (h1 - h0 < best) {
+      best = h1 - h0;
+      off = 0.5 * (h0 + h1) - double(g) * 1e-9;
+    }
+  }
+  cudaFree(d);
+  cudaGetLastError();
+  return off;
+}
 
 uint64_t estimate(const gwcp_pool* p, const gwcp_trace_desc& t) {
   const double b = p->bpe[width_class(t.geo.num_agents)] * double(t.n) + (t.ev_is_device ? 0.0 : 16.0 * t.n);
@@ -150,6 +182,9 @@ void run_request(gwcp_pool* p, Lane& L, Request& r) {
   }
   r.info.rc = rc;
   r.info.n_races = nr;
+  // the check's stamp of its first race, on the pool's clock
+  const unsigned long long fr = rc == GWCP_OK || rc == GWCP_ERR_CAPACITY ? ctx_first_race_ns(L.ctx) : 0;
+  r.info.t_first_race = fr ? double(fr) * 1e-9 + p->gt_offset : 0.0;
   r.info.first_bad_index = rc == GWCP_ERR_INVALID_TRACE ? gwcp_first_bad_index(L.ctx) : ~0ull;
 }
 
@@ -239,6 +274,7 @@ int gwcp_pool_create(gwcp_pool** out, int device, const gwcp_pool_options* opt) 
   p->device = device;
   p->opt = o;
   p->t0 = Clock::now();
+  p->gt_offset = globaltimer_offset(p);
   p->active = o.lanes;
   p->pack = o.pack_walkers != 0;
   for (int c = 0; c < kClasses; ++c) {

@@ -627,6 +627,8 @@ constexpr uint32_t kCheckThreads = 256;
 
 __device__ __forceinline__ void emit_race(const WideCheckArgs& a, uint64_t v, uint32_t* s_cnt, uint64_t* s_buf) {
   const uint32_t slot = atomicAdd(s_cnt, 1u);
+  if (slot == 0) atomicCAS(&a.st->first_race_ns, 0ull, global_ns());  // the block's first race: the earliest
+                                                                       // stamp wins
   if (slot < kRaceStage) {
     s_buf[slot] = v;
     return;

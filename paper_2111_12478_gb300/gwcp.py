@@ -70,7 +70,7 @@ class PoolOptions(ctypes.Structure):
 class RequestInfo(ctypes.Structure):
     _fields_ = [("rc", ctypes.c_int32), ("lane", ctypes.c_uint32), ("n_races", ctypes.c_uint64),
                 ("first_bad_index", ctypes.c_uint64), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
-                ("t_done", ctypes.c_double)]
+                ("t_done", ctypes.c_double), ("t_first_race", ctypes.c_double)]
 
 
 class Race(ctypes.Structure):
