@@ -216,6 +216,11 @@ uint64_t gwcp_first_bad_index(const gwcp_ctx* ctx);
  * Returns GWCP_ERR_ARGS when i is past the end. */
 int gwcp_profile_get(const gwcp_ctx* ctx, int i, const char** name, float* ms, double* bytes);
 
+/* Start of profile entry i in ms after the start of entry 0 (the kernels of the side
+ * stream overlap those of the main stream: this gives the timeline). GWCP_ERR_ARGS when
+ * i is past the end or start_ms is NULL. */
+int gwcp_profile_start(const gwcp_ctx* ctx, int i, float* start_ms);
+
 /* Storage of the clock versions of the last compute (the rows the check reads, one per
  * agent and clock-changing step), in bytes: [0] as dense rows of W words (W rounded up to
  * 32 * 2^k), [1] as stored (compressed: headers and written pool words; tiles: tables and

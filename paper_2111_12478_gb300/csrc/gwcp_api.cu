@@ -65,13 +65,18 @@ struct gwcp_ctx {
   unsigned long long bad_index = ~0ull;
   uint64_t counters[GWCP_N_COUNTERS] = {};
   unsigned long long first_race_ns = 0;  // last compute: %globaltimer of its first race (0: none)
+  uint64_t key_mask = 0;                 // last compute: location-key bits that vary
   uint64_t clock_words[3] = {};  // last compute: tiles, pool words taken, words written
   uint64_t tile_cap_hint = 0;  // wide clocks: pool size that the last run needed
   bool compressed = false;     // GWCP_CLOCKS_COMPRESSED was in force at gwcp_load_trace
   uint64_t cv_cap_hint = 0;    // compressed versions: pool words that the last run needed
   uint64_t alloc_limit = 0;    // gwcp_debug_alloc_limit: cap on the cached buffers' bytes (0 = none)
-  cudaStream_t side = nullptr;  // runs the access grouping beside the propagation
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t side = nullptr;  // runs the access grouping beside the propagation (lowest priority)
+  cudaStream_t hi = nullptr;    // runs the main phases (highest priority: the block scheduler
+                                // serves its short, latency-bound kernels before the side
+                                // stream's sort)
+  cudaEvent_t in_ev = nullptr, out_ev = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr;
   cudaEvent_t sync_ev = nullptr;  // options.blocking_sync: host waits sleep on this event
   cudaStream_t alloc_s = nullptr;  // stream that buffer (re)allocations are ordered on
   void* stage_host = nullptr;       // pinned staging for race copies into pageable memory
@@ -81,6 +86,7 @@ struct gwcp_ctx {
   uint32_t check_mode = GWCP_CHECK_AUTO;   // gwcp_set_check_mode
   uint32_t n_chunks_timeline = 0; // chunks of the last check's timeline
   std::vector<float> prof_ms;
+  std::vector<float> prof_start;  // ms from the first kernel's start
   std::vector<double> prof_bytes;
   std::vector<const char*> prof_names;
 };
@@ -200,6 +206,21 @@ int read_status(gwcp_ctx* c, cudaStream_t s, const uint32_t* const* extra, int n
   return cuda_rc();
 }
 
+// Once work is on the side stream, every exit from run() makes s wait for it, so that the
+// next use of the context's buffers on s is ordered after it.
+struct SideJoin {
+  gwcp_ctx* c;
+  cudaStream_t s;
+  bool armed = false;
+  void join() {
+    if (!armed) return;
+    cudaEventRecord(c->join, c->side);
+    cudaStreamWaitEvent(s, c->join, 0);
+    armed = false;
+  }
+  ~SideJoin() { join(); }
+};
+
 int run(gwcp_ctx* c, cudaStream_t s) {
   use_stream(c, s);
   c->first_race_ns = 0;
@@ -252,6 +273,26 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   z.n_bar = c->cnt_host[3];
   z.n_sync = z.nS - z.n_acc;
   const uint64_t key_mask = c->st_host->key_or ^ c->st_host->key_and;
+  c->key_mask = key_mask;
+  // grouped access order for the partner check (no ranker): the composite key (location,
+  // class, agent) must fit 64 bits, i.e. the location's varying address bits at most 48
+  uint64_t sort_mask = key_mask;
+  if (z.sparse_check && c->rank_theta.empty()) {
+    const uint64_t m = key_mask & ~(1ull << 63);
+    const uint32_t lo = m ? uint32_t(__builtin_ctzll(m)) : 0u, hi = m ? uint32_t(63 - __builtin_clzll(m)) : 0u;
+    const uint32_t span = m ? hi - lo + 1 : 1u;
+    if (span + 1 + 15 <= 64) {
+      z.grouped = true;
+      z.comp_lo = lo;
+      z.comp_span = span;
+      uint32_t ab = 0;
+      while ((1u << ab) < g.W) ++ab;
+      sort_mask = (((m >> lo) | ((key_mask >> 63) << span)) << 15) | (3ull << 13) | ((1ull << ab) - 1);
+      // written-location bitmap of about four bits per access
+      z.wl_log2 = 16;
+      while (z.wl_log2 < 31 && (1ull << z.wl_log2) < 4ull * z.n_acc) ++z.wl_log2;
+    }
+  }
   const uint64_t lock_mask = c->st_host->lock_or ^ c->st_host->lock_and;
 
   b.S = get<uint32_t>(c, "S", z.nS, &oom);
@@ -312,9 +353,26 @@ int run(gwcp_ctx* c, cudaStream_t s) {
     b.fb_rec = get<uint4>(c, "fb_rec", ns1, &oom);
     b.fb_boff = get<uint32_t>(c, "fb_boff", ns1, &oom);
   }
+  // scratch of the side stream's sorts and scans
+  uint32_t* side_tmp = get<uint32_t>(
+      c, "side_tmp", std::max(radix_tmp_need(size_t(z.n_acc) + 1), scan_tmp_need(size_t(z.n_acc) * 4 + 2)) + 64, &oom);
+  uint32_t* fl_cnt = nullptr;
+  if (z.wl_log2) {
+    b.wl_bits = get<uint32_t>(c, "wl_bits", (size_t(1) << z.wl_log2) / 32, &oom);
+    b.n_kept = get<uint32_t>(c, "n_kept", 1, &oom);
+    fl_cnt = get<uint32_t>(c, "fl_cnt", size_t(filter_blocks(z.n_acc)) + 2, &oom);
+  }
   if (oom) return GWCP_ERR_OOM;
 
   phaseA_scatter(b, g, z, s, c->prof);
+  // the access sort needs only the decoded accesses: it runs on the side stream beside the
+  // main stream's other phases and the propagation
+  SideJoin side{c, s};
+  cudaEventRecord(c->fork, s);
+  cudaStreamWaitEvent(c->side, c->fork, 0);
+  side.armed = true;
+  if (z.wl_log2) phaseH_filter(b, z, fl_cnt, side_tmp, c->side, c->prof);
+  phaseH_sort(b, g, z, sort_mask, side_tmp, c->side, c->prof);
   phaseB_sync(b, g, z, s, c->prof);
   cudaMemsetAsync(b.vcount, 0, size_t(g.W + 1) * 4, s);
   cudaMemsetAsync(b.cs_of_sync, 0xFF, ns1 * 4, s);
@@ -413,10 +471,12 @@ int run(gwcp_ctx* c, cudaStream_t s) {
     const size_t na = size_t(z.n_acc) + 1;
     b.wc_flag = get<uint32_t>(c, "wc_flag", na, &oom);
     b.wc_run = get<uint32_t>(c, "wc_run", na + 1, &oom);  // [n] runs, [n + 1] accesses kept by the regrouping
-    b.wc_key = get<uint64_t>(c, "wc_key", na, &oom);
-    b.wc_val = get<uint32_t>(c, "wc_val", na, &oom);
-    b.wc_key2 = get<uint64_t>(c, "wc_key2", na, &oom);
-    b.wc_val2 = get<uint32_t>(c, "wc_val2", na, &oom);
+    if (!z.grouped) {  // the regrouping sort of the location order
+      b.wc_key = get<uint64_t>(c, "wc_key", na, &oom);
+      b.wc_val = get<uint32_t>(c, "wc_val", na, &oom);
+      b.wc_key2 = get<uint64_t>(c, "wc_key2", na, &oom);
+      b.wc_val2 = get<uint32_t>(c, "wc_val2", na, &oom);
+    }
     b.wc_gflag = get<uint32_t>(c, "wc_gflag", na, &oom);
     b.wc_gexcl = get<uint32_t>(c, "wc_gexcl", na, &oom);
     b.wc_grp_lo = get<uint32_t>(c, "wc_grp_lo", na, &oom);
@@ -446,10 +506,9 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   }
 
   phaseD_gaps(b, g, z, s, c->prof);
-  // the access grouping and the check's carries do not depend on clock values: they run
-  // on a side stream, with their own scratch, while the propagation runs on s
-  uint32_t* side_tmp = get<uint32_t>(
-      c, "side_tmp", std::max(radix_tmp_need(size_t(z.n_acc) + 1), scan_tmp_need(size_t(z.n_acc) * 4 + 2)) + 64, &oom);
+  // the access grouping and the check's carries need the access records (phase D), not
+  // clock values: they follow the sort on the side stream while the propagation runs on s
+  cudaEventRecord(c->fork2, s);
   const bool ranked = !c->rank_theta.empty() && z.n_acc;
   RankIn rin{};
   uint32_t *rk_tmp = nullptr, *rk_nloc = nullptr, *rk_val = nullptr, *rk_val2 = nullptr;
@@ -482,12 +541,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   phaseF_walk(b, g, z, key_mask, s, c->prof);
   z.n_groups = z.n_exp;  // upper bound; the kernel reads the exact count on the device
   phaseF_deps(b, g, z, s, c->prof);
-  // the access grouping (and the ranker) need only the decoded accesses: they run on the
-  // side stream while the propagation occupies its few SMs, after the main stream's other
-  // phases so that they do not compete with them
-  cudaEventRecord(c->fork, s);
-  cudaStreamWaitEvent(c->side, c->fork, 0);
-  phaseH_sort(b, g, z, key_mask, side_tmp, c->side, c->prof);
+  cudaStreamWaitEvent(c->side, c->fork2, 0);
   if (ranked) {
     // the ranker's order of the check: location runs by descending score
     c->prof.begin("h_rank", double(z.n_acc) * (12 + 16 + 12 * 2 * 6 + 12), c->side);
@@ -510,12 +564,12 @@ int run(gwcp_ctx* c, cudaStream_t s) {
     c->prof.end();
   }
   if (z.sparse_check)
-    phaseI_wide_group(b, g, z, side_tmp, c->side, c->prof);
+    z.grouped ? phaseI_grouped(b, g, z, side_tmp, c->side, c->prof)
+              : phaseI_wide_group(b, g, z, side_tmp, c->side, c->prof);
   else
     phaseI_carry(b, g, z, c->side, c->prof);
-  cudaEventRecord(c->join, c->side);
   int prc = phaseG_propagate(b, g, z, s, c->prof);
-  cudaStreamWaitEvent(s, c->join, 0);
+  side.join();
   if (prc) return prc;
   if (b.chunk_ns) stamp_now(&b.st->spare[5], s);  // the check's start, for the timeline
   if (z.sparse_check)
@@ -646,11 +700,17 @@ int gwcp_create(gwcp_ctx** out, int device, const gwcp_options* opt) {
   auto* c = new gwcp_ctx();
   c->device = device;
   if (opt) c->opt = *opt;
+  int prio_least = 0, prio_greatest = 0;
   if (cudaMallocHost(&c->st_host, sizeof(DevStatus)) != cudaSuccess ||
       cudaMallocHost(&c->cnt_host, 16 * sizeof(uint32_t)) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->in_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->out_ev, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork2, cudaEventDisableTiming) != cudaSuccess ||
       (c->opt.blocking_sync &&
        cudaEventCreateWithFlags(&c->sync_ev, cudaEventDisableTiming | cudaEventBlockingSync) != cudaSuccess)) {
     gwcp_destroy(c);
@@ -737,9 +797,16 @@ int gwcp_compute_order(gwcp_ctx* c, void* stream) {
     std::memset(c->clock_words, 0, sizeof(c->clock_words));
     return GWCP_OK;
   }
-  int rc = run(c, static_cast<cudaStream_t>(stream));
-  for (int attempt = 0; rc == kRerun && attempt < 6; ++attempt) rc = run(c, static_cast<cudaStream_t>(stream));
+  // the analysis runs on the context's high-priority stream, after the caller's earlier
+  // work on `stream`, which then waits for it
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+  cudaEventRecord(c->in_ev, user);
+  cudaStreamWaitEvent(c->hi, c->in_ev, 0);
+  int rc = run(c, c->hi);
+  for (int attempt = 0; rc == kRerun && attempt < 6; ++attempt) rc = run(c, c->hi);
   if (rc == kRerun) rc = GWCP_ERR_OOM;
+  cudaEventRecord(c->out_ev, c->hi);
+  cudaStreamWaitEvent(user, c->out_ev, 0);
   c->computed = true;
   c->compute_rc = rc;
   return rc;
@@ -769,6 +836,7 @@ int gwcp_report_races(gwcp_ctx* c, gwcp_race* out, uint64_t cap, uint64_t* n_rac
   }
   // profile of this compute
   c->prof_ms.clear();
+  c->prof_start.clear();
   c->prof_bytes.clear();
   c->prof_names.clear();
   if (c->prof.on) {
@@ -776,6 +844,9 @@ int gwcp_report_races(gwcp_ctx* c, gwcp_race* out, uint64_t cap, uint64_t* n_rac
       float ms = 0;
       cudaEventElapsedTime(&ms, r.a, r.b);
       c->prof_ms.push_back(ms);
+      float at = 0;
+      cudaEventElapsedTime(&at, c->prof.recs[0].a, r.a);
+      c->prof_start.push_back(at);
       c->prof_bytes.push_back(r.bytes);
       c->prof_names.push_back(r.name);
     }
@@ -927,6 +998,23 @@ int gwcp_set_ranker(gwcp_ctx* c, const float* theta) {
   return GWCP_OK;
 }
 
+namespace {
+// location order rebuilt from the trace (the grouped order leaves read-only locations
+// out): the accesses' (location key, trace index) pairs in trace order, then a stable sort
+__global__ void k_lf_flag(const Event* ev, uint64_t N, uint32_t* flag) {
+  const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < N) flag[i] = ev[i].op <= GWCP_ATOMIC ? 1u : 0u;
+}
+__global__ void k_lf_acc(const Event* ev, uint64_t N, uint32_t apb, const uint32_t* flag, const uint32_t* pos,
+                         uint64_t* k, uint32_t* v) {
+  const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < N && flag[i]) {
+    k[pos[i]] = location_key(ev[i], apb);
+    v[pos[i]] = uint32_t(i);
+  }
+}
+}  // namespace
+
 int gwcp_location_features(gwcp_ctx* c, float* feat, uint64_t* keys, uint64_t cap, uint64_t* n_loc, void* stream) {
   if (!c || !n_loc || (cap && (!feat || !keys))) return GWCP_ERR_ARGS;
   if (!c->computed || c->compute_rc) return GWCP_ERR_STATE;
@@ -949,6 +1037,29 @@ int gwcp_location_features(gwcp_ctx* c, float* feat, uint64_t* keys, uint64_t ca
   const Bufs& b = c->b;
   in.key = b.acc_key;
   in.idx = b.acc_idx;
+  if (z.grouped) {  // the check ran on the grouped order: rebuild the location order
+    const size_t n = z.n_acc;
+    uint64_t* k0 = get<uint64_t>(c, "lf_k0", n, &oom);
+    uint64_t* k1 = get<uint64_t>(c, "lf_k1", n, &oom);
+    uint32_t* v0 = get<uint32_t>(c, "lf_v0", n, &oom);
+    uint32_t* v1 = get<uint32_t>(c, "lf_v1", n, &oom);
+    uint32_t* flag = get<uint32_t>(c, "lf_flag", z.N, &oom);
+    uint32_t* pos = get<uint32_t>(c, "lf_pos", z.N, &oom);
+    uint32_t* st2 = get<uint32_t>(c, "lf_tmp", std::max(radix_tmp_need(n + 1), scan_tmp_need(z.N)) + 64, &oom);
+    if (oom) return GWCP_ERR_OOM;
+    const uint32_t nbN = uint32_t((z.N + 255) / 256);
+    k_lf_flag<<<nbN, 256, 0, s>>>(b.ev, z.N, flag);
+    count_launch();
+    scan_exclusive(flag, pos, z.N, nullptr, st2, s);
+    k_lf_acc<<<nbN, 256, 0, s>>>(b.ev, z.N, c->g.apb, flag, pos, k0, v0);
+    count_launch();
+    if (radix_sort_pairs(k0, v0, k1, v1, n, c->key_mask, st2, s)) {
+      std::swap(k0, k1);
+      std::swap(v0, v1);
+    }
+    in.key = k0;
+    in.idx = v0;
+  }
   in.info = b.acc_info;
   in.n_acc = z.n_acc;
   in.incs_idx = b.incs_idx;
@@ -1079,6 +1190,12 @@ int gwcp_profile_get(const gwcp_ctx* c, int i, const char** name, float* ms, dou
   return GWCP_OK;
 }
 
+int gwcp_profile_start(const gwcp_ctx* c, int i, float* start_ms) {
+  if (!c || i < 0 || size_t(i) >= c->prof_start.size() || !start_ms) return GWCP_ERR_ARGS;
+  *start_ms = c->prof_start[i];
+  return GWCP_OK;
+}
+
 int gwcp_counters(const gwcp_ctx* c, uint64_t* out8) {
   if (!c || !out8) return GWCP_ERR_ARGS;
   std::memcpy(out8, c->counters, 8 * sizeof(uint64_t));
@@ -1108,8 +1225,13 @@ void gwcp_destroy(gwcp_ctx* c) {
   for (auto e : c->prof.pool) cudaEventDestroy(e);
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->join) cudaEventDestroy(c->join);
+  if (c->fork2) cudaEventDestroy(c->fork2);
   if (c->sync_ev) cudaEventDestroy(c->sync_ev);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->hi) cudaStreamSynchronize(c->hi);
+  if (c->hi) cudaStreamDestroy(c->hi);
+  if (c->in_ev) cudaEventDestroy(c->in_ev);
+  if (c->out_ev) cudaEventDestroy(c->out_ev);
   delete c;
 }
 

@@ -197,6 +197,10 @@ struct Bufs {
   uint32_t* wc_who = nullptr;    // [n_acc] record fields in key order: who, version row, epoch
   uint32_t* wc_row = nullptr;
   uint32_t* wc_ep = nullptr;
+  // grouped order: hashed bitmap of the locations with a write-class access, and the
+  // number of accesses the filter keeps (those whose location's bit is set)
+  uint32_t* wl_bits = nullptr;  // [2^wl_log2 / 32]
+  uint32_t* n_kept = nullptr;   // [1]
   unsigned long long* chunk_ns = nullptr;  // [n_chunks] check timeline (options.timeline)
   uint32_t* chunk_races = nullptr;         // [n_chunks]
   uint64_t* races = nullptr;    // [race_cap] (later << 32) | earlier
@@ -359,7 +363,33 @@ struct Sizes {
   bool forced_barrier = false;  // members leave a barrier at their highest local time
   bool compress = false;        // clock versions in the block/warp compressed form
   uint64_t cv_cap = 0;          // words of the compressed-version pool
+  // grouped access order (partner check without a ranker): the access keys are the
+  // composite (location, class, agent), one sort groups each location's accesses by class
+  // and agent in trace order. The location part is the key's varying bits [comp_lo,
+  // comp_lo + comp_span) and the shared-memory flag above them.
+  bool grouped = false;
+  uint32_t comp_lo = 0, comp_span = 0;
+  uint32_t wl_log2 = 0;  // bits of the written-location bitmap (log2); 0 = no filter
 };
+
+// bit of a location (the composite key without its class and agent) in the
+// written-location bitmap of 2^log2 bits: the top bits of MurmurHash3's 64-bit finaliser
+__host__ __device__ inline uint32_t wl_bit(uint64_t loc_part, uint32_t log2) {
+  uint64_t x = loc_part;
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return uint32_t(x >> (64 - log2));
+}
+
+// composite access key of the grouped order (see Sizes::grouped)
+__host__ __device__ inline uint64_t composite_key(uint64_t loc, uint32_t cls, uint32_t agent, uint32_t lo,
+                                                 uint32_t span) {
+  const uint64_t addr = ((loc & ~(1ull << 63)) >> lo) & ((1ull << span) - 1);
+  return ((addr | ((loc >> 63) << span)) << 15) | (uint64_t(cls) << 13) | agent;
+}
 
 // profiling hook: records an event pair around each launch when enabled
 struct Prof {
@@ -437,6 +467,10 @@ void stamp_now(unsigned long long* at, cudaStream_t s);
 // regrouping of accesses (beside the propagation) and the per-access partner check
 int phaseG_wide(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s);
 void phaseI_wide_group(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t s, Prof& p);
+void phaseI_grouped(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t s, Prof& p);
+// written-location filter of the grouped order (before its sort); cnt: filter_blocks + 1 words
+void phaseH_filter(Bufs& b, const Sizes& z, uint32_t* cnt, uint32_t* tmp, cudaStream_t s, Prof& p);
+uint32_t filter_blocks(uint32_t n_acc);
 void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 uint32_t sparse_check_blocks(uint32_t n_acc);  // timeline entries of the partner-group check
 

@@ -46,9 +46,28 @@ __device__ __forceinline__ uint32_t entry_kind(uint8_t op) {
   return op <= GWCP_ATOMIC ? K_ACCESS : op == GWCP_ACQ ? K_ACQ : op == GWCP_REL ? K_REL : K_BAR;
 }
 
+// Phase A walks each tile with one warp, 32 events a round; with many agents few warps fit
+// an SM (each holds a per-agent count table in shared memory), so each lane loads the
+// events of kAhead rounds before it processes them.
+constexpr int kAhead = 8;
+
+// event i; vec: the array is 16-byte aligned (one 128-bit load)
+__device__ __forceinline__ Event load_event(const Event* ev, uint64_t i, bool vec) {
+  if (!vec) return ev[i];
+  const uint4 v = __ldg(reinterpret_cast<const uint4*>(ev) + i);
+  Event e;
+  e.agent = v.x;
+  e.op = uint8_t(v.y);
+  e.scope = uint8_t(v.y >> 8);
+  e.space = uint8_t(v.y >> 16);
+  e.flags = uint8_t(v.y >> 24);
+  e.addr = uint64_t(v.z) | (uint64_t(v.w) << 32);
+  return e;
+}
+
 // Phase A, pass 1: per (agent, tile) entry counts and per-tile compaction counts.
 __global__ void k_a_count(const Event* ev, uint64_t N, Geo g, uint32_t TA, uint32_t ntA, uint32_t* hist,
-                          uint32_t* tile_cnt, DevStatus* st) {
+                          uint32_t* tile_cnt, DevStatus* st, bool vec) {
   extern __shared__ uint32_t sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -59,33 +78,43 @@ __global__ void k_a_count(const Event* ev, uint64_t N, Geo g, uint32_t TA, uint3
   const uint64_t lo = uint64_t(tile) * TA, hi = (lo + TA < N ? lo + TA : N);
   uint32_t n_acc = 0, n_ar = 0, n_bar = 0;
   uint64_t kor = 0, kand = ~0ull, lor = 0, land = ~0ull;
-  for (uint64_t base = lo; base < hi; base += 32) {
-    const uint64_t i = base + lane;
-    const bool valid = i < hi;
-    Event e{};
-    if (valid) e = ev[i];
-    bool ok = !valid || validate_w1(e, g);
-    if (!ok) set_error(st, GWCP_ERR_INVALID_TRACE, i);
-    const bool acc = valid && ok && e.op <= GWCP_ATOMIC;
-    const bool ar = valid && ok && (e.op == GWCP_ACQ || e.op == GWCP_REL);
-    const bool bar = valid && ok && e.op == GWCP_BARRIER;
-    if (acc || ar) atomicAdd(&cnt[e.agent], 1u);
-    if (acc) {
-      uint64_t k = location_key(e, g.apb);
-      kor |= k;
-      kand &= k;
+  for (uint64_t base0 = lo; base0 < hi; base0 += 32 * kAhead) {
+    Event eb[kAhead];
+#pragma unroll
+    for (int r = 0; r < kAhead; ++r) {
+      const uint64_t i = base0 + r * 32 + lane;
+      eb[r] = i < hi ? load_event(ev, i, vec) : Event{};
     }
-    if (ar) {
-      lor |= e.addr;
-      land &= e.addr;
+#pragma unroll
+    for (int r = 0; r < kAhead; ++r) {
+      const uint64_t base = base0 + r * 32;
+      if (base >= hi) break;
+      const uint64_t i = base + lane;
+      const bool valid = i < hi;
+      const Event e = eb[r];
+      bool ok = !valid || validate_w1(e, g);
+      if (!ok) set_error(st, GWCP_ERR_INVALID_TRACE, i);
+      const bool acc = valid && ok && e.op <= GWCP_ATOMIC;
+      const bool ar = valid && ok && (e.op == GWCP_ACQ || e.op == GWCP_REL);
+      const bool bar = valid && ok && e.op == GWCP_BARRIER;
+      if (acc || ar) atomicAdd(&cnt[e.agent], 1u);
+      if (acc) {
+        uint64_t k = location_key(e, g.apb);
+        kor |= k;
+        kand &= k;
+      }
+      if (ar) {
+        lor |= e.addr;
+        land &= e.addr;
+      }
+      if (bar) {
+        BarMembers m = barrier_members(e, g);
+        for (uint32_t j = 0; j < m.count; ++j) atomicAdd(&cnt[member_at(m, j)], 1u);
+      }
+      n_acc += __popc(__ballot_sync(0xffffffffu, acc));
+      n_ar += __popc(__ballot_sync(0xffffffffu, ar));
+      n_bar += __popc(__ballot_sync(0xffffffffu, bar));
     }
-    if (bar) {
-      BarMembers m = barrier_members(e, g);
-      for (uint32_t j = 0; j < m.count; ++j) atomicAdd(&cnt[member_at(m, j)], 1u);
-    }
-    n_acc += __popc(__ballot_sync(0xffffffffu, acc));
-    n_ar += __popc(__ballot_sync(0xffffffffu, ar));
-    n_bar += __popc(__ballot_sync(0xffffffffu, bar));
   }
   __syncwarp();
   for (uint32_t u = lane; u < g.W; u += 32) hist[size_t(u) * ntA + tile] = cnt[u];
@@ -115,7 +144,8 @@ __global__ void k_a_count(const Event* ev, uint64_t N, Geo g, uint32_t TA, uint3
 // compactions. Chunks with a barrier are processed one event at a time.
 __global__ void k_a_scatter(const Event* ev, uint64_t N, Geo g, uint32_t TA, uint32_t ntA, const uint32_t* hist,
                             const uint32_t* tile_off, uint32_t* S, uint64_t* acc_key, uint32_t* acc_idx,
-                            uint32_t* acqrel, uint32_t* bar) {
+                            uint32_t* acqrel, uint32_t* bar, uint32_t comp_lo, uint32_t comp_span,
+                            uint32_t* wl_bits, uint32_t wl_log2, bool vec) {
   extern __shared__ uint32_t sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -126,69 +156,86 @@ __global__ void k_a_scatter(const Event* ev, uint64_t N, Geo g, uint32_t TA, uin
   uint32_t o_acc = tile_off[tile], o_ar = tile_off[ntA + 1 + tile], o_bar = tile_off[2 * (ntA + 1) + tile];
   const uint32_t lt = lanemask_lt();
   const uint64_t lo = uint64_t(tile) * TA, hi = (lo + TA < N ? lo + TA : N);
-  for (uint64_t base = lo; base < hi; base += 32) {
-    const uint64_t i = base + lane;
-    const bool valid = i < hi;
-    Event e{};
-    if (valid) e = ev[i];
-    // events that break W1 are left out, as in the counting pass
-    const bool ok = valid && validate_w1(e, g);
-    const bool acc = ok && e.op <= GWCP_ATOMIC;
-    const bool ar = ok && (e.op == GWCP_ACQ || e.op == GWCP_REL);
-    const bool isbar = ok && e.op == GWCP_BARRIER;
-    const uint32_t kind = entry_kind(e.op);
-    // trace-order compactions
-    uint32_t m = __ballot_sync(0xffffffffu, acc);
-    if (acc) {
-      uint32_t p = o_acc + __popc(m & lt);
-      acc_key[p] = location_key(e, g.apb);
-      acc_idx[p] = uint32_t(i);
+  for (uint64_t base0 = lo; base0 < hi; base0 += 32 * kAhead) {
+    Event eb[kAhead];
+#pragma unroll
+    for (int r = 0; r < kAhead; ++r) {
+      const uint64_t i = base0 + r * 32 + lane;
+      eb[r] = i < hi ? load_event(ev, i, vec) : Event{};
     }
-    o_acc += __popc(m);
-    m = __ballot_sync(0xffffffffu, ar);
-    if (ar) acqrel[o_ar + __popc(m & lt)] = uint32_t(i);
-    o_ar += __popc(m);
-    m = __ballot_sync(0xffffffffu, isbar);
-    if (isbar) bar[o_bar + __popc(m & lt)] = uint32_t(i);
-    o_bar += __popc(m);
-    // agent-sorted stream
-    if (!m) {
-      const bool in_s = acc || ar;
-      const uint32_t key = in_s ? e.agent : 0xFFFFFFFFu;
-      const uint32_t peers = __match_any_sync(0xffffffffu, key);
-      const uint32_t b0 = in_s ? cnt[e.agent] : 0;
-      __syncwarp();
-      if (in_s) {
-        S[b0 + __popc(peers & lt)] = (kind << 30) | uint32_t(i);
-        if (lane == __ffs(peers) - 1) cnt[e.agent] = b0 + __popc(peers);
+#pragma unroll
+    for (int r = 0; r < kAhead; ++r) {
+      const uint64_t base = base0 + r * 32;
+      if (base >= hi) break;
+      const uint64_t i = base + lane;
+      const bool valid = i < hi;
+      const Event e = eb[r];
+      // events that break W1 are left out, as in the counting pass
+      const bool ok = valid && validate_w1(e, g);
+      const bool acc = ok && e.op <= GWCP_ATOMIC;
+      const bool ar = ok && (e.op == GWCP_ACQ || e.op == GWCP_REL);
+      const bool isbar = ok && e.op == GWCP_BARRIER;
+      const uint32_t kind = entry_kind(e.op);
+      // trace-order compactions
+      uint32_t m = __ballot_sync(0xffffffffu, acc);
+      if (acc) {
+        uint32_t p = o_acc + __popc(m & lt);
+        const uint64_t loc = location_key(e, g.apb);
+        const uint32_t cls = access_class(e);
+        const uint64_t key = comp_span ? composite_key(loc, cls, e.agent, comp_lo, comp_span) : loc;
+        acc_key[p] = key;
+        acc_idx[p] = uint32_t(i);
+        if (wl_log2 && cls != C_READ) {  // a write-class access marks its location
+          const uint32_t h = wl_bit(key >> 15, wl_log2);
+          atomicOr(wl_bits + (h >> 5), 1u << (h & 31));
+        }
       }
-      __syncwarp();
-    } else {
-      for (int L = 0; L < 32; ++L) {
-        const uint32_t eop = __shfl_sync(0xffffffffu, uint32_t(e.op), L);
-        const uint32_t eagent = __shfl_sync(0xffffffffu, e.agent, L);
-        const uint32_t escope = __shfl_sync(0xffffffffu, uint32_t(e.scope), L);
-        const uint64_t eaddr = __shfl_sync(0xffffffffu, e.addr, L);
-        const bool ev_valid = __shfl_sync(0xffffffffu, valid, L);
-        const bool ev_ok = __shfl_sync(0xffffffffu, ok, L);
-        if (!ev_valid) break;
-        const uint32_t idx = uint32_t(base) + L;
-        if (!ev_ok) continue;
-        if (eop <= GWCP_REL) {
-          if (lane == 0) S[cnt[eagent]++] = (entry_kind(uint8_t(eop)) << 30) | idx;
-        } else if (eop == GWCP_BARRIER) {
-          Event be{};
-          be.agent = eagent;
-          be.op = GWCP_BARRIER;
-          be.scope = uint8_t(escope);
-          be.addr = eaddr;
-          BarMembers bm = barrier_members(be, g);
-          for (uint32_t j = lane; j < bm.count; j += 32) {
-            uint32_t mb = member_at(bm, j);
-            S[cnt[mb]++] = (K_BAR << 30) | idx;
-          }
+      o_acc += __popc(m);
+      m = __ballot_sync(0xffffffffu, ar);
+      if (ar) acqrel[o_ar + __popc(m & lt)] = uint32_t(i);
+      o_ar += __popc(m);
+      m = __ballot_sync(0xffffffffu, isbar);
+      if (isbar) bar[o_bar + __popc(m & lt)] = uint32_t(i);
+      o_bar += __popc(m);
+      // agent-sorted stream
+      if (!m) {
+        const bool in_s = acc || ar;
+        const uint32_t key = in_s ? e.agent : 0xFFFFFFFFu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, key);
+        const uint32_t b0 = in_s ? cnt[e.agent] : 0;
+        __syncwarp();
+        if (in_s) {
+          S[b0 + __popc(peers & lt)] = (kind << 30) | uint32_t(i);
+          if (lane == __ffs(peers) - 1) cnt[e.agent] = b0 + __popc(peers);
         }
         __syncwarp();
+      } else {
+        for (int L = 0; L < 32; ++L) {
+          const uint32_t eop = __shfl_sync(0xffffffffu, uint32_t(e.op), L);
+          const uint32_t eagent = __shfl_sync(0xffffffffu, e.agent, L);
+          const uint32_t escope = __shfl_sync(0xffffffffu, uint32_t(e.scope), L);
+          const uint64_t eaddr = __shfl_sync(0xffffffffu, e.addr, L);
+          const bool ev_valid = __shfl_sync(0xffffffffu, valid, L);
+          const bool ev_ok = __shfl_sync(0xffffffffu, ok, L);
+          if (!ev_valid) break;
+          const uint32_t idx = uint32_t(base) + L;
+          if (!ev_ok) continue;
+          if (eop <= GWCP_REL) {
+            if (lane == 0) S[cnt[eagent]++] = (entry_kind(uint8_t(eop)) << 30) | idx;
+          } else if (eop == GWCP_BARRIER) {
+            Event be{};
+            be.agent = eagent;
+            be.op = GWCP_BARRIER;
+            be.scope = uint8_t(escope);
+            be.addr = eaddr;
+            BarMembers bm = barrier_members(be, g);
+            for (uint32_t j = lane; j < bm.count; j += 32) {
+              uint32_t mb = member_at(bm, j);
+              S[cnt[mb]++] = (K_BAR << 30) | idx;
+            }
+          }
+          __syncwarp();
+        }
       }
     }
   }
@@ -391,7 +438,38 @@ __global__ void k_c_walk(const Event* ev, Geo g, const uint32_t* seg, const uint
   }
 }
 
-// Phase D: one warp per gap between consecutive synchronisation entries of an agent.
+// Phase D, accesses outside critical sections, in trace order (coalesced reads of the
+// events and writes of the records): the access's gap is the one after its agent's latest
+// synchronisation entry before it (a binary search in the agent's entries, which are in
+// trace order); all accesses of such a gap share the epoch and the clock version.
+__global__ void k_d_trace(const Event* ev, uint64_t N, Geo g, const uint32_t* sy_start, const uint32_t* sy_idx,
+                          const uint32_t* sy_N, const uint32_t* sy_depth, const uint32_t* sy_ver,
+                          const uint32_t* rowbase, AccInfo* acc_info, const DevStatus* st, bool vec) {
+  const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= N || st->code) return;
+  const Event e = load_event(ev, i, vec);
+  if (e.op > GWCP_ATOMIC) return;
+  const uint32_t u = e.agent;
+  uint32_t lo = sy_start[u], hi = sy_start[u + 1];  // first entry at or after i: lo
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (sy_idx[mid] < uint32_t(i))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  uint32_t epoch = 1, ver = 0;
+  if (lo > sy_start[u]) {
+    const uint32_t k = lo - 1;
+    if (sy_depth[k] > 0) return;  // in a critical section: the gap walk below
+    epoch = sy_N[k];
+    ver = sy_ver[k];
+  }
+  acc_info[i] = AccInfo{epoch, rowbase[u] + ver, make_who(u, access_class(e), u / g.apb), 0};
+}
+
+// Phase D, accesses inside critical sections: one warp per gap after a synchronisation
+// entry at nesting depth > 0 (each access there has a clock version of its own).
 __global__ void k_d_fill(const Event* ev, Geo g, uint32_t n_sync, const uint32_t* S, const uint32_t* seg,
                          const uint32_t* sy_start, const uint32_t* sy_agent, const uint32_t* sy_spos,
                          const uint32_t* sy_N,
@@ -400,40 +478,27 @@ __global__ void k_d_fill(const Event* ev, Geo g, uint32_t n_sync, const uint32_t
                          uint32_t* incs_k, uint64_t* incs_key, uint32_t* incs_wr, const DevStatus* st) {
   const int lane = threadIdx.x & 31;
   const uint64_t gid = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  if (gid >= uint64_t(g.W) + n_sync || st->code) return;
-  uint32_t u, lo, hi, epoch, vbase, k = NONE;
-  bool incs = false;
-  if (gid < g.W) {
-    u = uint32_t(gid);
-    lo = seg[u];
-    hi = sy_start[u] < sy_start[u + 1] ? sy_spos[sy_start[u]] : seg[u + 1];
-    epoch = 1;
-    vbase = 0;
-  } else {
-    k = uint32_t(gid - g.W);
-    u = sy_agent[k];
-    lo = sy_spos[k] + 1;
-    hi = (k + 1 < sy_start[u + 1]) ? sy_spos[k + 1] : seg[u + 1];
-    epoch = sy_N[k];
-    vbase = sy_ver[k];
-    incs = sy_depth[k] > 0;
-  }
+  if (gid >= n_sync || st->code) return;
+  const uint32_t k = uint32_t(gid);
+  if (sy_depth[k] == 0) return;
+  const uint32_t u = sy_agent[k];
+  const uint32_t lo = sy_spos[k] + 1;
+  const uint32_t hi = (k + 1 < sy_start[u + 1]) ? sy_spos[k + 1] : seg[u + 1];
+  const uint32_t epoch = sy_N[k], vbase = sy_ver[k];
   const uint32_t rb = rowbase[u];
   for (uint32_t p = lo + lane; p < hi; p += 32) {
     const uint32_t j = p - lo + 1;
     const uint32_t idx = s_idx(S[p]);
     const Event e = ev[idx];
     const uint32_t cls = access_class(e);
-    const uint32_t ver = incs ? vbase + j : vbase;
+    const uint32_t ver = vbase + j;
     acc_info[idx] = AccInfo{epoch, rb + ver, make_who(u, cls, u / g.apb), 0};
-    if (incs) {
-      const uint32_t r = incs_off[k] + j - 1;
-      incs_idx[r] = idx;
-      incs_ver[r] = ver;
-      incs_k[r] = k;
-      incs_key[r] = location_key(e, g.apb);
-      incs_wr[r] = cls != C_READ;
-    }
+    const uint32_t r = incs_off[k] + j - 1;
+    incs_idx[r] = idx;
+    incs_ver[r] = ver;
+    incs_k[r] = k;
+    incs_key[r] = location_key(e, g.apb);
+    incs_wr[r] = cls != C_READ;
   }
 }
 
@@ -645,22 +710,40 @@ struct LockSlot {
 };
 
 // One thread per lock: acquire joins (the latest release on each overlapping scope),
-// W3 (overlapping critical sections never interleave).
+// W3 (overlapping critical sections never interleave). A lock's scopes get slots in order
+// of first use, found through a small open-addressing table. Device scope (0) overlaps
+// every scope; a block scope overlaps itself and device scope. An acquire at block scope
+// joins the latest critical section of its own scope and of device scope; one at device
+// scope joins the latest of device scope and of every scope released since then (the
+// `recent` list, emptied by each device-scope release).
 template <int MAXS>
 __global__ void k_e_walk(const uint32_t* kk, const uint32_t* lock_first, uint32_t n_locks, const uint32_t* csid,
                          const uint32_t* sy_kind, const uint32_t* sy_idx, const uint32_t* cs_of_sync,
                          const uint32_t* cs_sid, uint32_t* acq_dep_off, uint32_t* acq_dep_cnt, uint32_t* pool,
                          uint32_t pool_cap, DevStatus* st) {
+  constexpr int HS = MAXS <= 64 ? 128 : 1024;  // power of two, at least twice MAXS
   uint32_t lr = blockIdx.x * blockDim.x + threadIdx.x;
   const int code = st->code;
   if (lr >= n_locks || (code && code != GWCP_ERR_INVALID_TRACE)) return;
   LockSlot sl[MAXS];
-  int ns = 0;
+  uint16_t hslot[HS];    // slot + 1, 0 = empty
+  uint16_t recent[MAXS];  // slots released since the latest device-scope release
+  bool in_recent[MAXS];
+  for (int h = 0; h < HS; ++h) hslot[h] = 0;
+  int ns = 0, n_recent = 0, q0 = -1;
+  uint32_t open_total = 0;
   auto slot = [&](uint32_t sid) -> int {
-    for (int q = 0; q < ns; ++q)
-      if (sl[q].sid == sid) return q;
+    uint32_t h = (sid * 0x9E3779B1u) >> 16;
+    for (;; ++h) {
+      const uint32_t e = hslot[h & (HS - 1)];
+      if (e == 0) break;
+      if (sl[e - 1].sid == sid) return int(e - 1);
+    }
     if (ns == MAXS) return -1;
     sl[ns] = LockSlot{sid, NONE, NONE, 0};
+    in_recent[ns] = false;
+    hslot[h & (HS - 1)] = uint16_t(ns + 1);
+    if (sid == 0) q0 = ns;
     return ns++;
   };
   for (uint32_t m = lock_first[lr]; m < lock_first[lr + 1]; ++m) {
@@ -674,23 +757,18 @@ __global__ void k_e_walk(const uint32_t* kk, const uint32_t* lock_first, uint32_
       return;
     }
     if (sy_kind[k] == K_ACQ) {
-      int q0 = -1;
-      bool clash = false;
-      for (int r = 0; r < ns; ++r) {
-        if (sl[r].sid == 0) q0 = r;
-        if (sl[r].open && scopes_overlap(sl[r].sid, sid)) clash = true;
-      }
+      const bool clash = sid == 0 ? open_total > 0 : (sl[q].open > 0 || (q0 >= 0 && sl[q0].open > 0));
       if (clash) {
         set_error(st, GWCP_ERR_INVALID_TRACE, idx);
         return;
       }
       uint32_t deps[MAXS];
       uint32_t nd = 0;
-      const uint32_t rel0 = q0 >= 0 ? sl[q0].latest_rel : NONE;
       if (q0 >= 0 && sl[q0].latest_cs != NONE) deps[nd++] = sl[q0].latest_cs;
-      for (int r = 0; r < ns; ++r) {
-        if (r == q0 || sl[r].latest_cs == NONE) continue;
-        if (sid == 0 ? (rel0 == NONE || sl[r].latest_rel > rel0) : sl[r].sid == sid) deps[nd++] = sl[r].latest_cs;
+      if (sid == 0) {
+        for (int r = 0; r < n_recent; ++r) deps[nd++] = sl[recent[r]].latest_cs;
+      } else if (q != q0 && sl[q].latest_cs != NONE) {
+        deps[nd++] = sl[q].latest_cs;
       }
       const uint32_t cid = csid[m];
       uint32_t off = 0;
@@ -705,10 +783,19 @@ __global__ void k_e_walk(const uint32_t* kk, const uint32_t* lock_first, uint32_
       acq_dep_off[cid] = off;
       acq_dep_cnt[cid] = nd;
       sl[q].open++;
+      open_total++;
     } else {
       sl[q].open--;
+      open_total--;
       sl[q].latest_cs = c;
       sl[q].latest_rel = idx;
+      if (q == q0) {
+        for (int r = 0; r < n_recent; ++r) in_recent[recent[r]] = false;
+        n_recent = 0;
+      } else if (!in_recent[q]) {
+        in_recent[q] = true;
+        recent[n_recent++] = uint16_t(q);
+      }
     }
   }
 }
@@ -862,8 +949,9 @@ inline uint32_t a_warps(const Geo& g) {
 void phaseA_count(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   p.begin("a_count", double(z.N) * 16);
   const uint32_t aw = a_warps(g);
+  const bool vec = (reinterpret_cast<uintptr_t>(b.ev) & 15) == 0;
   k_a_count<<<blocks(z.ntA, aw), aw * 32, aw * g.Wp * 4, s>>>(b.ev, z.N, g, z.TA, z.ntA, b.hist_a,
-                                                                          b.tile_cnt, b.st);
+                                                                          b.tile_cnt, b.st, vec);
   count_launch();
   p.end();
   // in-place exclusive scans: agent histogram and the three per-tile counts
@@ -876,9 +964,12 @@ void phaseA_count(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, P
 
 void phaseA_scatter(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   p.begin("a_scatter", double(z.N) * 16 + double(z.nS) * 4 + double(z.n_acc) * 12);
+  if (z.wl_log2) cudaMemsetAsync(b.wl_bits, 0, (size_t(1) << z.wl_log2) / 8, s);
   const uint32_t aw = a_warps(g);
   k_a_scatter<<<blocks(z.ntA, aw), aw * 32, aw * g.Wp * 4, s>>>(
-      b.ev, z.N, g, z.TA, z.ntA, b.hist_a, b.tile_cnt, b.S, b.acc_key, b.acc_idx, b.acqrel, b.bar);
+      b.ev, z.N, g, z.TA, z.ntA, b.hist_a, b.tile_cnt, b.S, b.acc_key, b.acc_idx, b.acqrel, b.bar,
+      z.grouped ? z.comp_lo : 0u, z.grouped ? z.comp_span : 0u, b.wl_bits, z.wl_log2,
+      (reinterpret_cast<uintptr_t>(b.ev) & 15) == 0);
   count_launch();
   k_a_segments<<<blocks(g.W + 1, 256), 256, 0, s>>>(b.hist_a, g.W, z.ntA, z.nS, b.seg);
   count_launch();
@@ -942,12 +1033,15 @@ void phaseC_forced(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, 
 
 void phaseD_gaps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   p.begin("d_gaps", double(z.n_acc) * (4 + 16 + 16), s);
-  const uint64_t gaps = uint64_t(g.W) + z.n_sync;
-  k_d_fill<<<blocks(gaps * 32, 256), 256, 0, s>>>(b.ev, g, z.n_sync, b.S, b.seg, b.sy_start, b.sy_agent, b.sy_spos,
-                                                  b.sy_N,
-                                                  b.sy_depth, b.sy_ver, b.incs_cnt, b.vcount, b.acc_info, b.incs_idx,
-                                                  b.incs_ver, b.incs_k, b.incs_key, b.incs_wr, b.st);
+  k_d_trace<<<blocks(z.N, 256), 256, 0, s>>>(b.ev, z.N, g, b.sy_start, b.sy_idx, b.sy_N, b.sy_depth, b.sy_ver,
+                                              b.vcount, b.acc_info, b.st, (reinterpret_cast<uintptr_t>(b.ev) & 15) == 0);
   count_launch();
+  if (z.n_sync) {
+    k_d_fill<<<blocks(uint64_t(z.n_sync) * 32, 256), 256, 0, s>>>(
+        b.ev, g, z.n_sync, b.S, b.seg, b.sy_start, b.sy_agent, b.sy_spos, b.sy_N, b.sy_depth, b.sy_ver, b.incs_cnt,
+        b.vcount, b.acc_info, b.incs_idx, b.incs_ver, b.incs_k, b.incs_key, b.incs_wr, b.st);
+    count_launch();
+  }
   p.end();
 }
 

@@ -558,10 +558,12 @@ __global__ void k_wc_groups(const uint64_t* ck, const uint32_t* gflag, const uin
 struct WideCheckArgs {
   Geo g;
   uint32_t n;
+  const uint32_t* n_dev;     // the count on the device (at most n), or null
   const uint32_t* idx;       // key order -> trace index
   const uint32_t* flag;      // run starts
   const uint32_t* run_excl;  // exclusive scan of flag
-  const uint32_t* gs;        // grouped order -> key-order position
+  const uint32_t* gs;        // grouped order -> key-order position (grouped: the trace index itself)
+  uint32_t grouped;          // the primary order is the grouped order (compare trace indices)
   const uint32_t* grp_lo;    // [n_groups + 1]
   const uint32_t* grp_agent;
   const uint32_t* rc_off;    // [(run << 2 | class) + 1]
@@ -581,18 +583,19 @@ struct WideCheckArgs {
   uint32_t* chunk_races;         // and the races it found
 };
 
-// latest key-order position < p in group gi, or NONE
-__device__ __forceinline__ uint32_t pred_in_group(const WideCheckArgs& a, uint32_t gi, uint32_t p) {
-  uint32_t lo = a.grp_lo[gi], hi = a.grp_lo[gi + 1];  // positions gs[lo..hi) ascend
-  if (lo == hi || a.gs[lo] >= p) return NONE;
-  while (hi - lo > 1) {  // invariant: gs[lo] < p, and gs[hi] >= p or hi is the end
+// position j in group gi of the latest member with gs[j] < x (gs ascends within a group:
+// key-order positions, or trace indices in the grouped order), or NONE
+__device__ __forceinline__ uint32_t pred_in_group(const WideCheckArgs& a, uint32_t gi, uint32_t x) {
+  uint32_t lo = a.grp_lo[gi], hi = a.grp_lo[gi + 1];
+  if (lo == hi || a.gs[lo] >= x) return NONE;
+  while (hi - lo > 1) {  // invariant: gs[lo] < x, and gs[hi] >= x or hi is the end
     const uint32_t mid = (lo + hi) >> 1;
-    if (a.gs[mid] < p)
+    if (a.gs[mid] < x)
       lo = mid;
     else
       hi = mid;
   }
-  return a.gs[lo];
+  return lo;
 }
 
 // group of agent v among the groups [g0, g1) (sorted by agent), or NONE
@@ -650,6 +653,7 @@ __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cn
   const uint32_t run = a.run_excl[p] + a.flag[p] - 1;
   const uint32_t* rowtab = a.rows + size_t(a.s_row[p]) * a.row_words;
   const uint32_t any_mask = conflict_classes(cb, false) | conflict_classes(cb, true);
+  const uint32_t x = a.grouped ? b : p;  // "earlier than b" in the order gs holds
   uint32_t tests = 0;
   for (uint32_t q = 0; q < 4; ++q) {
     if (!((any_mask >> q) & 1u)) continue;
@@ -659,8 +663,9 @@ __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cn
       if (v == u) continue;
       const uint32_t cm = conflict_classes(cb, v / a.g.apb == bu);
       if (!((cm >> q) & 1u)) continue;
-      const uint32_t pos = pred_in_group(a, gi, p);
-      if (pos == NONE) continue;
+      const uint32_t j = pred_in_group(a, gi, x);
+      if (j == NONE) continue;
+      const uint32_t pos = a.gs[j];
       // tested once per agent: from the class holding its latest conflicting access
       bool latest = true;
       for (uint32_t q2 = 0; q2 < 4 && latest; ++q2) {
@@ -668,13 +673,15 @@ __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cn
         const uint32_t h0 = a.rc_off[(run << 2) | q2], h1 = a.rc_off[((run << 2) | q2) + 1];
         const uint32_t g2 = find_agent(a, h0, h1, v);
         if (g2 == NONE) continue;
-        const uint32_t pos2 = pred_in_group(a, g2, p);
+        const uint32_t j2 = pred_in_group(a, g2, x);
+        const uint32_t pos2 = j2 == NONE ? NONE : a.gs[j2];
         if (pos2 != NONE && (pos2 > pos || (pos2 == pos && q2 < q))) latest = false;
       }
       if (!latest) continue;
       ++tests;
-      const uint32_t ai = a.idx[pos];
-      const uint32_t na = a.s_ep[pos];
+      const uint32_t qa = a.grouped ? j : pos;  // a*'s position in the primary order
+      const uint32_t ai = a.idx[qa];
+      const uint32_t na = a.s_ep[qa];
       uint32_t cv;
       if constexpr (REP == REP_COMPRESSED) {
         cv = cv_entry(rowtab, a.cv_pool, a.cv_cap, v, a.g.apb, cv_group(a.g.gran));
@@ -698,8 +705,9 @@ __global__ void __launch_bounds__(kCheckThreads, 8) k_wc_check(WideCheckArgs a) 
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n_eff = a.n_dev ? min(a.n, *a.n_dev) : a.n;
   uint32_t tests = 0;
-  if (p < a.n) tests = check_one<REP>(a, p, &s_cnt, s_buf);
+  if (p < n_eff) tests = check_one<REP>(a, p, &s_cnt, s_buf);
   tests = __reduce_add_sync(0xffffffffu, tests);
   if ((threadIdx.x & 31) == 0 && tests) atomicAdd(&a.st->partner_tests, (unsigned long long)tests);
   __syncthreads();
@@ -714,6 +722,116 @@ __global__ void __launch_bounds__(kCheckThreads, 8) k_wc_check(WideCheckArgs a) 
     a.chunk_ns[blockIdx.x] = t;
     a.chunk_races[blockIdx.x] = s_cnt;
   }
+}
+
+// ---- grouped order: the accesses sorted once by (location, class, agent, trace index) ----
+// Before the sort, the accesses of locations without a write-class access are left out
+// (two reads never race): a stable compaction of those whose location's bit is set in the
+// hashed bitmap that the decoding pass filled from the write-class accesses. A bit shared
+// with a written location keeps a few read-only locations; they have no partners.
+constexpr uint32_t kFlThreads = 256, kFlItems = 8, kFlTile = kFlThreads * kFlItems;
+
+__device__ __forceinline__ bool wl_kept(uint64_t ck, const uint32_t* bits, uint32_t log2) {
+  const uint32_t h = wl_bit(ck >> 15, log2);
+  return (__ldg(bits + (h >> 5)) >> (h & 31)) & 1u;
+}
+
+__global__ void k_fl_count(const uint64_t* ck, uint32_t n, const uint32_t* bits, uint32_t log2, uint32_t* cnt) {
+  const size_t base = size_t(blockIdx.x) * kFlTile;
+  uint32_t c = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kFlItems; ++j) {
+    const size_t i = base + j * kFlThreads + threadIdx.x;
+    if (i < n && wl_kept(ck[i], bits, log2)) ++c;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  __shared__ uint32_t ws[kFlThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (uint32_t w = 0; w < kFlThreads / 32; ++w) t += ws[w];
+    cnt[blockIdx.x] = t;
+  }
+}
+
+// rounds of kFlThreads consecutive accesses; a block-wide count per round keeps the order
+__global__ void k_fl_scatter(const uint64_t* ck, const uint32_t* idx, uint32_t n, const uint32_t* bits,
+                             uint32_t log2, const uint32_t* off, uint64_t* ck_out, uint32_t* idx_out) {
+  const size_t base = size_t(blockIdx.x) * kFlTile;
+  uint32_t run = off[blockIdx.x];
+  __shared__ uint32_t ws[kFlThreads / 32];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t j = 0; j < kFlItems; ++j) {
+    const size_t i = base + j * kFlThreads + threadIdx.x;
+    const uint64_t k = i < n ? ck[i] : 0;
+    const bool keep = i < n && wl_kept(k, bits, log2);
+    const uint32_t m = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) ws[warp] = __popc(m);
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (uint32_t w = 0; w < kFlThreads / 32; ++w) {
+      if (w < warp) before += ws[w];
+      total += ws[w];
+    }
+    if (keep) {
+      const uint32_t q = run + before + __popc(m & lanemask_lt());
+      ck_out[q] = k;
+      idx_out[q] = idx[i];
+    }
+    run += total;
+    __syncthreads();
+  }
+}
+
+// location runs and (class, agent) groups of the composite keys (the first *n_dev keys)
+__global__ void k_gr_flags(const uint64_t* ck, uint32_t n, const uint32_t* n_dev, uint32_t* run_flag,
+                           uint32_t* grp_flag) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  if (p >= *n_dev) {
+    run_flag[p] = 0;
+    grp_flag[p] = 0;
+    return;
+  }
+  run_flag[p] = (p == 0 || (ck[p] >> 15) != (ck[p - 1] >> 15)) ? 1u : 0u;
+  grp_flag[p] = (p == 0 || ck[p] != ck[p - 1]) ? 1u : 0u;
+}
+
+// The groups ascend by (run, class, agent); rc_off[(run << 2) | q] is the first group whose
+// (run, class) slot is >= (run, q). The first group of a slot writes it and the empty slots
+// before it; the last access writes the slots after the last group (up to 4 * runs).
+__global__ void k_gr_groups(const uint64_t* ck, const uint32_t* run_flag, const uint32_t* run_excl,
+                            const uint32_t* gflag, const uint32_t* gexcl, const uint32_t* n_dev, uint32_t* grp_lo,
+                            uint32_t* grp_agent, uint32_t* rc_off) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = *n_dev;
+  if (i >= n) return;
+  const uint32_t run = run_excl[i] + run_flag[i] - 1;
+  const uint32_t slot = (run << 2) | uint32_t((ck[i] >> 13) & 3u);
+  if (i == n - 1) {
+    const uint32_t n_groups = gexcl[i] + gflag[i];
+    grp_lo[n_groups] = n;
+    for (uint32_t t = slot + 1; t <= (run << 2) + 4; ++t) rc_off[t] = n_groups;
+  }
+  if (!gflag[i]) return;
+  const uint32_t gi = gexcl[i];
+  grp_lo[gi] = i;
+  grp_agent[gi] = uint32_t(ck[i] & 0x1FFF);
+  // slot of the previous group (-1 before the first)
+  const int64_t prev = i == 0 ? -1 : int64_t(((run - run_flag[i]) << 2) | uint32_t((ck[i - 1] >> 13) & 3u));
+  for (int64_t t = prev + 1; t <= int64_t(slot); ++t) rc_off[t] = gi;
+}
+
+// the fields of each access record the check needs, copied into the primary order
+__global__ void k_wc_fields(const uint32_t* idx, const AccInfo* info, const uint32_t* n_dev, uint32_t* s_who,
+                            uint32_t* s_row, uint32_t* s_ep) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= *n_dev) return;
+  const AccInfo in = info[idx[p]];
+  s_who[p] = in.who;
+  s_row[p] = in.row;
+  s_ep[p] = in.epoch;
 }
 
 __global__ void k_wc_grp_end(const uint32_t* n_groups, const uint32_t* n_dev, uint32_t* grp_lo) {
@@ -825,6 +943,49 @@ void phaseI_wide_group(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStrea
   p.end();
 }
 
+// Groups of the grouped order (the accesses already sorted by (location, class, agent),
+// trace order within): location runs, (class, agent) groups, the first group of each
+// (run, class), and the record fields in that order. One sort instead of a location sort
+// followed by a regrouping sort.
+void phaseI_grouped(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t s, Prof& p) {
+  (void)g;
+  const uint32_t n = z.n_acc;
+  if (!n) return;
+  p.begin("i_wide_group", double(n) * (8 + 4 * 4 + 16 + 12 + 16), s);  // ~ per access
+  k_gr_flags<<<nblk(n, 256), 256, 0, s>>>(b.acc_key, n, b.n_kept, b.wc_flag, b.wc_gflag);
+  count_launch();
+  scan_exclusive(b.wc_flag, b.wc_run, n, b.wc_run + n, tmp, s);
+  scan_exclusive(b.wc_gflag, b.wc_gexcl, n, b.wc_gexcl + n, tmp, s);
+  k_gr_groups<<<nblk(n, 256), 256, 0, s>>>(b.acc_key, b.wc_flag, b.wc_run, b.wc_gflag, b.wc_gexcl, b.n_kept,
+                                          b.wc_grp_lo, b.wc_grp_agent, b.wc_rc);
+  count_launch();
+  k_wc_fields<<<nblk(n, 256), 256, 0, s>>>(b.acc_idx, b.acc_info, b.n_kept, b.wc_who, b.wc_row, b.wc_ep);
+  count_launch();
+  p.end();
+}
+
+// The written-location filter of the grouped order: the kept accesses (count at n_kept)
+// into the alternate buffers, which then become the primary ones.
+void phaseH_filter(Bufs& b, const Sizes& z, uint32_t* cnt, uint32_t* tmp, cudaStream_t s, Prof& p) {
+  const uint32_t n = z.n_acc;
+  p.begin("h_filter", double(n) * (8 + 12) + double(n) * 0.5 * 12, s);
+  if (!n) {
+    cudaMemsetAsync(b.n_kept, 0, 4, s);
+  } else {
+    const uint32_t nb = nblk(n, kFlTile);
+    k_fl_count<<<nb, kFlThreads, 0, s>>>(b.acc_key, n, b.wl_bits, z.wl_log2, cnt);
+    count_launch();
+    scan_exclusive(cnt, cnt, nb, b.n_kept, tmp, s);
+    k_fl_scatter<<<nb, kFlThreads, 0, s>>>(b.acc_key, b.acc_idx, n, b.wl_bits, z.wl_log2, cnt, b.acc_key2,
+                                           b.acc_idx2);
+    count_launch();
+    std::swap(b.acc_key, b.acc_key2);
+    std::swap(b.acc_idx, b.acc_idx2);
+  }
+  p.end();
+}
+uint32_t filter_blocks(uint32_t n_acc) { return nblk(n_acc, kFlTile); }
+
 uint32_t sparse_check_blocks(uint32_t n_acc) { return nblk(n_acc, kCheckThreads); }
 
 void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
@@ -833,10 +994,12 @@ void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t
   WideCheckArgs a{};
   a.g = g;
   a.n = n;
+  a.n_dev = z.grouped ? b.n_kept : nullptr;
   a.idx = b.acc_idx;
   a.flag = b.wc_flag;
   a.run_excl = b.wc_run;
-  a.gs = b.wc_val;
+  a.gs = z.grouped ? b.acc_idx : b.wc_val;
+  a.grouped = z.grouped ? 1u : 0u;
   a.grp_lo = b.wc_grp_lo;
   a.grp_agent = b.wc_grp_agent;
   a.rc_off = b.wc_rc;

@@ -19,7 +19,7 @@ ERRORS = {-1: "INVALID_TRACE", -2: "OOM", -3: "CUDA", -4: "CAPACITY", -5: "TIMEO
           -8: "UNSUPPORTED"}
 ERR_INVALID_TRACE, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_STATE, ERR_ARGS, ERR_UNSUPPORTED = range(-1, -9, -1)
 EXPORTS = ("gwcp_create", "gwcp_load_trace", "gwcp_compute_order", "gwcp_report_races", "gwcp_debug_clock",
-           "gwcp_first_bad_index", "gwcp_profile_get", "gwcp_counters", "gwcp_launch_count", "gwcp_destroy",
+           "gwcp_first_bad_index", "gwcp_profile_get", "gwcp_profile_start", "gwcp_counters", "gwcp_launch_count", "gwcp_destroy",
            "gwcp_strerror", "gwcp_analyze_noalloc", "gwcp_pool_create", "gwcp_pool_submit", "gwcp_pool_wait",
            "gwcp_pool_run_batch", "gwcp_pool_set_active_lanes", "gwcp_pool_autotune", "gwcp_pool_now",
            "gwcp_pool_device_bytes", "gwcp_pool_destroy", "gwcp_set_ranker", "gwcp_location_features",
@@ -98,6 +98,7 @@ def load_library():
     L.gwcp_first_bad_index.restype = u64
     L.gwcp_profile_get.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(ctypes.c_double)]
+    L.gwcp_profile_start.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
     L.gwcp_counters.argtypes = [vp, ctypes.POINTER(u64)]
     L.gwcp_counters_ex.argtypes = [vp, ctypes.POINTER(u64), ctypes.c_uint32]
     L.gwcp_clock_bytes.argtypes = [vp, ctypes.POINTER(u64)]
@@ -151,7 +152,7 @@ def load_library():
     L.gwcp_strerror.argtypes = [i32]
     L.gwcp_strerror.restype = ctypes.c_char_p
     for name in ("gwcp_create", "gwcp_load_trace", "gwcp_compute_order", "gwcp_report_races", "gwcp_debug_clock",
-                 "gwcp_profile_get", "gwcp_counters", "gwcp_counters_ex"):
+                 "gwcp_profile_get", "gwcp_profile_start", "gwcp_counters", "gwcp_counters_ex"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -343,6 +344,16 @@ class Context:
         while self._L.gwcp_profile_get(self._h, i, ctypes.byref(name), ctypes.byref(ms), ctypes.byref(by)) == 0:
             out.append((name.value.decode(), float(ms.value), float(by.value)))
             i += 1
+        return out
+
+    def timeline(self) -> list[tuple[str, float, float]]:
+        """(name, start ms after the first kernel, duration ms) of each profiled kernel."""
+        out = []
+        at = ctypes.c_float()
+        for i, (name, ms, _) in enumerate(self.profile()):
+            if self._L.gwcp_profile_start(self._h, i, ctypes.byref(at)) != 0:
+                break
+            out.append((name, float(at.value), ms))
         return out
 
     def counters(self) -> dict:
