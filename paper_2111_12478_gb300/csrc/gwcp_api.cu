@@ -71,11 +71,7 @@ struct gwcp_ctx {
   bool compressed = false;     // GWCP_CLOCKS_COMPRESSED was in force at gwcp_load_trace
   uint64_t cv_cap_hint = 0;    // compressed versions: pool words that the last run needed
   uint64_t alloc_limit = 0;    // gwcp_debug_alloc_limit: cap on the cached buffers' bytes (0 = none)
-  cudaStream_t side = nullptr;  // runs the access grouping beside the propagation (lowest priority)
-  cudaStream_t hi = nullptr;    // runs the main phases (highest priority: the block scheduler
-                                // serves its short, latency-bound kernels before the side
-                                // stream's sort)
-  cudaEvent_t in_ev = nullptr, out_ev = nullptr;
+  cudaStream_t side = nullptr;  // runs the access sort and grouping beside the main phases
   cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr;
   cudaEvent_t sync_ev = nullptr;  // options.blocking_sync: host waits sleep on this event
   cudaStream_t alloc_s = nullptr;  // stream that buffer (re)allocations are ordered on
@@ -356,22 +352,21 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   // scratch of the side stream's sorts and scans
   uint32_t* side_tmp = get<uint32_t>(
       c, "side_tmp", std::max(radix_tmp_need(size_t(z.n_acc) + 1), scan_tmp_need(size_t(z.n_acc) * 4 + 2)) + 64, &oom);
-  uint32_t* fl_cnt = nullptr;
   if (z.wl_log2) {
     b.wl_bits = get<uint32_t>(c, "wl_bits", (size_t(1) << z.wl_log2) / 32, &oom);
     b.n_kept = get<uint32_t>(c, "n_kept", 1, &oom);
-    fl_cnt = get<uint32_t>(c, "fl_cnt", size_t(filter_blocks(z.n_acc)) + 2, &oom);
   }
   if (oom) return GWCP_ERR_OOM;
 
   phaseA_scatter(b, g, z, s, c->prof);
   // the access sort needs only the decoded accesses: it runs on the side stream beside the
-  // main stream's other phases and the propagation
+  // main stream's other phases (measured on the 8192-warp workload: it overlaps them, and
+  // the grouping ends before the propagation starts; with the side stream at a lower
+  // priority the sort drifts into the propagation and slows its latency-bound walkers)
   SideJoin side{c, s};
   cudaEventRecord(c->fork, s);
   cudaStreamWaitEvent(c->side, c->fork, 0);
   side.armed = true;
-  if (z.wl_log2) phaseH_filter(b, z, fl_cnt, side_tmp, c->side, c->prof);
   phaseH_sort(b, g, z, sort_mask, side_tmp, c->side, c->prof);
   phaseB_sync(b, g, z, s, c->prof);
   cudaMemsetAsync(b.vcount, 0, size_t(g.W + 1) * 4, s);
@@ -700,14 +695,9 @@ int gwcp_create(gwcp_ctx** out, int device, const gwcp_options* opt) {
   auto* c = new gwcp_ctx();
   c->device = device;
   if (opt) c->opt = *opt;
-  int prio_least = 0, prio_greatest = 0;
   if (cudaMallocHost(&c->st_host, sizeof(DevStatus)) != cudaSuccess ||
       cudaMallocHost(&c->cnt_host, 16 * sizeof(uint32_t)) != cudaSuccess ||
-      cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess ||
-      cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
-      cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->in_ev, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->out_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork2, cudaEventDisableTiming) != cudaSuccess ||
@@ -797,16 +787,9 @@ int gwcp_compute_order(gwcp_ctx* c, void* stream) {
     std::memset(c->clock_words, 0, sizeof(c->clock_words));
     return GWCP_OK;
   }
-  // the analysis runs on the context's high-priority stream, after the caller's earlier
-  // work on `stream`, which then waits for it
-  cudaStream_t user = static_cast<cudaStream_t>(stream);
-  cudaEventRecord(c->in_ev, user);
-  cudaStreamWaitEvent(c->hi, c->in_ev, 0);
-  int rc = run(c, c->hi);
-  for (int attempt = 0; rc == kRerun && attempt < 6; ++attempt) rc = run(c, c->hi);
+  int rc = run(c, static_cast<cudaStream_t>(stream));
+  for (int attempt = 0; rc == kRerun && attempt < 6; ++attempt) rc = run(c, static_cast<cudaStream_t>(stream));
   if (rc == kRerun) rc = GWCP_ERR_OOM;
-  cudaEventRecord(c->out_ev, c->hi);
-  cudaStreamWaitEvent(user, c->out_ev, 0);
   c->computed = true;
   c->compute_rc = rc;
   return rc;
@@ -1228,10 +1211,6 @@ void gwcp_destroy(gwcp_ctx* c) {
   if (c->fork2) cudaEventDestroy(c->fork2);
   if (c->sync_ev) cudaEventDestroy(c->sync_ev);
   if (c->side) cudaStreamDestroy(c->side);
-  if (c->hi) cudaStreamSynchronize(c->hi);
-  if (c->hi) cudaStreamDestroy(c->hi);
-  if (c->in_ev) cudaEventDestroy(c->in_ev);
-  if (c->out_ev) cudaEventDestroy(c->out_ev);
   delete c;
 }
 

@@ -328,8 +328,14 @@ size_t check_group_count(uint32_t n_acc) { return (check_chunks(n_acc) + GRP - 1
 void phaseH_sort(Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, uint32_t* tmp, cudaStream_t s, Prof& p) {
   (void)g;
   p.begin("h_sort", double(z.n_acc) * 12 * 3 * radix_windows(key_mask).size(), s);
-  if (radix_sort_pairs(b.acc_key, b.acc_idx, b.acc_key2, b.acc_idx2, z.n_acc, key_mask, tmp, s,
-                       z.wl_log2 ? b.n_kept : nullptr)) {
+  RadixKeep keep;
+  if (z.wl_log2) {  // the written-location filter of the grouped order, in the first pass
+    keep.bits = b.wl_bits;
+    keep.log2 = z.wl_log2;
+    keep.shift = 15;
+    keep.n_out = b.n_kept;
+  }
+  if (radix_sort_pairs(b.acc_key, b.acc_idx, b.acc_key2, b.acc_idx2, z.n_acc, key_mask, tmp, s, nullptr, keep)) {
     std::swap(b.acc_key, b.acc_key2);
     std::swap(b.acc_idx, b.acc_idx2);
   }

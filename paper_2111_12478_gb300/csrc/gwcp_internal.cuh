@@ -222,9 +222,17 @@ void scan_exclusive(const uint32_t* in, uint32_t* out, size_t n, uint32_t* total
 // Ping-pongs between (k0, v0) and (k1, v1); returns true if the result is in (k1, v1).
 // tmp must hold radix_tmp_need(n) u32. With n_dev, only the first min(n, *n_dev) pairs are
 // sorted (a count known on the device only; n bounds it).
+// With keep.bits, the first pass keeps only the pairs whose bit wl_bit(key >> keep.shift,
+// keep.log2) is set in keep.bits (a stable filter folded into the sort); the kept count is
+// written to keep.n_out and bounds the later passes.
+struct RadixKeep {
+  const uint32_t* bits = nullptr;
+  uint32_t log2 = 0, shift = 0;
+  uint32_t* n_out = nullptr;
+};
 size_t radix_tmp_need(size_t n);
 bool radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, size_t n, uint64_t mask,
-                      uint32_t* tmp, cudaStream_t s, const uint32_t* n_dev = nullptr);
+                      uint32_t* tmp, cudaStream_t s, const uint32_t* n_dev = nullptr, RadixKeep keep = {});
 // Digit windows covering the bits of `mask` (low bit of each window).
 std::vector<int> radix_windows(uint64_t mask);
 
@@ -468,9 +476,6 @@ void stamp_now(unsigned long long* at, cudaStream_t s);
 int phaseG_wide(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s);
 void phaseI_wide_group(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t s, Prof& p);
 void phaseI_grouped(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t s, Prof& p);
-// written-location filter of the grouped order (before its sort); cnt: filter_blocks + 1 words
-void phaseH_filter(Bufs& b, const Sizes& z, uint32_t* cnt, uint32_t* tmp, cudaStream_t s, Prof& p);
-uint32_t filter_blocks(uint32_t n_acc);
 void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 uint32_t sparse_check_blocks(uint32_t n_acc);  // timeline entries of the partner-group check
 

@@ -77,8 +77,15 @@ __global__ void k_scan_apply(const uint32_t* in, uint32_t* out, size_t n, const 
 
 constexpr int RS_THREADS = 256, RS_ITEMS = 8, RS_TILE = RS_THREADS * RS_ITEMS;
 
+// a pair the filter of the first pass keeps
+__device__ __forceinline__ bool radix_kept(uint64_t key, const RadixKeep& kp) {
+  if (!kp.bits) return true;
+  const uint32_t h = wl_bit(key >> kp.shift, kp.log2);
+  return (__ldg(kp.bits + (h >> 5)) >> (h & 31)) & 1u;
+}
+
 __global__ void k_radix_hist(const uint64_t* keys, size_t n, const uint32_t* n_dev, int shift, uint32_t* hist,
-                             uint32_t ntiles) {
+                             uint32_t ntiles, RadixKeep kp) {
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
   if (n_dev && *n_dev < n) n = *n_dev;  // the count may be known on the device only
@@ -87,7 +94,10 @@ __global__ void k_radix_hist(const uint64_t* keys, size_t n, const uint32_t* n_d
 #pragma unroll
   for (int j = 0; j < RS_ITEMS; ++j) {
     size_t i = base + size_t(j) * RS_THREADS + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    if (i < n) {
+      const uint64_t k = keys[i];
+      if (radix_kept(k, kp)) atomicAdd(&h[(k >> shift) & 255u], 1u);
+    }
   }
   __syncthreads();
   hist[size_t(threadIdx.x) * ntiles + blockIdx.x] = h[threadIdx.x];
@@ -101,7 +111,8 @@ __global__ void k_radix_hist(const uint64_t* keys, size_t n, const uint32_t* n_d
 __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint64_t* kin, const uint32_t* vin,
                                                               uint64_t* kout, uint32_t* vout, size_t n,
                                                               const uint32_t* n_dev, int shift,
-                                                              const uint32_t* offs, uint32_t ntiles) {
+                                                              const uint32_t* offs, uint32_t ntiles,
+                                                              RadixKeep kp) {
   if (n_dev && *n_dev < n) n = *n_dev;
   __shared__ uint32_t cnt[RS_THREADS / 32][256];
   __shared__ uint32_t tile_off[256];  // first position of each digit in the tile's digit order
@@ -120,8 +131,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint64_t* ki
 #pragma unroll
   for (int r = 0; r < RS_ITEMS; ++r) {
     size_t i = base + size_t(r) * 32 + lane;
-    bool valid = i < n;
-    k[r] = valid ? kin[i] : 0;
+    k[r] = i < n ? kin[i] : 0;
+    const bool valid = i < n && radix_kept(k[r], kp);
     v[r] = (valid && vin) ? vin[i] : 0;
     uint32_t d = valid ? uint32_t((k[r] >> shift) & 255u) : 256u;
     uint32_t peers = __match_any_sync(0xffffffffu, d);
@@ -156,7 +167,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint64_t* ki
     }
   }
   __syncthreads();
-  const uint32_t nvalid = tile_base >= n ? 0u : n - tile_base < size_t(RS_TILE) ? uint32_t(n - tile_base) : uint32_t(RS_TILE);
+  const uint32_t nvalid = tot;  // the tile's (kept) pairs, in digit order in sk / sv
   for (uint32_t i = threadIdx.x; i < nvalid; i += RS_THREADS) {
     const uint64_t key = sk[i];
     const uint32_t d = uint32_t((key >> shift) & 255u);
@@ -206,22 +217,33 @@ size_t radix_tmp_need(size_t n) {
 }
 
 bool radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, size_t n, uint64_t mask,
-                      uint32_t* tmp, cudaStream_t s, const uint32_t* n_dev) {
-  if (n <= 1) return false;
+                      uint32_t* tmp, cudaStream_t s, const uint32_t* n_dev, RadixKeep keep) {
+  if (keep.bits) {
+    if (n == 0) {
+      cudaMemsetAsync(keep.n_out, 0, 4, s);
+      return false;
+    }
+    if (mask == 0) mask = 1;  // the filter needs one pass
+  } else if (n <= 1) {
+    return false;
+  }
   const uint32_t ntiles = uint32_t((n + RS_TILE - 1) / RS_TILE);
   uint32_t* hist = tmp;
   uint32_t* stmp = tmp + size_t(256) * ntiles;
-  bool in_second = false;
+  bool in_second = false, first = true;
   for (int lo : radix_windows(mask)) {
     uint64_t* kin = in_second ? k1 : k0;
     uint32_t* vin = in_second ? v1 : v0;
     uint64_t* kout = in_second ? k0 : k1;
     uint32_t* vout = in_second ? v0 : v1;
-    k_radix_hist<<<ntiles, RS_THREADS, 0, s>>>(kin, n, n_dev, lo, hist, ntiles);
+    const RadixKeep kp = first ? keep : RadixKeep{};
+    first = false;
+    k_radix_hist<<<ntiles, RS_THREADS, 0, s>>>(kin, n, n_dev, lo, hist, ntiles, kp);
     count_launch();
-    scan_exclusive(hist, hist, size_t(256) * ntiles, nullptr, stmp, s);
-    k_radix_scatter<<<ntiles, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, n_dev, lo, hist, ntiles);
+    scan_exclusive(hist, hist, size_t(256) * ntiles, kp.bits ? kp.n_out : nullptr, stmp, s);
+    k_radix_scatter<<<ntiles, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, n_dev, lo, hist, ntiles, kp);
     count_launch();
+    if (kp.bits) n_dev = kp.n_out;  // later passes sort the kept pairs
     in_second = !in_second;
   }
   return in_second;

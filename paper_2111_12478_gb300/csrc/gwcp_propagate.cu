@@ -52,25 +52,25 @@ struct PropArgs {
   unsigned long long *cv_used, *cv_words;  // pool words handed out; words written
 };
 
+// Clock rows another walker may still be writing: every word goes once from SENTINEL to
+// its value, and a reader takes a row only when no word is SENTINEL, so relaxed gpu-scope
+// accesses (each word single-copy atomic, no order between words needed) make the
+// exchange race-free under the PTX memory model; they cost what .cg accesses cost.
 template <int K>
 __device__ __forceinline__ void load_row(const uint32_t* row, uint32_t (&x)[K]) {
   const int lane = threadIdx.x & 31;
   const uint32_t* p = row + lane * K;
   if constexpr (K == 1) {
-    x[0] = __ldcg(p);
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(x[0]) : "l"(p) : "memory");
   } else if constexpr (K == 2) {
-    uint2 a = __ldcg(reinterpret_cast<const uint2*>(p));
-    x[0] = a.x;
-    x[1] = a.y;
+    asm volatile("ld.relaxed.gpu.global.v2.u32 {%0, %1}, [%2];" : "=r"(x[0]), "=r"(x[1]) : "l"(p) : "memory");
   } else {
 #pragma unroll
-    for (int j = 0; j < K; j += 4) {
-      uint4 a = __ldcg(reinterpret_cast<const uint4*>(p + j));
-      x[j] = a.x;
-      x[j + 1] = a.y;
-      x[j + 2] = a.z;
-      x[j + 3] = a.w;
-    }
+    for (int j = 0; j < K; j += 4)
+      asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                   : "=r"(x[j]), "=r"(x[j + 1]), "=r"(x[j + 2]), "=r"(x[j + 3])
+                   : "l"(p + j)
+                   : "memory");
   }
 }
 
@@ -79,12 +79,15 @@ __device__ __forceinline__ void store_row(uint32_t* row, const uint32_t (&x)[K])
   const int lane = threadIdx.x & 31;
   uint32_t* p = row + lane * K;
   if constexpr (K == 1) {
-    __stcg(p, x[0]);
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(x[0]) : "memory");
   } else if constexpr (K == 2) {
-    __stcg(reinterpret_cast<uint2*>(p), make_uint2(x[0], x[1]));
+    asm volatile("st.relaxed.gpu.global.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(x[0]), "r"(x[1]) : "memory");
   } else {
 #pragma unroll
-    for (int j = 0; j < K; j += 4) __stcg(reinterpret_cast<uint4*>(p + j), make_uint4(x[j], x[j + 1], x[j + 2], x[j + 3]));
+    for (int j = 0; j < K; j += 4)
+      asm volatile("st.relaxed.gpu.global.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p + j), "r"(x[j]), "r"(x[j + 1]),
+                   "r"(x[j + 2]), "r"(x[j + 3])
+                   : "memory");
   }
 }
 

@@ -726,63 +726,9 @@ __global__ void __launch_bounds__(kCheckThreads, 8) k_wc_check(WideCheckArgs a) 
 
 // ---- grouped order: the accesses sorted once by (location, class, agent, trace index) ----
 // Before the sort, the accesses of locations without a write-class access are left out
-// (two reads never race): a stable compaction of those whose location's bit is set in the
-// hashed bitmap that the decoding pass filled from the write-class accesses. A bit shared
-// with a written location keeps a few read-only locations; they have no partners.
-constexpr uint32_t kFlThreads = 256, kFlItems = 8, kFlTile = kFlThreads * kFlItems;
-
-__device__ __forceinline__ bool wl_kept(uint64_t ck, const uint32_t* bits, uint32_t log2) {
-  const uint32_t h = wl_bit(ck >> 15, log2);
-  return (__ldg(bits + (h >> 5)) >> (h & 31)) & 1u;
-}
-
-__global__ void k_fl_count(const uint64_t* ck, uint32_t n, const uint32_t* bits, uint32_t log2, uint32_t* cnt) {
-  const size_t base = size_t(blockIdx.x) * kFlTile;
-  uint32_t c = 0;
-#pragma unroll
-  for (uint32_t j = 0; j < kFlItems; ++j) {
-    const size_t i = base + j * kFlThreads + threadIdx.x;
-    if (i < n && wl_kept(ck[i], bits, log2)) ++c;
-  }
-  c = __reduce_add_sync(0xffffffffu, c);
-  __shared__ uint32_t ws[kFlThreads / 32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t t = 0;
-    for (uint32_t w = 0; w < kFlThreads / 32; ++w) t += ws[w];
-    cnt[blockIdx.x] = t;
-  }
-}
-
-// rounds of kFlThreads consecutive accesses; a block-wide count per round keeps the order
-__global__ void k_fl_scatter(const uint64_t* ck, const uint32_t* idx, uint32_t n, const uint32_t* bits,
-                             uint32_t log2, const uint32_t* off, uint64_t* ck_out, uint32_t* idx_out) {
-  const size_t base = size_t(blockIdx.x) * kFlTile;
-  uint32_t run = off[blockIdx.x];
-  __shared__ uint32_t ws[kFlThreads / 32];
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t j = 0; j < kFlItems; ++j) {
-    const size_t i = base + j * kFlThreads + threadIdx.x;
-    const uint64_t k = i < n ? ck[i] : 0;
-    const bool keep = i < n && wl_kept(k, bits, log2);
-    const uint32_t m = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) ws[warp] = __popc(m);
-    __syncthreads();
-    uint32_t before = 0, total = 0;
-    for (uint32_t w = 0; w < kFlThreads / 32; ++w) {
-      if (w < warp) before += ws[w];
-      total += ws[w];
-    }
-    if (keep) {
-      const uint32_t q = run + before + __popc(m & lanemask_lt());
-      ck_out[q] = k;
-      idx_out[q] = idx[i];
-    }
-    run += total;
-    __syncthreads();
-  }
-}
+// (two reads never race): the sort's first pass keeps only those whose location's bit is
+// set in the hashed bitmap that the decoding pass filled from the write-class accesses. A
+// bit shared with a written location keeps a few read-only locations; they have no partners.
 
 // location runs and (class, agent) groups of the composite keys (the first *n_dev keys)
 __global__ void k_gr_flags(const uint64_t* ck, uint32_t n, const uint32_t* n_dev, uint32_t* run_flag,
@@ -964,27 +910,6 @@ void phaseI_grouped(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t
   p.end();
 }
 
-// The written-location filter of the grouped order: the kept accesses (count at n_kept)
-// into the alternate buffers, which then become the primary ones.
-void phaseH_filter(Bufs& b, const Sizes& z, uint32_t* cnt, uint32_t* tmp, cudaStream_t s, Prof& p) {
-  const uint32_t n = z.n_acc;
-  p.begin("h_filter", double(n) * (8 + 12) + double(n) * 0.5 * 12, s);
-  if (!n) {
-    cudaMemsetAsync(b.n_kept, 0, 4, s);
-  } else {
-    const uint32_t nb = nblk(n, kFlTile);
-    k_fl_count<<<nb, kFlThreads, 0, s>>>(b.acc_key, n, b.wl_bits, z.wl_log2, cnt);
-    count_launch();
-    scan_exclusive(cnt, cnt, nb, b.n_kept, tmp, s);
-    k_fl_scatter<<<nb, kFlThreads, 0, s>>>(b.acc_key, b.acc_idx, n, b.wl_bits, z.wl_log2, cnt, b.acc_key2,
-                                           b.acc_idx2);
-    count_launch();
-    std::swap(b.acc_key, b.acc_key2);
-    std::swap(b.acc_idx, b.acc_idx2);
-  }
-  p.end();
-}
-uint32_t filter_blocks(uint32_t n_acc) { return nblk(n_acc, kFlTile); }
 
 uint32_t sparse_check_blocks(uint32_t n_acc) { return nblk(n_acc, kCheckThreads); }
 
