@@ -726,21 +726,25 @@ def main():
     # the step's result lands in a reused pinned buffer (one DMA, no page faults)
     out_pinned = torch.empty((max(len(races), 1) + 1024) * 2, dtype=torch.int64).pin_memory()
     out_np = out_pinned.numpy().view(np.uint64).reshape(-1, 2)
+    parts = []  # per step: device ms of the H2D copy, the analysis, the race read-back
     for it in range(args.e2e_steps + 1 if args.e2e_steps else 0):
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        ev4 = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev4[0].record(stream)
         t0 = time.perf_counter()
         rc = ctx_e2e._L.gwcp_load_trace(ctx_e2e._h, pinned.data_ptr(), n_ev, gwcp.Geometry(*geo.astuple(), 0), 0,
                                         stream.cuda_stream)
         assert rc == 0, rc
+        ev4[1].record(stream)
         ctx_e2e.compute_order(stream=stream)
+        ev4[2].record(stream)
         got = ctx_e2e.report_races(stream=stream, out=out_np)
-        e1.record(stream)
+        ev4[3].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         if it:  # the first round sizes the context's buffers
-            e2e_times.append(max(wall, e0.elapsed_time(e1) / 1e3))
+            e2e_times.append(max(wall, ev4[0].elapsed_time(ev4[3]) / 1e3))
+            parts.append([ev4[j].elapsed_time(ev4[j + 1]) for j in range(3)])
         d2h = got.nbytes + 8
     e2e_value = n_ev * world / statistics.mean(e2e_times) if e2e_times else None
     ctx_e2e.close()
@@ -784,7 +788,10 @@ def main():
                        "plant_frac": wp["plant_frac"], "seed": SEED, "parallelism": f"replicas{world}",
                        "l2": f"inputs larger than L2 ({ev.nbytes / 1e6:.0f} MB trace; larger working set per step)"},
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": int(ev.nbytes),
-                    "d2h_bytes_per_step": int(d2h)} if e2e_value else None,
+                    "d2h_bytes_per_step": int(d2h), "steps": len(e2e_times),
+                    "step_ms": [round(t * 1e3, 2) for t in e2e_times],
+                    "device_ms_h2d_analysis_d2h": [round(float(np.mean([p[j] for p in parts])), 2) for j in range(3)]}
+            if e2e_value else None,
             "roofline": prop_roofline("k_prop_wide" if tiles else "k_propagate", args.workload,
                                       phases["g_propagate"][0], cnt, geo.num_agents, tiles, peak, peak_kind),
             "roofline_check": (check_roofline(phases["i_check"][0], phases["i_check"][1], cnt, len(races),

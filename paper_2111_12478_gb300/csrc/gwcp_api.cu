@@ -232,14 +232,19 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   z.forced_barrier = c->opt.forced_barrier != 0 || z.compress;
   z.sparse_check = g.nT || z.compress || c->check_mode == GWCP_CHECK_SPARSE ||
                    (c->check_mode == GWCP_CHECK_AUTO && g.W >= kSparseCheckFromAgents);
-  z.TA = g.Wp <= 256 ? 2048 : 8192;
-  while (uint64_t(g.W) * ((z.N + z.TA - 1) / z.TA) > (1ull << 26)) z.TA <<= 1;  // bounded agent histogram
+  // many agents: S by a sort on the agent (a per-warp count table of Wp words would leave
+  // phase A a few warps per SM)
+  z.agent_sort = g.Wp > 2048;
+  z.TA = g.Wp <= 256 || z.agent_sort ? 2048 : 8192;
+  if (!z.agent_sort)
+    while (uint64_t(g.W) * ((z.N + z.TA - 1) / z.TA) > (1ull << 26)) z.TA <<= 1;  // bounded agent histogram
   z.ntA = uint32_t((z.N + z.TA - 1) / z.TA);
+  const size_t hist_words = z.agent_sort ? 1 : size_t(g.W) * z.ntA + 1;
   b.ev = c->ev_dev;
   b.st = get<DevStatus>(c, "st", 1, &oom);
-  b.hist_a = get<uint32_t>(c, "hist_a", size_t(g.W) * z.ntA + 1, &oom);
-  b.tile_cnt = get<uint32_t>(c, "tile_cnt", 3 * (size_t(z.ntA) + 1), &oom);
-  const size_t scan_need = std::max({scan_tmp_need(size_t(g.W) * z.ntA + 1), radix_tmp_need(z.N + 1),
+  b.hist_a = get<uint32_t>(c, "hist_a", hist_words, &oom);
+  b.tile_cnt = get<uint32_t>(c, "tile_cnt", 4 * (size_t(z.ntA) + 1), &oom);
+  const size_t scan_need = std::max({scan_tmp_need(hist_words), radix_tmp_need(z.N + 1),
                                      scan_tmp_need(z.N + 1)}) + 64;
   b.scan_tmp = get<uint32_t>(c, "scan_tmp", scan_need, &oom);
   if (oom) return GWCP_ERR_OOM;
@@ -256,8 +261,8 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   // ---- A: counts, then sync 1 -------------------------------------------------------
   phaseA_count(b, g, z, s, c->prof);
   {
-    const uint32_t* ex[4] = {b.hist_a + size_t(g.W) * z.ntA, b.tile_cnt + z.ntA, b.tile_cnt + 2 * z.ntA + 1,
-                             b.tile_cnt + 3 * z.ntA + 2};
+    const uint32_t* ex[4] = {z.agent_sort ? b.tile_cnt + 4 * z.ntA + 3 : b.hist_a + size_t(g.W) * z.ntA,
+                             b.tile_cnt + z.ntA, b.tile_cnt + 2 * z.ntA + 1, b.tile_cnt + 3 * z.ntA + 2};
     int rc = read_status(c, s, ex, 4);
     if (rc) return rc;
   }
@@ -295,6 +300,11 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   b.seg = get<uint32_t>(c, "seg", g.W + 1, &oom);
   b.acqrel = get<uint32_t>(c, "acqrel", z.n_acqrel, &oom);
   b.bar = get<uint32_t>(c, "bar", z.n_bar, &oom);
+  if (z.agent_sort) {
+    b.s_key = get<uint64_t>(c, "s_key", z.nS, &oom);
+    b.s_key2 = get<uint64_t>(c, "s_key2", z.nS, &oom);
+    b.s_tmp = get<uint32_t>(c, "s_tmp", radix_tmp_need(size_t(z.nS) + 1) + 64, &oom);
+  }
   b.acc_key = get<uint64_t>(c, "acc_key", z.n_acc, &oom);
   b.acc_idx = get<uint32_t>(c, "acc_idx", z.n_acc, &oom);
   b.acc_key2 = get<uint64_t>(c, "acc_key2", z.n_acc, &oom);

@@ -91,7 +91,11 @@ struct Bufs {
   DevStatus* st = nullptr;
   // phase A: agent counting sort, trace-order compactions
   uint32_t* hist_a = nullptr;    // [W * ntA + 1]
-  uint32_t* tile_cnt = nullptr;  // [3 * ntA + 3]: accesses, acq/rel, barriers per tile
+  uint32_t* tile_cnt = nullptr;  // [3 * ntA + 3]: accesses, acq/rel, barriers per tile (+ S entries
+                                 // per tile when S is built by sorting)
+  uint64_t* s_key = nullptr;     // [nS] (agent << 32 | S entry), sorted by agent (+ alt)
+  uint64_t* s_key2 = nullptr;
+  uint32_t* s_tmp = nullptr;     // the agent sort's scratch
   uint32_t* S = nullptr;         // [nS]
   uint32_t* seg = nullptr;       // [W + 1] start of each agent's segment in S
   uint32_t* acqrel = nullptr;    // [n_acqrel] trace indices
@@ -378,6 +382,9 @@ struct Sizes {
   bool grouped = false;
   uint32_t comp_lo = 0, comp_span = 0;
   uint32_t wl_log2 = 0;  // bits of the written-location bitmap (log2); 0 = no filter
+  // many agents: S is built by a stable sort of (agent, entry) keys instead of per-(agent,
+  // tile) counting tables (which would limit phase A to a few warps per SM)
+  bool agent_sort = false;
 };
 
 // bit of a location (the composite key without its class and agent) in the

@@ -140,12 +140,49 @@ __global__ void k_a_count(const Event* ev, uint64_t N, Geo g, uint32_t TA, uint3
   }
 }
 
+// Trace-order compactions of one round of 32 events (lane order is trace order): access
+// keys and indices (with the written-location bitmap of the grouped order), acquire/release
+// and barrier indices. Returns the barrier ballot of the round.
+struct ACompact {
+  uint64_t* acc_key;
+  uint32_t* acc_idx;
+  uint32_t* acqrel;
+  uint32_t* bar;
+  uint32_t comp_lo, comp_span;  // composite access keys when comp_span > 0
+  uint32_t* wl_bits;
+  uint32_t wl_log2;
+};
+
+__device__ __forceinline__ uint32_t a_compact(const ACompact& c, const Event& e, uint64_t i, bool acc, bool ar,
+                                              bool isbar, const Geo& g, uint32_t lt, uint32_t& o_acc,
+                                              uint32_t& o_ar, uint32_t& o_bar) {
+  uint32_t m = __ballot_sync(0xffffffffu, acc);
+  if (acc) {
+    const uint32_t p = o_acc + __popc(m & lt);
+    const uint64_t loc = location_key(e, g.apb);
+    const uint32_t cls = access_class(e);
+    const uint64_t key = c.comp_span ? composite_key(loc, cls, e.agent, c.comp_lo, c.comp_span) : loc;
+    c.acc_key[p] = key;
+    c.acc_idx[p] = uint32_t(i);
+    if (c.wl_log2 && cls != C_READ) {  // a write-class access marks its location
+      const uint32_t h = wl_bit(key >> 15, c.wl_log2);
+      atomicOr(c.wl_bits + (h >> 5), 1u << (h & 31));
+    }
+  }
+  o_acc += __popc(m);
+  m = __ballot_sync(0xffffffffu, ar);
+  if (ar) c.acqrel[o_ar + __popc(m & lt)] = uint32_t(i);
+  o_ar += __popc(m);
+  m = __ballot_sync(0xffffffffu, isbar);
+  if (isbar) c.bar[o_bar + __popc(m & lt)] = uint32_t(i);
+  o_bar += __popc(m);
+  return m;
+}
+
 // Phase A, pass 2: stable scatter into the agent-sorted stream S and the trace-order
 // compactions. Chunks with a barrier are processed one event at a time.
 __global__ void k_a_scatter(const Event* ev, uint64_t N, Geo g, uint32_t TA, uint32_t ntA, const uint32_t* hist,
-                            const uint32_t* tile_off, uint32_t* S, uint64_t* acc_key, uint32_t* acc_idx,
-                            uint32_t* acqrel, uint32_t* bar, uint32_t comp_lo, uint32_t comp_span,
-                            uint32_t* wl_bits, uint32_t wl_log2, bool vec) {
+                            const uint32_t* tile_off, uint32_t* S, ACompact cpt, bool vec) {
   extern __shared__ uint32_t sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -176,27 +213,7 @@ __global__ void k_a_scatter(const Event* ev, uint64_t N, Geo g, uint32_t TA, uin
       const bool ar = ok && (e.op == GWCP_ACQ || e.op == GWCP_REL);
       const bool isbar = ok && e.op == GWCP_BARRIER;
       const uint32_t kind = entry_kind(e.op);
-      // trace-order compactions
-      uint32_t m = __ballot_sync(0xffffffffu, acc);
-      if (acc) {
-        uint32_t p = o_acc + __popc(m & lt);
-        const uint64_t loc = location_key(e, g.apb);
-        const uint32_t cls = access_class(e);
-        const uint64_t key = comp_span ? composite_key(loc, cls, e.agent, comp_lo, comp_span) : loc;
-        acc_key[p] = key;
-        acc_idx[p] = uint32_t(i);
-        if (wl_log2 && cls != C_READ) {  // a write-class access marks its location
-          const uint32_t h = wl_bit(key >> 15, wl_log2);
-          atomicOr(wl_bits + (h >> 5), 1u << (h & 31));
-        }
-      }
-      o_acc += __popc(m);
-      m = __ballot_sync(0xffffffffu, ar);
-      if (ar) acqrel[o_ar + __popc(m & lt)] = uint32_t(i);
-      o_ar += __popc(m);
-      m = __ballot_sync(0xffffffffu, isbar);
-      if (isbar) bar[o_bar + __popc(m & lt)] = uint32_t(i);
-      o_bar += __popc(m);
+      const uint32_t m = a_compact(cpt, e, i, acc, ar, isbar, g, lt, o_acc, o_ar, o_bar);
       // agent-sorted stream
       if (!m) {
         const bool in_s = acc || ar;
@@ -239,6 +256,145 @@ __global__ void k_a_scatter(const Event* ev, uint64_t N, Geo g, uint32_t TA, uin
       }
     }
   }
+}
+
+// ---- Phase A with many agents: S from a stable sort on the agent ---------------------
+// Pass 1, one warp per tile of TA events: per-tile counts of accesses, acquires/releases,
+// barriers and S entries (an access or acquire/release is one entry of its agent, a
+// barrier one entry per member), W1 and the key / lock bit summaries.
+__global__ void k_aw_count(const Event* ev, uint64_t N, Geo g, uint32_t TA, uint32_t ntA, uint32_t* tile_cnt,
+                           DevStatus* st, bool vec) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (tile >= ntA) return;
+  const uint64_t lo = uint64_t(tile) * TA, hi = (lo + TA < N ? lo + TA : N);
+  uint32_t n_acc = 0, n_ar = 0, n_bar = 0, n_s = 0;
+  uint64_t kor = 0, kand = ~0ull, lor = 0, land = ~0ull;
+  for (uint64_t base0 = lo; base0 < hi; base0 += 32 * kAhead) {
+    Event eb[kAhead];
+#pragma unroll
+    for (int r = 0; r < kAhead; ++r) {
+      const uint64_t i = base0 + r * 32 + lane;
+      eb[r] = i < hi ? load_event(ev, i, vec) : Event{};
+    }
+#pragma unroll
+    for (int r = 0; r < kAhead; ++r) {
+      if (base0 + r * 32 >= hi) break;
+      const uint64_t i = base0 + r * 32 + lane;
+      const bool valid = i < hi;
+      const Event e = eb[r];
+      const bool ok = !valid || validate_w1(e, g);
+      if (!ok) set_error(st, GWCP_ERR_INVALID_TRACE, i);
+      const bool acc = valid && ok && e.op <= GWCP_ATOMIC;
+      const bool ar = valid && ok && (e.op == GWCP_ACQ || e.op == GWCP_REL);
+      const bool bar = valid && ok && e.op == GWCP_BARRIER;
+      const uint32_t ns = bar ? barrier_members(e, g).count : (acc || ar) ? 1u : 0u;
+      if (acc) {
+        const uint64_t k = location_key(e, g.apb);
+        kor |= k;
+        kand &= k;
+      }
+      if (ar) {
+        lor |= e.addr;
+        land &= e.addr;
+      }
+      n_acc += __popc(__ballot_sync(0xffffffffu, acc));
+      n_ar += __popc(__ballot_sync(0xffffffffu, ar));
+      n_bar += __popc(__ballot_sync(0xffffffffu, bar));
+      n_s += __reduce_add_sync(0xffffffffu, ns);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    kor |= __shfl_xor_sync(0xffffffffu, kor, o);
+    kand &= __shfl_xor_sync(0xffffffffu, kand, o);
+    lor |= __shfl_xor_sync(0xffffffffu, lor, o);
+    land &= __shfl_xor_sync(0xffffffffu, land, o);
+  }
+  if (lane == 0) {
+    tile_cnt[tile] = n_acc;
+    tile_cnt[ntA + 1 + tile] = n_ar;
+    tile_cnt[2 * (ntA + 1) + tile] = n_bar;
+    tile_cnt[3 * (ntA + 1) + tile] = n_s;
+    if (n_acc) {
+      atomicOr(&st->key_or, kor);
+      atomicAnd(&st->key_and, kand);
+    }
+    if (n_ar) {
+      atomicOr(&st->lock_or, lor);
+      atomicAnd(&st->lock_and, land);
+    }
+  }
+}
+
+// Pass 2: the trace-order compactions and the S keys (agent << 32 | S entry) in trace
+// order, barrier members at the barrier's place; a stable sort on the agent bits then
+// gives S (each agent's entries in trace order).
+__global__ void k_aw_scatter(const Event* ev, uint64_t N, Geo g, uint32_t TA, uint32_t ntA, const uint32_t* tile_off,
+                             uint64_t* skey, ACompact cpt, bool vec) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (tile >= ntA) return;
+  uint32_t o_acc = tile_off[tile], o_ar = tile_off[ntA + 1 + tile], o_bar = tile_off[2 * (ntA + 1) + tile];
+  uint32_t o_s = tile_off[3 * (ntA + 1) + tile];
+  const uint32_t lt = lanemask_lt();
+  const uint64_t lo = uint64_t(tile) * TA, hi = (lo + TA < N ? lo + TA : N);
+  for (uint64_t base0 = lo; base0 < hi; base0 += 32 * kAhead) {
+    Event eb[kAhead];
+#pragma unroll
+    for (int r = 0; r < kAhead; ++r) {
+      const uint64_t i = base0 + r * 32 + lane;
+      eb[r] = i < hi ? load_event(ev, i, vec) : Event{};
+    }
+#pragma unroll
+    for (int r = 0; r < kAhead; ++r) {
+      if (base0 + r * 32 >= hi) break;
+      const uint64_t i = base0 + r * 32 + lane;
+      const Event e = eb[r];
+      // events that break W1 are left out, as in the counting pass
+      const bool ok = i < hi && validate_w1(e, g);
+      const bool acc = ok && e.op <= GWCP_ATOMIC;
+      const bool ar = ok && (e.op == GWCP_ACQ || e.op == GWCP_REL);
+      const bool isbar = ok && e.op == GWCP_BARRIER;
+      a_compact(cpt, e, i, acc, ar, isbar, g, lt, o_acc, o_ar, o_bar);
+      BarMembers bm{0, 0, 0, false};
+      uint32_t ns = (acc || ar) ? 1u : 0u;
+      if (isbar) {
+        bm = barrier_members(e, g);
+        ns = bm.count;
+      }
+      const uint32_t incl = warp_inclusive_scan(ns);
+      const uint32_t q = o_s + incl - ns;
+      if (acc || ar) {
+        skey[q] = (uint64_t(e.agent) << 32) | (entry_kind(e.op) << 30) | uint32_t(i);
+      } else if (isbar) {
+        for (uint32_t j = 0; j < bm.count; ++j)
+          skey[q + j] = (uint64_t(member_at(bm, j)) << 32) | (K_BAR << 30) | uint32_t(i);
+      }
+      o_s += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+}
+
+__global__ void k_aw_extract(const uint64_t* key, uint32_t n, uint32_t* S) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) S[p] = uint32_t(key[p]);
+}
+
+// seg[u]: the first S position of agent u (seg[W] = n)
+__global__ void k_aw_seg(const uint64_t* key, uint32_t n, uint32_t W, uint32_t* seg) {
+  const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u > W) return;
+  const uint64_t x = uint64_t(u) << 32;
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (key[mid] < x)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  seg[u] = lo;
 }
 
 __global__ void k_a_segments(const uint32_t* hist, uint32_t W, uint32_t ntA, uint32_t nS, uint32_t* seg) {
@@ -948,8 +1104,18 @@ inline uint32_t a_warps(const Geo& g) {
 
 void phaseA_count(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   p.begin("a_count", double(z.N) * 16);
-  const uint32_t aw = a_warps(g);
   const bool vec = (reinterpret_cast<uintptr_t>(b.ev) & 15) == 0;
+  if (z.agent_sort) {
+    k_aw_count<<<blocks(z.ntA, 8), 256, 0, s>>>(b.ev, z.N, g, z.TA, z.ntA, b.tile_cnt, b.st, vec);
+    count_launch();
+    p.end();
+    for (int q = 0; q < 4; ++q) {  // in-place exclusive scans of the per-tile counts
+      uint32_t* t = b.tile_cnt + q * (z.ntA + 1);
+      scan_exclusive(t, t, z.ntA, t + z.ntA, b.scan_tmp, s);
+    }
+    return;
+  }
+  const uint32_t aw = a_warps(g);
   k_a_count<<<blocks(z.ntA, aw), aw * 32, aw * g.Wp * 4, s>>>(b.ev, z.N, g, z.TA, z.ntA, b.hist_a,
                                                                           b.tile_cnt, b.st, vec);
   count_launch();
@@ -965,11 +1131,29 @@ void phaseA_count(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, P
 void phaseA_scatter(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   p.begin("a_scatter", double(z.N) * 16 + double(z.nS) * 4 + double(z.n_acc) * 12);
   if (z.wl_log2) cudaMemsetAsync(b.wl_bits, 0, (size_t(1) << z.wl_log2) / 8, s);
+  const bool vec = (reinterpret_cast<uintptr_t>(b.ev) & 15) == 0;
+  const ACompact cpt{b.acc_key, b.acc_idx, b.acqrel, b.bar, z.grouped ? z.comp_lo : 0u,
+                     z.grouped ? z.comp_span : 0u, b.wl_bits, z.wl_log2};
+  if (z.agent_sort) {
+    k_aw_scatter<<<blocks(z.ntA, 8), 256, 0, s>>>(b.ev, z.N, g, z.TA, z.ntA, b.tile_cnt, b.s_key, cpt, vec);
+    count_launch();
+    uint32_t ab = 0;
+    while ((1u << ab) < g.W) ++ab;
+    const uint64_t mask = ((1ull << ab) - 1) << 32;
+    const uint64_t* sorted =
+        radix_sort_pairs(b.s_key, nullptr, b.s_key2, nullptr, z.nS, mask, b.s_tmp, s) ? b.s_key2 : b.s_key;
+    if (z.nS) {
+      k_aw_extract<<<blocks(z.nS, 256), 256, 0, s>>>(sorted, z.nS, b.S);
+      count_launch();
+    }
+    k_aw_seg<<<blocks(g.W + 1, 256), 256, 0, s>>>(sorted, z.nS, g.W, b.seg);
+    count_launch();
+    p.end();
+    return;
+  }
   const uint32_t aw = a_warps(g);
-  k_a_scatter<<<blocks(z.ntA, aw), aw * 32, aw * g.Wp * 4, s>>>(
-      b.ev, z.N, g, z.TA, z.ntA, b.hist_a, b.tile_cnt, b.S, b.acc_key, b.acc_idx, b.acqrel, b.bar,
-      z.grouped ? z.comp_lo : 0u, z.grouped ? z.comp_span : 0u, b.wl_bits, z.wl_log2,
-      (reinterpret_cast<uintptr_t>(b.ev) & 15) == 0);
+  k_a_scatter<<<blocks(z.ntA, aw), aw * 32, aw * g.Wp * 4, s>>>(b.ev, z.N, g, z.TA, z.ntA, b.hist_a, b.tile_cnt,
+                                                                b.S, cpt, vec);
   count_launch();
   k_a_segments<<<blocks(g.W + 1, 256), 256, 0, s>>>(b.hist_a, g.W, z.ntA, z.nS, b.seg);
   count_launch();
