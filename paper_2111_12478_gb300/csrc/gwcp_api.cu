@@ -325,6 +325,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   b.sy_match = get<uint32_t>(c, "sy_match", ns1, &oom);
   b.sy_relk = get<uint32_t>(c, "sy_relk", ns1, &oom);
   b.sy_agent = get<uint32_t>(c, "sy_agent", ns1, &oom);
+  b.sy_samp = get<uint32_t>(c, "sy_samp", ns1 / 32 + 2, &oom);
   b.incs_cnt = get<uint32_t>(c, "incs_cnt", ns1, &oom);
   b.vcount = get<uint32_t>(c, "vcount", g.W + 1, &oom);
   const size_t na1 = size_t(z.n_acqrel) + 1;

@@ -93,6 +93,7 @@ struct Bufs {
   uint32_t* hist_a = nullptr;    // [W * ntA + 1]
   uint32_t* tile_cnt = nullptr;  // [3 * ntA + 3]: accesses, acq/rel, barriers per tile (+ S entries
                                  // per tile when S is built by sorting)
+  uint32_t* sy_samp = nullptr;   // [n_sync / 32 + 1] every 32nd synchronisation entry's trace index
   uint64_t* s_key = nullptr;     // [nS] (agent << 32 | S entry), sorted by agent (+ alt)
   uint64_t* s_key2 = nullptr;
   uint32_t* s_tmp = nullptr;     // the agent sort's scratch

@@ -138,6 +138,7 @@ int analyze(const Event* ev, uint64_t n, const Geo& g, gwcp_race* out, uint64_t 
   uint32_t** sy[] = {&b.sy_spos, &b.sy_idx, &b.sy_kind, &b.sy_aux, &b.sy_N, &b.sy_depth, &b.sy_inner,
                      &b.sy_ver, &b.sy_match, &b.sy_relk, &b.sy_agent, &b.incs_cnt, &b.cs_of_sync};
   for (uint32_t** q : sy) *q = A.take<uint32_t>(ns1);
+  b.sy_samp = A.take<uint32_t>(ns1 / 32 + 2);
   b.sy_start = A.take<uint32_t>(g.W + 1);
   b.vcount = A.take<uint32_t>(g.W + 1);
   b.lk_key = A.take<uint64_t>(na1);

@@ -598,25 +598,50 @@ __global__ void k_c_walk(const Event* ev, Geo g, const uint32_t* seg, const uint
 // events and writes of the records): the access's gap is the one after its agent's latest
 // synchronisation entry before it (a binary search in the agent's entries, which are in
 // trace order); all accesses of such a gap share the epoch and the clock version.
+// every kDSample-th synchronisation entry's trace index: the search below narrows to one
+// block of kDSample entries through this small (cache-resident) array first
+constexpr uint32_t kDSample = 32;
+
+__global__ void k_d_samples(const uint32_t* sy_idx, uint32_t n_sync, uint32_t* samp) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (uint64_t(j) * kDSample < n_sync) samp[j] = sy_idx[size_t(j) * kDSample];
+}
+
 __global__ void k_d_trace(const Event* ev, uint64_t N, Geo g, const uint32_t* sy_start, const uint32_t* sy_idx,
-                          const uint32_t* sy_N, const uint32_t* sy_depth, const uint32_t* sy_ver,
-                          const uint32_t* rowbase, AccInfo* acc_info, const DevStatus* st, bool vec) {
+                          const uint32_t* samp, const uint32_t* sy_N, const uint32_t* sy_depth,
+                          const uint32_t* sy_ver, const uint32_t* rowbase, AccInfo* acc_info, const DevStatus* st,
+                          bool vec) {
   const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N || st->code) return;
   const Event e = load_event(ev, i, vec);
   if (e.op > GWCP_ATOMIC) return;
-  const uint32_t u = e.agent;
-  uint32_t lo = sy_start[u], hi = sy_start[u + 1];  // first entry at or after i: lo
-  while (lo < hi) {
+  const uint32_t u = e.agent, x = uint32_t(i);
+  const uint32_t k0 = sy_start[u], k1 = sy_start[u + 1];
+  // the agent's first entry at or after i is in the block after the last sample (within
+  // [k0, k1)) below i
+  uint32_t lo = (k0 + kDSample - 1) / kDSample, hi = k1 ? (k1 - 1) / kDSample + 1 : 0;
+  const uint32_t js = lo;
+  if (hi < lo) hi = lo;
+  while (lo < hi) {  // first sample at or after i
     const uint32_t mid = (lo + hi) >> 1;
-    if (sy_idx[mid] < uint32_t(i))
+    if (samp[mid] < x)
       lo = mid + 1;
     else
       hi = mid;
   }
+  uint32_t a = lo == js ? k0 : (lo - 1) * kDSample;
+  uint32_t b = lo * kDSample < k1 ? lo * kDSample : k1;
+  if (b < a) b = a;
+  while (a < b) {  // first entry at or after i within the block
+    const uint32_t mid = (a + b) >> 1;
+    if (sy_idx[mid] < x)
+      a = mid + 1;
+    else
+      b = mid;
+  }
   uint32_t epoch = 1, ver = 0;
-  if (lo > sy_start[u]) {
-    const uint32_t k = lo - 1;
+  if (a > k0) {
+    const uint32_t k = a - 1;
     if (sy_depth[k] > 0) return;  // in a critical section: the gap walk below
     epoch = sy_N[k];
     ver = sy_ver[k];
@@ -1217,8 +1242,13 @@ void phaseC_forced(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, 
 
 void phaseD_gaps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   p.begin("d_gaps", double(z.n_acc) * (4 + 16 + 16), s);
-  k_d_trace<<<blocks(z.N, 256), 256, 0, s>>>(b.ev, z.N, g, b.sy_start, b.sy_idx, b.sy_N, b.sy_depth, b.sy_ver,
-                                              b.vcount, b.acc_info, b.st, (reinterpret_cast<uintptr_t>(b.ev) & 15) == 0);
+  if (z.n_sync) {
+    k_d_samples<<<blocks(z.n_sync / kDSample + 1, 256), 256, 0, s>>>(b.sy_idx, z.n_sync, b.sy_samp);
+    count_launch();
+  }
+  k_d_trace<<<blocks(z.N, 256), 256, 0, s>>>(b.ev, z.N, g, b.sy_start, b.sy_idx, b.sy_samp, b.sy_N, b.sy_depth,
+                                              b.sy_ver, b.vcount, b.acc_info, b.st,
+                                              (reinterpret_cast<uintptr_t>(b.ev) & 15) == 0);
   count_launch();
   if (z.n_sync) {
     k_d_fill<<<blocks(uint64_t(z.n_sync) * 32, 256), 256, 0, s>>>(
