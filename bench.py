@@ -727,7 +727,7 @@ def main():
     out_pinned = torch.empty((max(len(races), 1) + 1024) * 2, dtype=torch.int64).pin_memory()
     out_np = out_pinned.numpy().view(np.uint64).reshape(-1, 2)
     parts = []  # per step: device ms of the H2D copy, the analysis, the race read-back
-    for it in range(args.e2e_steps + 1 if args.e2e_steps else 0):
+    for it in range(args.e2e_steps + max(1, args.warmup) if args.e2e_steps else 0):
         torch.cuda.synchronize()
         ev4 = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev4[0].record(stream)
@@ -742,7 +742,7 @@ def main():
         ev4[3].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        if it:  # the first round sizes the context's buffers
+        if it >= max(1, args.warmup):  # untimed rounds size the context's buffers and warm the path
             e2e_times.append(max(wall, ev4[0].elapsed_time(ev4[3]) / 1e3))
             parts.append([ev4[j].elapsed_time(ev4[j + 1]) for j in range(3)])
         d2h = got.nbytes + 8

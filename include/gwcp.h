@@ -405,7 +405,9 @@ int gwcp_pool_set_active_lanes(gwcp_pool* p, uint32_t active);
  * them one after another with dense and with tile clocks and keeps the faster for that
  * class (gwcp_pool_clock_modes). Then runs the n traces as one batch with each candidate
  * number of active lanes (1, 2, 4, 8, 12, 16, 24, 32, up to the pool's lanes), keeps the
- * fastest and returns it in *best (seconds per candidate in secs[], up to 8 entries, may
+ * largest whose time is within 5% of the fastest (near the optimum the times differ by
+ * about that much from run to run, and more lanes overlap more requests that arrive over
+ * time) and returns it in *best (seconds per candidate in secs[], up to 8 entries, may
  * be NULL). Last, with that many lanes, runs the batch once more with the other setting
  * of pack_walkers and keeps whichever was faster (gwcp_pool_settings). Races are counted,
  * not copied. */
