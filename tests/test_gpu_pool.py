@@ -147,7 +147,10 @@ def test_autotune(gw, mix):
     with gw.Pool(0, lanes=8) as P:
         best, secs = P.autotune([(ev, geo.astuple()) for ev, geo in traces])
         assert best in secs and set(secs) == {1, 2, 4, 8}
-        assert secs[best] == min(secs.values())
+        # the most lanes whose batch time is within 5% of the fastest
+        fastest = min(secs.values())
+        assert secs[best] <= 1.05 * fastest
+        assert all(k <= best for k, v in secs.items() if v <= 1.05 * fastest)
         assert P.settings()[0] == best  # (active lanes, packed walkers)
         # width classes 7..10 (128..1024 warps) hold only traces that take both clock
         # representations; class 6 also holds thread-granularity traces
