@@ -73,6 +73,7 @@ struct gwcp_ctx {
   uint64_t alloc_limit = 0;    // gwcp_debug_alloc_limit: cap on the cached buffers' bytes (0 = none)
   cudaStream_t side = nullptr;  // runs the access sort and grouping beside the main phases
   cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr;
+  cudaEvent_t kept_ev = nullptr;  // the access sort's kept count has reached cnt_host[15]
   cudaEvent_t sync_ev = nullptr;  // options.blocking_sync: host waits sleep on this event
   cudaStream_t alloc_s = nullptr;  // stream that buffer (re)allocations are ordered on
   void* stage_host = nullptr;       // pinned staging for race copies into pageable memory
@@ -379,6 +380,10 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   cudaStreamWaitEvent(c->side, c->fork, 0);
   side.armed = true;
   phaseH_sort(b, g, z, sort_mask, side_tmp, c->side, c->prof);
+  if (z.grouped) {  // the kept count sizes the grouping and the check (read before they are enqueued)
+    cudaMemcpyAsync(c->cnt_host + 15, b.n_kept, 4, cudaMemcpyDeviceToHost, c->side);
+    cudaEventRecord(c->kept_ev, c->side);
+  }
   phaseB_sync(b, g, z, s, c->prof);
   cudaMemsetAsync(b.vcount, 0, size_t(g.W + 1) * 4, s);
   cudaMemsetAsync(b.cs_of_sync, 0xFF, ns1 * 4, s);
@@ -548,6 +553,12 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   z.n_groups = z.n_exp;  // upper bound; the kernel reads the exact count on the device
   phaseF_deps(b, g, z, s, c->prof);
   cudaStreamWaitEvent(c->side, c->fork2, 0);
+  if (z.grouped) {
+    // the main stream has phases D-F queued; the sort has usually finished by now
+    if (cudaEventSynchronize(c->kept_ev) != cudaSuccess) return GWCP_ERR_CUDA;
+    z.n_kept = std::min(c->cnt_host[15], z.n_acc);
+    z.n_timeline = sparse_check_blocks(z.n_kept);
+  }
   if (ranked) {
     // the ranker's order of the check: location runs by descending score
     c->prof.begin("h_rank", double(z.n_acc) * (12 + 16 + 12 * 2 * 6 + 12), c->side);
@@ -712,6 +723,7 @@ int gwcp_create(gwcp_ctx** out, int device, const gwcp_options* opt) {
       cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork2, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->kept_ev, cudaEventDisableTiming) != cudaSuccess ||
       (c->opt.blocking_sync &&
        cudaEventCreateWithFlags(&c->sync_ev, cudaEventDisableTiming | cudaEventBlockingSync) != cudaSuccess)) {
     gwcp_destroy(c);
@@ -1220,6 +1232,7 @@ void gwcp_destroy(gwcp_ctx* c) {
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->join) cudaEventDestroy(c->join);
   if (c->fork2) cudaEventDestroy(c->fork2);
+  if (c->kept_ev) cudaEventDestroy(c->kept_ev);
   if (c->sync_ev) cudaEventDestroy(c->sync_ev);
   if (c->side) cudaStreamDestroy(c->side);
   delete c;

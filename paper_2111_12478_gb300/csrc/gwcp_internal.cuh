@@ -383,6 +383,7 @@ struct Sizes {
   bool grouped = false;
   uint32_t comp_lo = 0, comp_span = 0;
   uint32_t wl_log2 = 0;  // bits of the written-location bitmap (log2); 0 = no filter
+  uint32_t n_kept = 0;   // grouped order: accesses the filter kept (read back after the sort)
   // many agents: S is built by a stable sort of (agent, entry) keys instead of per-(agent,
   // tile) counting tables (which would limit phase A to a few warps per SM)
   bool agent_sort = false;

@@ -623,14 +623,17 @@ __device__ __forceinline__ uint32_t conflict_classes(uint32_t cb, bool same_bloc
   }
 }
 
-// Races found by a block are staged in shared memory and appended with one global atomic
-// per block; a block that finds more than kRaceStage spills the rest with one atomic each.
-constexpr uint32_t kRaceStage = 2048;
+// Races found by a warp are staged in shared memory and appended with one global atomic
+// per warp; a warp that finds more than kRaceStage spills the rest with one atomic each.
+// Per warp, not per block: the threads of an access at a hot location search many more
+// partner groups than the rest, and a block-wide append would hold every warp of the
+// block until its slowest thread is done.
+constexpr uint32_t kRaceStage = 256;
 constexpr uint32_t kCheckThreads = 256;
 
 __device__ __forceinline__ void emit_race(const WideCheckArgs& a, uint64_t v, uint32_t* s_cnt, uint64_t* s_buf) {
   const uint32_t slot = atomicAdd(s_cnt, 1u);
-  if (slot == 0) atomicCAS(&a.st->first_race_ns, 0ull, global_ns());  // the block's first race: the earliest
+  if (slot == 0) atomicCAS(&a.st->first_race_ns, 0ull, global_ns());  // the warp's first race: the earliest
                                                                        // stamp wins
   if (slot < kRaceStage) {
     s_buf[slot] = v;
@@ -699,28 +702,39 @@ __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cn
 
 template <int REP>
 __global__ void __launch_bounds__(kCheckThreads, 8) k_wc_check(WideCheckArgs a) {
-  __shared__ uint32_t s_cnt;
-  __shared__ unsigned long long s_base;
-  __shared__ uint64_t s_buf[kRaceStage];
-  if (threadIdx.x == 0) s_cnt = 0;
+  constexpr uint32_t kWarps = kCheckThreads / 32;
+  __shared__ uint32_t s_cnt[kWarps];
+  __shared__ uint64_t s_buf[kWarps][kRaceStage];
+  __shared__ uint32_t s_done, s_found;  // timeline: warps finished, races found by the block
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) s_cnt[warp] = 0;
+  if (threadIdx.x == 0) s_done = s_found = 0;
   __syncthreads();
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t n_eff = a.n_dev ? min(a.n, *a.n_dev) : a.n;
   uint32_t tests = 0;
-  if (p < n_eff) tests = check_one<REP>(a, p, &s_cnt, s_buf);
+  if (p < n_eff) tests = check_one<REP>(a, p, &s_cnt[warp], s_buf[warp]);
   tests = __reduce_add_sync(0xffffffffu, tests);
-  if ((threadIdx.x & 31) == 0 && tests) atomicAdd(&a.st->partner_tests, (unsigned long long)tests);
-  __syncthreads();
-  const uint32_t n = min(s_cnt, kRaceStage);
-  if (threadIdx.x == 0) s_base = n ? atomicAdd(&a.st->n_races, (unsigned long long)n) : 0ull;
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
-    if (s_base + i < a.race_cap) a.races[s_base + i] = s_buf[i];
-  if (a.chunk_ns && threadIdx.x == 0) {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    a.chunk_ns[blockIdx.x] = t;
-    a.chunk_races[blockIdx.x] = s_cnt;
+  __syncwarp();
+  const uint32_t found = s_cnt[warp];
+  const uint32_t n = min(found, kRaceStage);
+  unsigned long long base = 0;
+  if (lane == 0) {
+    if (tests) atomicAdd(&a.st->partner_tests, (unsigned long long)tests);
+    if (n) base = atomicAdd(&a.st->n_races, (unsigned long long)n);
+  }
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (uint32_t i = lane; i < n; i += 32)
+    if (base + i < a.race_cap) a.races[base + i] = s_buf[warp][i];
+  if (a.chunk_ns && lane == 0) {  // the block's last warp stamps the block's end
+    atomicAdd(&s_found, found);
+    __threadfence_block();
+    if (atomicAdd(&s_done, 1u) == kWarps - 1) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      a.chunk_ns[blockIdx.x] = t;
+      a.chunk_races[blockIdx.x] = atomicAdd(&s_found, 0u);
+    }
   }
 }
 
@@ -895,7 +909,7 @@ void phaseI_wide_group(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStrea
 // followed by a regrouping sort.
 void phaseI_grouped(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t s, Prof& p) {
   (void)g;
-  const uint32_t n = z.n_acc;
+  const uint32_t n = z.n_kept;  // the accesses the written-location filter kept
   if (!n) return;
   p.begin("i_wide_group", double(n) * (8 + 4 * 4 + 16 + 12 + 16), s);  // ~ per access
   k_gr_flags<<<nblk(n, 256), 256, 0, s>>>(b.acc_key, n, b.n_kept, b.wc_flag, b.wc_gflag);
@@ -914,7 +928,7 @@ void phaseI_grouped(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t
 uint32_t sparse_check_blocks(uint32_t n_acc) { return nblk(n_acc, kCheckThreads); }
 
 void phaseI_wide_check(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
-  const uint32_t n = z.n_acc;
+  const uint32_t n = z.grouped ? z.n_kept : z.n_acc;
   if (!n) return;
   WideCheckArgs a{};
   a.g = g;
