@@ -598,20 +598,6 @@ __device__ __forceinline__ uint32_t pred_in_group(const WideCheckArgs& a, uint32
   return lo;
 }
 
-// group of agent v among the groups [g0, g1) (sorted by agent), or NONE
-__device__ __forceinline__ uint32_t find_agent(const WideCheckArgs& a, uint32_t g0, uint32_t g1, uint32_t v) {
-  while (g0 < g1) {
-    const uint32_t mid = (g0 + g1) >> 1;
-    const uint32_t x = a.grp_agent[mid];
-    if (x == v) return mid;
-    if (x < v)
-      g0 = mid + 1;
-    else
-      g1 = mid;
-  }
-  return NONE;
-}
-
 // classes a later access of class cb conflicts with and is not exempt from (bit q = class
 // q), given whether the partner shares b's block
 __device__ __forceinline__ uint32_t conflict_classes(uint32_t cb, bool same_block) {
@@ -658,29 +644,39 @@ __device__ uint32_t check_one(const WideCheckArgs& a, uint32_t p, uint32_t* s_cn
   const uint32_t any_mask = conflict_classes(cb, false) | conflict_classes(cb, true);
   const uint32_t x = a.grouped ? b : p;  // "earlier than b" in the order gs holds
   uint32_t tests = 0;
+  // The location's groups of each class are sorted by agent: walk the classes' lists
+  // together (a merge by agent), so that each agent is handled once, from the class
+  // holding its latest conflicting access before b (ties: the lower class).
+  uint32_t cur[4], end[4];
+#pragma unroll
   for (uint32_t q = 0; q < 4; ++q) {
-    if (!((any_mask >> q) & 1u)) continue;
-    const uint32_t g0 = a.rc_off[(run << 2) | q], g1 = a.rc_off[((run << 2) | q) + 1];
-    for (uint32_t gi = g0; gi < g1; ++gi) {
-      const uint32_t v = a.grp_agent[gi];
-      if (v == u) continue;
-      const uint32_t cm = conflict_classes(cb, v / a.g.apb == bu);
-      if (!((cm >> q) & 1u)) continue;
-      const uint32_t j = pred_in_group(a, gi, x);
-      if (j == NONE) continue;
-      const uint32_t pos = a.gs[j];
-      // tested once per agent: from the class holding its latest conflicting access
-      bool latest = true;
-      for (uint32_t q2 = 0; q2 < 4 && latest; ++q2) {
-        if (q2 == q || !((cm >> q2) & 1u)) continue;
-        const uint32_t h0 = a.rc_off[(run << 2) | q2], h1 = a.rc_off[((run << 2) | q2) + 1];
-        const uint32_t g2 = find_agent(a, h0, h1, v);
-        if (g2 == NONE) continue;
-        const uint32_t j2 = pred_in_group(a, g2, x);
-        const uint32_t pos2 = j2 == NONE ? NONE : a.gs[j2];
-        if (pos2 != NONE && (pos2 > pos || (pos2 == pos && q2 < q))) latest = false;
+    const bool on = (any_mask >> q) & 1u;
+    cur[q] = on ? a.rc_off[(run << 2) | q] : 0u;
+    end[q] = on ? a.rc_off[((run << 2) | q) + 1] : 0u;
+  }
+  for (;;) {
+    uint32_t v = NONE;
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q)
+      if (cur[q] < end[q]) v = min(v, a.grp_agent[cur[q]]);
+    if (v == NONE) break;
+    const uint32_t cm = conflict_classes(cb, v / a.g.apb == bu);
+    uint32_t j = NONE, pos = NONE;
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      if (cur[q] >= end[q] || a.grp_agent[cur[q]] != v) continue;
+      const uint32_t gi = cur[q]++;
+      if (v == u || !((cm >> q) & 1u)) continue;
+      const uint32_t jq = pred_in_group(a, gi, x);
+      if (jq == NONE) continue;
+      const uint32_t pq = a.gs[jq];
+      if (pos == NONE || pq > pos) {
+        pos = pq;
+        j = jq;
       }
-      if (!latest) continue;
+    }
+    if (pos == NONE) continue;
+    {
       ++tests;
       const uint32_t qa = a.grouped ? j : pos;  // a*'s position in the primary order
       const uint32_t ai = a.idx[qa];
