@@ -123,6 +123,46 @@ def test_tiled_random(ctx, W, apb):
             same(ctx, ev, geo)
 
 
+@pytest.mark.parametrize("W,apb", [(2080, 32), (4096, 16)])
+def test_agent_sorted_stream(ctx, W, apb):
+    # more than 2048 agents: phase A builds the agent-sorted stream by a sort on the agent
+    # (2080 agents: a ragged last tile), and the check runs on the grouped order with the
+    # written-location filter
+    from paper_2111_12478_gb300 import gwcp
+
+    for fam in TG.FAMILIES:
+        ev, geo = TG.random_small(3, fam, n_events=6000, num_agents=W, agents_per_block=apb,
+                                  granularity=WARP_GRAN, n_locks=4, n_keys=8)
+        same(ctx, ev, geo)
+    b = TG.TraceBuilder()  # synchronisation only
+    b.acq(0, 1)
+    b.rel(0, 1)
+    b.barrier(W // apb - 1, apb=apb)
+    b.acq(W - 1, 1)
+    b.rel(W - 1, 1)
+    assert len(same(ctx, b.build(), TG.Geometry(W, apb, WARP_GRAN))) == 0
+    b = TG.TraceBuilder()  # reads only: the filter leaves nothing to check
+    for k in range(64):
+        b.rd(k * 37 % W, 0x100 + 4 * (k % 5))
+    assert len(same(ctx, b.build(), TG.Geometry(W, apb, WARP_GRAN))) == 0
+    b = TG.TraceBuilder()  # one write among reads of the same location: races with each later read
+    b.wr(5, 0x40)
+    for k in range(1, 40):
+        b.rd(k * 53 % W, 0x40)
+    same(ctx, b.build(), TG.Geometry(W, apb, WARP_GRAN))
+    # an event that breaks W1 (agent out of range) after some valid ones
+    ev, geo = TG.random_small(4, "mixed", n_events=3000, num_agents=W, agents_per_block=apb,
+                              granularity=WARP_GRAN, n_locks=4, n_keys=8)
+    ev = ev.copy()
+    ev["agent"][1777] = W + 5
+    rc, bad = O.validate(ev, *geo.astuple())
+    assert rc == O.ERR_INVALID_TRACE and bad == 1777
+    ctx.load_trace(ev, *geo.astuple())
+    with pytest.raises(gwcp.GwcpError) as ei:
+        ctx.compute_order()
+    assert ei.value.code == gwcp.ERR_INVALID_TRACE and ei.value.bad_index == bad
+
+
 @pytest.mark.parametrize("W,apb", [(64, 8), (256, 32), (512, 16), (1024, 32)])
 def test_tiles_at_dense_widths(W, apb):
     # the tile-table clocks at widths the register clocks also take: same races as the oracle
