@@ -326,7 +326,11 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   b.sy_match = get<uint32_t>(c, "sy_match", ns1, &oom);
   b.sy_relk = get<uint32_t>(c, "sy_relk", ns1, &oom);
   b.sy_agent = get<uint32_t>(c, "sy_agent", ns1, &oom);
-  b.sy_samp = get<uint32_t>(c, "sy_samp", ns1 / 32 + 2, &oom);
+  // phase D's index: windows of 2^d_shift events, at most 2^23 entries over all agents
+  z.d_shift = 8;
+  while (uint64_t(g.W) * ((z.N >> z.d_shift) + 2) > (1ull << 23)) ++z.d_shift;
+  z.d_nw = uint32_t((z.N >> z.d_shift) + 2);
+  b.d_index = get<uint32_t>(c, "d_index", size_t(g.W) * z.d_nw, &oom);
   b.incs_cnt = get<uint32_t>(c, "incs_cnt", ns1, &oom);
   b.vcount = get<uint32_t>(c, "vcount", g.W + 1, &oom);
   const size_t na1 = size_t(z.n_acqrel) + 1;

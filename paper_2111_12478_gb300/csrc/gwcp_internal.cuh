@@ -93,7 +93,7 @@ struct Bufs {
   uint32_t* hist_a = nullptr;    // [W * ntA + 1]
   uint32_t* tile_cnt = nullptr;  // [3 * ntA + 3]: accesses, acq/rel, barriers per tile (+ S entries
                                  // per tile when S is built by sorting)
-  uint32_t* sy_samp = nullptr;   // [n_sync / 32 + 1] every 32nd synchronisation entry's trace index
+  uint32_t* d_index = nullptr;   // [W * d_nw] phase D: each agent's first sync entry per trace window
   uint64_t* s_key = nullptr;     // [nS] (agent << 32 | S entry), sorted by agent (+ alt)
   uint64_t* s_key2 = nullptr;
   uint32_t* s_tmp = nullptr;     // the agent sort's scratch
@@ -384,6 +384,7 @@ struct Sizes {
   uint32_t comp_lo = 0, comp_span = 0;
   uint32_t wl_log2 = 0;  // bits of the written-location bitmap (log2); 0 = no filter
   uint32_t n_kept = 0;   // grouped order: accesses the filter kept (read back after the sort)
+  uint32_t d_shift = 0, d_nw = 0;  // phase D index: trace windows of 2^d_shift events, d_nw per agent
   // many agents: S is built by a stable sort of (agent, entry) keys instead of per-(agent,
   // tile) counting tables (which would limit phase A to a few warps per SM)
   bool agent_sort = false;

@@ -138,7 +138,10 @@ int analyze(const Event* ev, uint64_t n, const Geo& g, gwcp_race* out, uint64_t 
   uint32_t** sy[] = {&b.sy_spos, &b.sy_idx, &b.sy_kind, &b.sy_aux, &b.sy_N, &b.sy_depth, &b.sy_inner,
                      &b.sy_ver, &b.sy_match, &b.sy_relk, &b.sy_agent, &b.incs_cnt, &b.cs_of_sync};
   for (uint32_t** q : sy) *q = A.take<uint32_t>(ns1);
-  b.sy_samp = A.take<uint32_t>(ns1 / 32 + 2);
+  z.d_shift = 8;
+  while (uint64_t(g.W) * ((z.N >> z.d_shift) + 2) > (1ull << 23)) ++z.d_shift;
+  z.d_nw = uint32_t((z.N >> z.d_shift) + 2);
+  b.d_index = A.take<uint32_t>(size_t(g.W) * z.d_nw);
   b.sy_start = A.take<uint32_t>(g.W + 1);
   b.vcount = A.take<uint32_t>(g.W + 1);
   b.lk_key = A.take<uint64_t>(na1);

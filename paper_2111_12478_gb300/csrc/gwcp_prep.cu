@@ -598,41 +598,47 @@ __global__ void k_c_walk(const Event* ev, Geo g, const uint32_t* seg, const uint
 // events and writes of the records): the access's gap is the one after its agent's latest
 // synchronisation entry before it (a binary search in the agent's entries, which are in
 // trace order); all accesses of such a gap share the epoch and the clock version.
-// every kDSample-th synchronisation entry's trace index: the search below narrows to one
-// block of kDSample entries through this small (cache-resident) array first
-constexpr uint32_t kDSample = 32;
+// Phase D's index: table[u * nw + w] is agent u's first synchronisation entry at or after
+// trace position w << shift (sy_start[u + 1] when there is none), so an access at i
+// searches only the entries of its own window, [table[w], table[w + 1]). One thread per
+// entry fills the windows from after its predecessor's window up to its own.
+__global__ void k_d_index(const uint32_t* sy_idx, const uint32_t* sy_agent, const uint32_t* sy_start, uint32_t n_sync,
+                          uint32_t shift, uint32_t nw, uint32_t* table) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_sync) return;
+  const uint32_t u = sy_agent[k];
+  const uint32_t wk = sy_idx[k] >> shift;
+  const uint32_t w0 = k > sy_start[u] ? (sy_idx[k - 1] >> shift) + 1 : 0;
+  uint32_t* row = table + size_t(u) * nw;
+  for (uint32_t w = w0; w <= wk; ++w) row[w] = k;
+}
 
-__global__ void k_d_samples(const uint32_t* sy_idx, uint32_t n_sync, uint32_t* samp) {
-  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (uint64_t(j) * kDSample < n_sync) samp[j] = sy_idx[size_t(j) * kDSample];
+// the windows after an agent's last entry (all of them when it has none): a warp per agent
+__global__ void k_d_index_tail(const uint32_t* sy_idx, const uint32_t* sy_start, uint32_t W, uint32_t shift,
+                               uint32_t nw, uint32_t* table) {
+  const uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (u >= W) return;
+  const uint32_t k0 = sy_start[u], k1 = sy_start[u + 1];
+  const uint32_t w0 = k1 > k0 ? (sy_idx[k1 - 1] >> shift) + 1 : 0;
+  uint32_t* row = table + size_t(u) * nw;
+  for (uint32_t w = w0 + lane; w < nw; w += 32) row[w] = k1;
 }
 
 __global__ void k_d_trace(const Event* ev, uint64_t N, Geo g, const uint32_t* sy_start, const uint32_t* sy_idx,
-                          const uint32_t* samp, const uint32_t* sy_N, const uint32_t* sy_depth,
-                          const uint32_t* sy_ver, const uint32_t* rowbase, AccInfo* acc_info, const DevStatus* st,
-                          bool vec) {
+                          const uint32_t* table, uint32_t shift, uint32_t nw, const uint32_t* sy_N,
+                          const uint32_t* sy_depth, const uint32_t* sy_ver, const uint32_t* rowbase, AccInfo* acc_info,
+                          const DevStatus* st, bool vec) {
   const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N || st->code) return;
   const Event e = load_event(ev, i, vec);
   if (e.op > GWCP_ATOMIC) return;
   const uint32_t u = e.agent, x = uint32_t(i);
-  const uint32_t k0 = sy_start[u], k1 = sy_start[u + 1];
-  // the agent's first entry at or after i is in the block after the last sample (within
-  // [k0, k1)) below i
-  uint32_t lo = (k0 + kDSample - 1) / kDSample, hi = k1 ? (k1 - 1) / kDSample + 1 : 0;
-  const uint32_t js = lo;
-  if (hi < lo) hi = lo;
-  while (lo < hi) {  // first sample at or after i
-    const uint32_t mid = (lo + hi) >> 1;
-    if (samp[mid] < x)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  uint32_t a = lo == js ? k0 : (lo - 1) * kDSample;
-  uint32_t b = lo * kDSample < k1 ? lo * kDSample : k1;
-  if (b < a) b = a;
-  while (a < b) {  // first entry at or after i within the block
+  const uint32_t k0 = sy_start[u];
+  // the agent's first entry at or after i: among its entries in i's window, else the first
+  // entry of a later window
+  const uint32_t* row = table + size_t(u) * nw + (x >> shift);
+  uint32_t a = row[0], b = row[1];
+  while (a < b) {
     const uint32_t mid = (a + b) >> 1;
     if (sy_idx[mid] < x)
       a = mid + 1;
@@ -1243,11 +1249,15 @@ void phaseC_forced(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, 
 void phaseD_gaps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   p.begin("d_gaps", double(z.n_acc) * (4 + 16 + 16), s);
   if (z.n_sync) {
-    k_d_samples<<<blocks(z.n_sync / kDSample + 1, 256), 256, 0, s>>>(b.sy_idx, z.n_sync, b.sy_samp);
+    k_d_index<<<blocks(z.n_sync, 256), 256, 0, s>>>(b.sy_idx, b.sy_agent, b.sy_start, z.n_sync, z.d_shift, z.d_nw,
+                                                    b.d_index);
     count_launch();
   }
-  k_d_trace<<<blocks(z.N, 256), 256, 0, s>>>(b.ev, z.N, g, b.sy_start, b.sy_idx, b.sy_samp, b.sy_N, b.sy_depth,
-                                              b.sy_ver, b.vcount, b.acc_info, b.st,
+  k_d_index_tail<<<blocks(uint64_t(g.W) * 32, 256), 256, 0, s>>>(b.sy_idx, b.sy_start, g.W, z.d_shift, z.d_nw,
+                                                                 b.d_index);
+  count_launch();
+  k_d_trace<<<blocks(z.N, 256), 256, 0, s>>>(b.ev, z.N, g, b.sy_start, b.sy_idx, b.d_index, z.d_shift, z.d_nw,
+                                              b.sy_N, b.sy_depth, b.sy_ver, b.vcount, b.acc_info, b.st,
                                               (reinterpret_cast<uintptr_t>(b.ev) & 15) == 0);
   count_launch();
   if (z.n_sync) {
