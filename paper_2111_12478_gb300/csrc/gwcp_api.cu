@@ -66,6 +66,7 @@ struct gwcp_ctx {
   uint64_t counters[GWCP_N_COUNTERS] = {};
   unsigned long long first_race_ns = 0;  // last compute: %globaltimer of its first race (0: none)
   uint64_t key_mask = 0;                 // last compute: location-key bits that vary
+  bool acc_info_partial = false;         // last compute wrote the kept accesses' records only
   uint64_t clock_words[3] = {};  // last compute: tiles, pool words taken, words written
   uint64_t tile_cap_hint = 0;  // wide clocks: pool size that the last run needed
   bool compressed = false;     // GWCP_CLOCKS_COMPRESSED was in force at gwcp_load_trace
@@ -276,6 +277,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   z.n_sync = z.nS - z.n_acc;
   const uint64_t key_mask = c->st_host->key_or ^ c->st_host->key_and;
   c->key_mask = key_mask;
+  c->acc_info_partial = false;
   // grouped access order for the partner check (no ranker): the composite key (location,
   // class, agent) must fit 64 bits, i.e. the location's varying address bits at most 48
   uint64_t sort_mask = key_mask;
@@ -521,6 +523,7 @@ int run(gwcp_ctx* c, cudaStream_t s) {
   }
 
   phaseD_gaps(b, g, z, s, c->prof);
+  c->acc_info_partial = z.wl_log2 != 0;
   // the access grouping and the check's carries need the access records (phase D), not
   // clock values: they follow the sort on the side stream while the propagation runs on s
   cudaEventRecord(c->fork2, s);
@@ -915,6 +918,16 @@ int read_version(gwcp_ctx* c, uint32_t row, uint32_t* out) {
 }
 }  // namespace
 
+namespace {
+// the records of every access (a grouped-order compute writes only the kept accesses')
+int complete_acc_info(gwcp_ctx* c, cudaStream_t s) {
+  if (!c->acc_info_partial) return GWCP_OK;
+  phaseD_trace(c->b, c->g, c->z, s, false);
+  c->acc_info_partial = false;
+  return cudaStreamSynchronize(s) == cudaSuccess ? GWCP_OK : GWCP_ERR_CUDA;
+}
+}  // namespace
+
 int gwcp_debug_clock(gwcp_ctx* c, uint64_t idx, int which, uint32_t* out) {
   if (!c || !out) return GWCP_ERR_ARGS;
   if (!c->computed || c->compute_rc) return GWCP_ERR_STATE;
@@ -930,6 +943,7 @@ int gwcp_debug_clock(gwcp_ctx* c, uint64_t idx, int which, uint32_t* out) {
   uint32_t version = kNoneHost;
   if (e.op <= GWCP_ATOMIC) {
     if (which != 0) return GWCP_ERR_UNSUPPORTED;
+    if (int rc = complete_acc_info(c, nullptr)) return rc;
     AccInfo inf;
     cudaMemcpy(&inf, b.acc_info + idx, sizeof(inf), cudaMemcpyDeviceToHost);
     version = inf.row;
@@ -1070,6 +1084,7 @@ int gwcp_location_features(gwcp_ctx* c, float* feat, uint64_t* keys, uint64_t ca
     in.key = k0;
     in.idx = v0;
   }
+  if (int rc = complete_acc_info(c, s)) return rc;
   in.info = b.acc_info;
   in.n_acc = z.n_acc;
   in.incs_idx = b.incs_idx;

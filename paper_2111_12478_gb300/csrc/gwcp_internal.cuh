@@ -433,6 +433,9 @@ void phaseB_sync(const Bufs& b, const Geo& g, Sizes& z, cudaStream_t s, Prof& p)
 void phaseC_walk(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 void phaseC_forced(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 void phaseD_gaps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
+// phase D's trace-order pass alone (filtered: the grouped order's kept accesses only; the
+// records of the others are then left unwritten)
+void phaseD_trace(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, bool filtered);
 void phaseE_locks(Bufs& b, const Geo& g, const Sizes& z, uint64_t lock_mask, cudaStream_t s, Prof& p);
 void phaseE_walk(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p);
 void phaseF_incs(const Bufs& b, const Geo& g, const Sizes& z, uint64_t key_mask, cudaStream_t s, Prof& p);

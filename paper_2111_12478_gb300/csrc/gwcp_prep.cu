@@ -627,12 +627,18 @@ __global__ void k_d_index_tail(const uint32_t* sy_idx, const uint32_t* sy_start,
 __global__ void k_d_trace(const Event* ev, uint64_t N, Geo g, const uint32_t* sy_start, const uint32_t* sy_idx,
                           const uint32_t* table, uint32_t shift, uint32_t nw, const uint32_t* sy_N,
                           const uint32_t* sy_depth, const uint32_t* sy_ver, const uint32_t* rowbase, AccInfo* acc_info,
-                          const DevStatus* st, bool vec) {
+                          const DevStatus* st, bool vec, const uint32_t* wl_bits, uint32_t wl_log2,
+                          uint32_t comp_lo, uint32_t comp_span) {
   const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N || st->code) return;
   const Event e = load_event(ev, i, vec);
   if (e.op > GWCP_ATOMIC) return;
   const uint32_t u = e.agent, x = uint32_t(i);
+  if (wl_log2) {  // grouped order: a location without write-class accesses is never checked
+    const uint64_t ck = composite_key(location_key(e, g.apb), access_class(e), u, comp_lo, comp_span);
+    const uint32_t h = wl_bit(ck >> 15, wl_log2);
+    if (!((__ldg(wl_bits + (h >> 5)) >> (h & 31)) & 1u)) return;
+  }
   const uint32_t k0 = sy_start[u];
   // the agent's first entry at or after i: among its entries in i's window, else the first
   // entry of a later window
@@ -1246,6 +1252,15 @@ void phaseC_forced(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, 
   p.end();
 }
 
+// the trace-order pass of phase D; filtered: only accesses the grouped order keeps
+void phaseD_trace(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, bool filtered) {
+  k_d_trace<<<blocks(z.N, 256), 256, 0, s>>>(b.ev, z.N, g, b.sy_start, b.sy_idx, b.d_index, z.d_shift, z.d_nw,
+                                              b.sy_N, b.sy_depth, b.sy_ver, b.vcount, b.acc_info, b.st,
+                                              (reinterpret_cast<uintptr_t>(b.ev) & 15) == 0, b.wl_bits,
+                                              filtered ? z.wl_log2 : 0u, z.comp_lo, z.comp_span);
+  count_launch();
+}
+
 void phaseD_gaps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Prof& p) {
   p.begin("d_gaps", double(z.n_acc) * (4 + 16 + 16), s);
   if (z.n_sync) {
@@ -1256,10 +1271,7 @@ void phaseD_gaps(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s, Pr
   k_d_index_tail<<<blocks(uint64_t(g.W) * 32, 256), 256, 0, s>>>(b.sy_idx, b.sy_start, g.W, z.d_shift, z.d_nw,
                                                                  b.d_index);
   count_launch();
-  k_d_trace<<<blocks(z.N, 256), 256, 0, s>>>(b.ev, z.N, g, b.sy_start, b.sy_idx, b.d_index, z.d_shift, z.d_nw,
-                                              b.sy_N, b.sy_depth, b.sy_ver, b.vcount, b.acc_info, b.st,
-                                              (reinterpret_cast<uintptr_t>(b.ev) & 15) == 0);
-  count_launch();
+  phaseD_trace(b, g, z, s, true);
   if (z.n_sync) {
     k_d_fill<<<blocks(uint64_t(z.n_sync) * 32, 256), 256, 0, s>>>(
         b.ev, g, z.n_sync, b.S, b.seg, b.sy_start, b.sy_agent, b.sy_spos, b.sy_N, b.sy_depth, b.sy_ver, b.incs_cnt,
