@@ -643,7 +643,7 @@ def main():
     ap.add_argument("--ref-events", type=int, default=500_000,
                     help="events of the headline workload the reference arm's oracle analyses per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--events", type=int, default=0, help="analyse only this many events of the workload "
                     "(profiling runs); 0 = the full workload")
     ap.add_argument("--workload", default=WORKLOAD, help="a trace shape of tracegen.WORKLOADS")
