@@ -790,7 +790,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": int(ev.nbytes),
                     "d2h_bytes_per_step": int(d2h), "steps": len(e2e_times),
                     "step_ms": [round(t * 1e3, 2) for t in e2e_times],
-                    "device_ms_h2d_analysis_d2h": [round(float(np.mean([p[j] for p in parts])), 2) for j in range(3)]}
+                    "device_ms_h2d_analysis_d2h": [round(float(np.mean([p[j] for p in parts])), 2) for j in range(3)],
+                    "device_ms_per_step": [[round(x, 2) for x in p] for p in parts]}
             if e2e_value else None,
             "roofline": prop_roofline("k_prop_wide" if tiles else "k_propagate", args.workload,
                                       phases["g_propagate"][0], cnt, geo.num_agents, tiles, peak, peak_kind),
