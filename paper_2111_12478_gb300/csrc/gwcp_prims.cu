@@ -107,8 +107,9 @@ __global__ void k_radix_hist(const uint64_t* keys, size_t n, const uint32_t* n_d
 // rounds of 32 consecutive items; ranks within a round follow lane order. The tile is
 // first put in digit order in shared memory, then written out so that consecutive threads
 // write consecutive positions of one digit's run (coalesced stores instead of one sector
-// per item).
-__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint64_t* kin, const uint32_t* vin,
+// per item). Five blocks per SM (48 registers; 60 allowed only four): measured 0.75 ms
+// faster per 200M-event analysis; six spill.
+__global__ void __launch_bounds__(RS_THREADS, 5) k_radix_scatter(const uint64_t* kin, const uint32_t* vin,
                                                               uint64_t* kout, uint32_t* vout, size_t n,
                                                               const uint32_t* n_dev, int shift,
                                                               const uint32_t* offs, uint32_t ntiles,
