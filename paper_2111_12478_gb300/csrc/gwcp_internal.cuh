@@ -187,7 +187,7 @@ struct Bufs {
   uint32_t* fb_boff = nullptr;                     // [n_sync] offset from each barrier entry on
   // phase I: check
   uint32_t* tails = nullptr;    // [n_chunks * 4 * Wp * 2]
-  // wide clocks: accesses regrouped by (location, class, agent)
+  // sparse check: accesses grouped by (location, class, agent)
   uint32_t* wc_flag = nullptr;   // [n_acc] location-run starts in key order
   uint32_t* wc_run = nullptr;    // [n_acc + 1] exclusive scan of wc_flag
   uint64_t* wc_key = nullptr;    // [n_acc] (run << 15 | class << 13 | agent) (+ alt)
@@ -484,8 +484,9 @@ void races_to_records(const uint64_t* words, uint64_t n, gwcp_race* out, cudaStr
 // check timeline: per chunk the globaltimer at its end and its race count (optional)
 void stamp_now(unsigned long long* at, cudaStream_t s);
 
-// wide clocks (gwcp_wide.cu): the walker over tile tables (after the plan is built), the
-// regrouping of accesses (beside the propagation) and the per-access partner check
+// wide clocks and the sparse check (gwcp_wide.cu): the walker over tile tables (after the
+// plan is built), the grouping of accesses (on the side stream: the grouped order's groups,
+// or with a ranker the regrouping of its location order) and the per-access partner check
 int phaseG_wide(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s);
 void phaseI_wide_group(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t s, Prof& p);
 void phaseI_grouped(Bufs& b, const Geo& g, Sizes& z, uint32_t* tmp, cudaStream_t s, Prof& p);
