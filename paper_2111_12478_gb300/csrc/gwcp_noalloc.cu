@@ -134,7 +134,7 @@ int analyze(const Event* ev, uint64_t n, const Geo& g, gwcp_race* out, uint64_t 
   b.acc_idx = A.take<uint32_t>(z.n_acc);
   b.acc_key2 = A.take<uint64_t>(z.n_acc);
   b.acc_idx2 = A.take<uint32_t>(z.n_acc);
-  b.sy_cnt = A.take<uint32_t>(z.nS / 4096 + 2);
+  b.sy_cnt = A.take<uint32_t>(z.nS / 512 + 2);
   uint32_t** sy[] = {&b.sy_spos, &b.sy_idx, &b.sy_kind, &b.sy_aux, &b.sy_N, &b.sy_depth, &b.sy_inner,
                      &b.sy_ver, &b.sy_match, &b.sy_relk, &b.sy_agent, &b.incs_cnt, &b.cs_of_sync};
   for (uint32_t** q : sy) *q = A.take<uint32_t>(ns1);

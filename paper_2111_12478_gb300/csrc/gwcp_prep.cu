@@ -416,51 +416,48 @@ __device__ __forceinline__ uint32_t lower_bound_dev(const T* a, uint32_t n, T x)
   return lo;
 }
 
-// Phase B
-constexpr int B_THREADS = 256, B_ITEMS = 16, B_TILE = B_THREADS * B_ITEMS;
+// Phase B: the synchronisation entries of S in S order. One warp per chunk of B_CHUNK
+// consecutive S positions (its own offset from the counting pass, ballot ranks within a
+// round of 32), so no warp waits for another.
+constexpr int B_THREADS = 256, B_ROUNDS = 16, B_CHUNK = 32 * B_ROUNDS;
 
-__global__ void k_b_count(const uint32_t* S, uint32_t nS, uint32_t* cnt) {
-  const uint32_t base = blockIdx.x * B_TILE;
+__global__ void k_b_count(const uint32_t* S, uint32_t nS, uint32_t n_chunks, uint32_t* cnt) {
+  const uint32_t chunk = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (chunk >= n_chunks) return;
+  const uint32_t base = chunk * B_CHUNK;
   uint32_t c = 0;
-  for (int j = 0; j < B_ITEMS; ++j) {
-    uint32_t p = base + j * B_THREADS + threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < B_ROUNDS; ++j) {
+    const uint32_t p = base + j * 32 + lane;
     if (p < nS && s_kind(S[p]) != K_ACCESS) ++c;
   }
   c = __reduce_add_sync(0xffffffffu, c);
-  __shared__ uint32_t ws[B_THREADS / 32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t t = 0;
-    for (int w = 0; w < B_THREADS / 32; ++w) t += ws[w];
-    cnt[blockIdx.x] = t;
-  }
+  if (lane == 0) cnt[chunk] = c;
 }
 
-__global__ void k_b_scatter(const Event* ev, const uint32_t* S, uint32_t nS, const uint32_t* off,
+__global__ void k_b_scatter(const Event* ev, const uint32_t* S, uint32_t nS, uint32_t n_chunks, const uint32_t* off,
                             const uint32_t* bar, uint32_t n_bar, const uint32_t* acqrel, uint32_t n_acqrel,
                             uint32_t* sy_spos, uint32_t* sy_idx, uint32_t* sy_kind, uint32_t* sy_aux,
                             uint64_t* lk_key, uint32_t* lk_k) {
-  // items visited in rounds of 256 consecutive S positions, so a block-wide scan per
-  // round preserves S order
-  const uint32_t base = blockIdx.x * B_TILE;
-  uint32_t run = off[blockIdx.x];
-  __shared__ uint32_t ws[B_THREADS / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j = 0; j < B_ITEMS; ++j) {
-    const uint32_t p = base + j * B_THREADS + threadIdx.x;
-    const uint32_t s = p < nS ? S[p] : 0;
-    const bool sy = p < nS && s_kind(s) != K_ACCESS;
+  const uint32_t chunk = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (chunk >= n_chunks) return;
+  const uint32_t base = chunk * B_CHUNK;
+  uint32_t sv[B_ROUNDS];
+#pragma unroll
+  for (int j = 0; j < B_ROUNDS; ++j) {
+    const uint32_t p = base + j * 32 + lane;
+    sv[j] = p < nS ? S[p] : (K_ACCESS << 30);
+  }
+  uint32_t run = off[chunk];
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int j = 0; j < B_ROUNDS; ++j) {
+    const uint32_t p = base + j * 32 + lane;
+    const uint32_t s = sv[j];
+    const bool sy = s_kind(s) != K_ACCESS;
     const uint32_t m = __ballot_sync(0xffffffffu, sy);
-    if (lane == 0) ws[warp] = __popc(m);
-    __syncthreads();
-    uint32_t before = 0, total = 0;
-    for (int w = 0; w < B_THREADS / 32; ++w) {
-      if (w < warp) before += ws[w];
-      total += ws[w];
-    }
     if (sy) {
-      const uint32_t k = run + before + __popc(m & lanemask_lt());
+      const uint32_t k = run + __popc(m & lt);
       const uint32_t idx = s_idx(s), kind = s_kind(s);
       sy_spos[k] = p;
       sy_idx[k] = idx;
@@ -472,8 +469,7 @@ __global__ void k_b_scatter(const Event* ev, const uint32_t* S, uint32_t nS, con
         lk_k[q] = k;
       }
     }
-    run += total;
-    __syncthreads();
+    run += __popc(m);
   }
 }
 
@@ -1198,14 +1194,15 @@ void phaseA_scatter(const Bufs& b, const Geo& g, const Sizes& z, cudaStream_t s,
 }
 
 void phaseB_sync(const Bufs& b, const Geo& g, Sizes& z, cudaStream_t s, Prof& p) {
-  z.ntS = blocks(z.nS, B_TILE);
+  z.ntS = blocks(z.nS, B_CHUNK);  // chunks of S, one warp each
   p.begin("b_sync", double(z.nS) * 8);
   if (z.ntS) {
-    k_b_count<<<z.ntS, B_THREADS, 0, s>>>(b.S, z.nS, b.sy_cnt);
+    k_b_count<<<blocks(uint64_t(z.ntS) * 32, B_THREADS), B_THREADS, 0, s>>>(b.S, z.nS, z.ntS, b.sy_cnt);
     count_launch();
     scan_exclusive(b.sy_cnt, b.sy_cnt, z.ntS, b.sy_cnt + z.ntS, b.scan_tmp, s);
-    k_b_scatter<<<z.ntS, B_THREADS, 0, s>>>(b.ev, b.S, z.nS, b.sy_cnt, b.bar, z.n_bar, b.acqrel, z.n_acqrel,
-                                            b.sy_spos, b.sy_idx, b.sy_kind, b.sy_aux, b.lk_key, b.lk_k);
+    k_b_scatter<<<blocks(uint64_t(z.ntS) * 32, B_THREADS), B_THREADS, 0, s>>>(
+        b.ev, b.S, z.nS, z.ntS, b.sy_cnt, b.bar, z.n_bar, b.acqrel, z.n_acqrel, b.sy_spos, b.sy_idx, b.sy_kind,
+        b.sy_aux, b.lk_key, b.lk_k);
     count_launch();
   }
   k_b_starts<<<blocks(g.W + 1, 256), 256, 0, s>>>(b.seg, g.W, b.sy_spos, z.n_sync, b.sy_start);
